@@ -1,0 +1,230 @@
+/*
+ * mpi_ffl.h -- C ABI of the GB300 library for the compressed 3D field-free-line
+ * (FFL) MPI operator and its regularised reconstruction (arXiv 2511.06627).
+ *
+ * Operator (Sec. 2.2, Eq. (23); Sec. 3.3, Eq. (24)):
+ *     b = A x,  A = blockdiag_m(S D_Gamma F V E H B) [P_theta_1; ...; P_theta_M]
+ *   P_theta  parallel-beam line integrals about z (Sec. 2.2, Eqs. (16)-(19)),
+ *            Joseph interpolation, rays marched along rows when |cos| >= |sin|
+ *   B        one scalar gain per angle (uniform receive coil, Sec. 1.3 Table 1)
+ *   H        Langevin-derivative PSF along the drive axis, h(u) = 3 L'(u/a) with
+ *            full width at half maximum fwhm_vox (Appendix B, Eq. (31)); evaluated
+ *            on a grid upsample_q times finer than the detector bins, full support
+ *   E, V     the convolved row sampled at the FFL position xi_j by linear
+ *            interpolation on that grid, times the FFL velocity v_j (Eq. (7))
+ *   F        unitary DFT with the +i sign (Appendix A, Eq. (27))
+ *   D_Gamma  receive-chain transfer function on the kept bins (Sec. 2.1, Eq. (13))
+ *   S        harmonic-band selection (Sec. 2.1, Eq. (11)): bins k*P + delta,
+ *            k = k_min..k_max, delta = -half_width..half_width
+ * Reconstruction (Sec. 3.3, Eqs. (25)-(26)): accelerated projected gradient
+ * descent on ||A x - b||^2 + lambda ||T x||^2, T = forward differences along
+ * x, y, z with no wrap-around.
+ *
+ * Layouts
+ *   volume  float x[z][y][x], nx == ny, contiguous
+ *   data    float b[m][z][k][delta][2]: complex (re, im) interleaved, one raster
+ *           line per z slice, bins k-major with delta ascending
+ *   A^T is taken under the real inner product: x = Re(A^H b).
+ *
+ * Ownership and streams
+ *   Every pointer named d_* is device memory owned by the caller. The handle owns
+ *   its tables and workspace and copies every host array it is given at create.
+ *   All work is enqueued on the caller's stream (cudaStream_t passed as void*,
+ *   NULL = legacy default stream); calls return without waiting for the GPU unless
+ *   stated. A handle may be used from one stream at a time.
+ *
+ * Errors
+ *   Every call returns 0 on success or a negative MPI_FFL_ERR_* code; nothing
+ *   throws or aborts across the ABI. mpi_ffl_last_error() gives a message for the
+ *   last failure of a handle (or of create, when passed NULL; thread-local).
+ */
+#ifndef MPI_FFL_H
+#define MPI_FFL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MPI_FFL_OK 0
+#define MPI_FFL_ERR_INVALID_ARG (-1)
+#define MPI_FFL_ERR_OOM (-2)
+#define MPI_FFL_ERR_CUDA (-3)
+#define MPI_FFL_ERR_NONFINITE (-4)
+#define MPI_FFL_ERR_TIMEOUT (-5)
+#define MPI_FFL_ERR_UNSUPPORTED (-6)
+
+/* Arithmetic of the harmonic-band DFT and its transpose (the other stages are FP32). */
+#define MPI_FFL_PREC_FP32 0   /* plain: FP32 FMA on CUDA cores, stage by stage        */
+#define MPI_FFL_PREC_BF16X3 1 /* tensor cores: bf16 hi+lo split, 3 products, FP32 acc  */
+#define MPI_FFL_PREC_TF32 2   /* tensor cores: tf32 operands, FP32 accumulate          */
+
+typedef struct mpi_ffl_handle mpi_ffl_handle;
+
+/* Volume and FFL angles (Sec. 2.2; Sec. 3.1: angles equally spaced over 180 deg). */
+typedef struct {
+    int32_t nx, ny, nz;        /* nx == ny; voxel (x, y) of slice z at x[(z*ny+y)*nx+x]      */
+    int32_t n_angles;          /* M >= 1                                                  */
+    const double *angles_rad;  /* host, n_angles; NULL -> theta_m = m*pi/M                */
+    const float *gain;         /* host, n_angles; NULL -> 1 (B of Sec. 1.3, Table 1)      */
+} mpi_ffl_geometry;
+
+/* Drive and slow raster (Sec. 1.2, Eqs. (3)-(4); Sec. 3.1). One raster line per z slice:
+ * xi_j = c_j + A sin(2 pi j / S + phi0), c_j = (N-1) j / (L-1) (reversed on odd lines
+ * when zigzag), j = 0..L-1, L = S*P; v_j = d xi / d j in detector bins per sample. */
+typedef struct {
+    int32_t samples_per_period; /* S >= 2                                         */
+    int32_t periods_per_line;   /* P >= 1                                         */
+    double drive_amp_vox;       /* A >= 0, in detector bins (= voxels)            */
+    double drive_phase;         /* phi0, radians                                  */
+    int32_t zigzag;             /* 1: odd lines run backwards                     */
+    int32_t upsample_q;         /* Q >= 1, fine-grid factor of the PSF stage      */
+} mpi_ffl_trajectory;
+
+/* Langevin-derivative PSF width (Appendix B, Eq. (31)). */
+typedef struct {
+    double fwhm_vox; /* > 0 */
+} mpi_ffl_psf;
+
+/* Kept harmonic bands (Sec. 2.1, Eqs. (11), (13)). Requires k_min*P - half_width >= 1
+ * and k_max*P + half_width < L/2. */
+typedef struct {
+    int32_t k_min, k_max, half_width;
+    const float *d_gamma_ri; /* host, n_bins complex (re, im) or NULL = identity */
+} mpi_ffl_harmonics;
+
+/* Solver settings (Sec. 3.3, Eq. (26)). */
+typedef struct {
+    int32_t iters;     /* K >= 0 iterations                                            */
+    double lambda;     /* < 0 -> 1e-3 * ||A^T A|| / ||T^T T||                          */
+    double tau;        /* > 0 used as given; <= 0 -> 1 / (||A^T A|| + lambda ||T^T T||) */
+    int32_t n_power;   /* power iterations for ||A^T A|| when it is needed (e.g. 50)   */
+    uint64_t seed;     /* SplitMix64 seed of the power-iteration start vector          */
+    int32_t nonneg;    /* 1: project each update onto x >= 0                           */
+    double stop_rel;   /* > 0: stop when |r_k - r_{k-1}| <= stop_rel r_{k-1}          */
+    double ata_norm;   /* > 0: use as ||A^T A|| and skip the power iteration           */
+} mpi_ffl_solve_params;
+
+typedef struct {
+    int32_t iters_done;
+    double tau, lambda, ata_norm;
+    double residual_first; /* ||A y - b|| at the first iteration (FP64) */
+    double residual_last;  /* ||A y - b|| at the last iteration  (FP64) */
+    double b_norm;         /* ||b||                                     */
+} mpi_ffl_solve_report;
+
+/* Sizes of a problem, in elements. */
+typedef struct {
+    int64_t n_vox;   /* nz*ny*nx floats of a volume                       */
+    int64_t n_data;  /* 2 * M * nz * n_bins floats of the data             */
+    int64_t n_proj;  /* M * nz * nx floats of the projections              */
+    int64_t n_fine;  /* M * nz * N_e floats of the PSF-convolved rows      */
+    int64_t n_sig;   /* M * nz * L floats of the time signal               */
+    int32_t n_bins;  /* (k_max - k_min + 1) * (2 half_width + 1)           */
+    int32_t fine_len;/* N_e = (nx-1) Q + 2 ceil(A Q) + 1                  */
+    int32_t line_len;/* L = S P                                           */
+    int64_t workspace_bytes; /* device memory the handle holds            */
+} mpi_ffl_sizes;
+
+/* Create a handle on the current CUDA device: validates the description, builds the
+ * PSF, trajectory and DFT tables in double precision on the host and uploads them,
+ * and allocates the workspace. Returns MPI_FFL_ERR_INVALID_ARG for an invalid
+ * description (nx != ny, band outside 1 <= omega < L/2, ...), MPI_FFL_ERR_OOM when a
+ * device allocation fails (nothing is leaked), MPI_FFL_ERR_CUDA otherwise. */
+int mpi_ffl_create(const mpi_ffl_geometry *geom, const mpi_ffl_trajectory *traj,
+                   const mpi_ffl_psf *psf, const mpi_ffl_harmonics *harm,
+                   mpi_ffl_handle **out);
+
+/* Release the handle and everything it owns. destroy(NULL) returns 0. Waits for the
+ * device to finish work that uses the handle's memory. */
+int mpi_ffl_destroy(mpi_ffl_handle *h);
+
+/* Message of the last failure of h (NULL: of the last create on this thread). */
+const char *mpi_ffl_last_error(const mpi_ffl_handle *h);
+
+int mpi_ffl_get_sizes(const mpi_ffl_handle *h, mpi_ffl_sizes *out);
+
+/* Arithmetic of the DFT stage for forward/adjoint/solve (MPI_FFL_PREC_*). */
+int mpi_ffl_set_precision(mpi_ffl_handle *h, int32_t precision);
+
+/* Replace the per-angle gains (host array of n_angles) or the PSF width. Both take
+ * effect for work enqueued after the call returns; the call synchronises the device
+ * before touching tables that queued work may still read. */
+int mpi_ffl_set_gain(mpi_ffl_handle *h, const float *gain);
+int mpi_ffl_set_psf_fwhm(mpi_ffl_handle *h, double fwhm_vox);
+
+/* b = A x (Sec. 2.2, Eq. (23)). d_x: n_vox floats; d_b_ri: n_data floats (written). */
+int mpi_ffl_forward(mpi_ffl_handle *h, const float *d_x, float *d_b_ri, void *stream);
+
+/* x = A^T b = Re(A^H b) (transpose of Eq. (23) under the real inner product). */
+int mpi_ffl_adjoint(mpi_ffl_handle *h, const float *d_b_ri, float *d_x, void *stream);
+
+/* One stage of A or of A^T on caller buffers, for stage-by-stage checks:
+ *   stage 0 = P   (n_vox  <-> n_proj)      stage 1 = H (n_proj <-> n_fine)
+ *   stage 2 = EVB (n_fine <-> n_sig)       stage 3 = S D_Gamma F (n_sig <-> n_data)
+ * transpose = 0 applies the stage, 1 its transpose. Stage 3 uses the precision set by
+ * mpi_ffl_set_precision only when it is FP32; the tensor-core precisions are used
+ * by forward/adjoint, where the DFT is fused with E V B. */
+int mpi_ffl_apply_stage(mpi_ffl_handle *h, int32_t stage, int32_t transpose,
+                        const float *d_in, float *d_out, void *stream);
+
+/* Gradients for calibration (the scan nonidealities of Sec. 1): given x and the
+ * gradient g_b of a loss with respect to b = A x (n_data floats), writes
+ *   d_g_gain[m] = <g_b[m], A_m x> / gain_m  (= d loss / d gain_m), n_angles floats
+ *   d_g_fwhm[0] = <g_b, (d A / d fwhm) x>  (= d loss / d fwhm)
+ * with real inner products accumulated in FP64 and stored as FP32. Either output may
+ * be NULL. The gradient with respect to x is mpi_ffl_adjoint(g_b). */
+int mpi_ffl_param_grad(mpi_ffl_handle *h, const float *d_x, const float *d_gb_ri,
+                       float *d_g_gain, float *d_g_fwhm, void *stream);
+
+/* T^T T x (Sec. 3.3, Eq. (25)) on a volume. */
+int mpi_ffl_apply_ttt(mpi_ffl_handle *h, const float *d_x, float *d_out, void *stream);
+
+/* ||A^T A||_2 by n_iter power iterations from a SplitMix64(seed) start vector (the
+ * Rayleigh quotient of the last iterate, FP64). Synchronises the stream. */
+int mpi_ffl_power_norm(mpi_ffl_handle *h, int32_t n_iter, uint64_t seed, double *out, void *stream);
+
+/* Reconstruct: runs Eq. (26) from x0 = d_x_inout, writes the result to d_x_inout.
+ * d_b_ri: n_data floats. Residual norms are reduced in FP64 on the device. If report
+ * is non-NULL the call synchronises the stream and fills it; otherwise it returns as
+ * soon as the work is enqueued (unless the power iteration or stop_rel needs a value
+ * on the host). Returns MPI_FFL_ERR_NONFINITE if a residual norm is not finite. */
+int mpi_ffl_solve(mpi_ffl_handle *h, const float *d_b_ri, float *d_x_inout,
+                  const mpi_ffl_solve_params *params, mpi_ffl_solve_report *report,
+                  void *stream);
+
+/* ---- Measurement hooks (not part of the method) ----------------------------------
+ * Kernel kinds for the per-kernel timers below. */
+#define MPI_FFL_K_TRANSPOSE 0     /* volume x/y transpose for column-marched angles */
+#define MPI_FFL_K_PROJECT 1       /* P                                              */
+#define MPI_FFL_K_BACKPROJECT 2   /* P^T                                            */
+#define MPI_FFL_K_PSF_FWD 3       /* H                                              */
+#define MPI_FFL_K_PSF_ADJ 4       /* H^T                                            */
+#define MPI_FFL_K_RESAMPLE_FWD 5  /* E V B (staged)                                 */
+#define MPI_FFL_K_RESAMPLE_ADJ 6  /* (E V B)^T (staged)                             */
+#define MPI_FFL_K_DFT_FWD 7       /* S D_Gamma F (staged, FP32)                     */
+#define MPI_FFL_K_DFT_ADJ 8       /* its transpose (staged, FP32)                   */
+#define MPI_FFL_K_TC_FWD 9        /* E V B fused with S D_Gamma F (tensor cores)    */
+#define MPI_FFL_K_TC_ADJ 10       /* its transpose (tensor cores)                   */
+#define MPI_FFL_K_SOLVER 11       /* momentum, residual, update and reductions      */
+#define MPI_FFL_N_KERNEL_KINDS 12
+
+/* enable != 0: record a CUDA event pair around every kernel the handle launches (on
+ * the launching stream) until disabled; enable == 0 stops recording. */
+int mpi_ffl_profile_enable(mpi_ffl_handle *h, int32_t enable);
+
+/* Waits for the recorded events, then writes per kind (MPI_FFL_N_KERNEL_KINDS entries
+ * each) the summed kernel time in ms and the number of timed launches, and clears the
+ * record. */
+int mpi_ffl_profile_read(mpi_ffl_handle *h, double *ms, int64_t *launches);
+
+/* Total kernel launches issued by the handle since create (always counted). */
+int64_t mpi_ffl_launch_count(const mpi_ffl_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MPI_FFL_H */

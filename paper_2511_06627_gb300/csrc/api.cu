@@ -1,0 +1,818 @@
+// C ABI of the library (include/mpi_ffl.h): handle life cycle, the host-side
+// tables (computed in double precision from the paper's formulas), and the
+// orchestration of the stage kernels into A, A^T and the solve of Eq. (26).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "internal.h"
+#include "tc.h"
+
+using namespace mpiffl;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+constexpr double kPi = 3.14159265358979323846;
+
+struct Fail {
+    int code;
+};
+
+#define CK(call)                                                                            \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess) {                                                            \
+            set_err(h, std::string(#call) + ": " + cudaGetErrorString(e_));                 \
+            throw Fail{e_ == cudaErrorMemoryAllocation ? MPI_FFL_ERR_OOM : MPI_FFL_ERR_CUDA}; \
+        }                                                                                   \
+    } while (0)
+
+void set_err(mpi_ffl_handle *h, const std::string &m) {
+    if (h) h->err = m;
+    else g_create_error = m;
+}
+
+void check_launch(mpi_ffl_handle *h, const char *what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_err(h, std::string(what) + ": " + cudaGetErrorString(e));
+        throw Fail{MPI_FFL_ERR_CUDA};
+    }
+}
+
+cudaEvent_t pool_event(mpi_ffl_handle *h) {
+    if (!h->ev_pool.empty()) {
+        cudaEvent_t e = h->ev_pool.back();
+        h->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Counts one kernel launch and, when profiling is on, brackets it with events.
+struct KTimer {
+    mpi_ffl_handle *h;
+    int kind;
+    cudaStream_t st;
+    cudaEvent_t a = nullptr;
+    KTimer(mpi_ffl_handle *h_, int kind_, cudaStream_t st_) : h(h_), kind(kind_), st(st_) {
+        h->launches++;
+        if (h->prof_on) {
+            a = pool_event(h);
+            cudaEventRecord(a, st);
+        }
+    }
+    ~KTimer() {
+        if (a) {
+            cudaEvent_t b = pool_event(h);
+            cudaEventRecord(b, st);
+            h->prof_rec.push_back(mpi_ffl_handle::ProfRec{kind, a, b});
+        }
+    }
+};
+
+#define TIMED(kind, call)                        \
+    do {                                         \
+        KTimer kt_(h, kind, st);                 \
+        call;                                    \
+    } while (0)
+
+template <class T>
+void dev_alloc(mpi_ffl_handle *h, T **p, size_t n) {
+    if (n == 0) n = 1;
+    cudaError_t e = cudaMalloc((void **)p, n * sizeof(T));
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        set_err(h, "cudaMalloc of " + std::to_string(n * sizeof(T)) + " bytes failed: " + cudaGetErrorString(e));
+        throw Fail{e == cudaErrorMemoryAllocation ? MPI_FFL_ERR_OOM : MPI_FFL_ERR_CUDA};
+    }
+    h->bytes += (int64_t)(n * sizeof(T));
+}
+
+template <class T>
+void upload(mpi_ffl_handle *h, T **p, const std::vector<T> &v) {
+    dev_alloc(h, p, v.size());
+    CK(cudaMemcpy(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+}
+
+// ------------------------------------------------------------ Langevin PSF
+// L'(x) = 1/x^2 - 1/sinh(x)^2 (Appendix B, Eq. (31) collinear term), with the
+// Taylor series 1/3 - x^2/15 + 2x^4/189 - x^6/675 for |x| < 0.05.
+double langevin_d1(double x) {
+    const double ax = std::fabs(x);
+    if (ax < 0.05) {
+        const double x2 = x * x;
+        return 1.0 / 3.0 - x2 / 15.0 + 2.0 * x2 * x2 / 189.0 - x2 * x2 * x2 / 675.0;
+    }
+    if (ax > 350.0) return 1.0 / (x * x);
+    const double sh = std::sinh(ax);
+    return 1.0 / (ax * ax) - 1.0 / (sh * sh);
+}
+
+// L''(x) = -2/x^3 + 2 cosh(x)/sinh(x)^3, series -2x/15 + 8x^3/189 - 6x^5/675.
+double langevin_d2(double x) {
+    const double ax = std::fabs(x);
+    if (ax < 0.05) return -2.0 * x / 15.0 + 8.0 * x * x * x / 189.0 - 6.0 * std::pow(x, 5) / 675.0;
+    if (ax > 350.0) return -2.0 / (x * x * x);
+    const double sh = std::sinh(x);
+    return -2.0 / (x * x * x) + 2.0 * std::cosh(x) / (sh * sh * sh);
+}
+
+// x_h with L'(x_h) = L'(0)/2 = 1/6, by bisection (L' decreases on x > 0).
+double langevin_half_point() {
+    double lo = 0.5, hi = 5.0;
+    for (int it = 0; it < 200; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (langevin_d1(mid) > 1.0 / 6.0) lo = mid;
+        else hi = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+void psf_tables(const Dims &d, double fwhm, std::vector<float> &h, std::vector<float> &dh) {
+    const double a = fwhm / (2.0 * langevin_half_point());
+    h.resize(d.htab_len);
+    dh.resize(d.htab_len);
+    for (int k = 0; k < d.htab_len; ++k) {
+        const double u = (double)(k - d.htab_off) / d.Q;
+        const double x = u / a;
+        h[k] = (float)(3.0 * langevin_d1(x));
+        // d/dfwhm of 3 L'(u/a), a = fwhm / (2 x_h): -3 L''(x) x / fwhm
+        dh[k] = (float)(-3.0 * langevin_d2(x) * x / fwhm);
+    }
+}
+
+// ------------------------------------------------------------ validation
+int compute_dims(const mpi_ffl_geometry *g, const mpi_ffl_trajectory *t, const mpi_ffl_harmonics *hm,
+                 Dims &d, std::string &why) {
+    if (!g || !t || !hm) { why = "NULL description"; return MPI_FFL_ERR_INVALID_ARG; }
+    if (g->nx != g->ny) { why = "nx must equal ny"; return MPI_FFL_ERR_INVALID_ARG; }
+    if (g->nx < 2 || g->nz < 1 || g->n_angles < 1) { why = "bad volume or angle count"; return MPI_FFL_ERR_INVALID_ARG; }
+    if (t->samples_per_period < 2 || t->periods_per_line < 1 || t->upsample_q < 1 || !(t->drive_amp_vox >= 0.0)) {
+        why = "bad trajectory";
+        return MPI_FFL_ERR_INVALID_ARG;
+    }
+    if (hm->half_width < 0 || hm->half_width > kMaxHw || hm->k_min < 0 || hm->k_max < hm->k_min) {
+        why = "bad harmonic band (half_width must be 0..8)";
+        return MPI_FFL_ERR_INVALID_ARG;
+    }
+    d.N = g->nx;
+    d.Nz = g->nz;
+    d.M = g->n_angles;
+    d.S = t->samples_per_period;
+    d.P = t->periods_per_line;
+    const int64_t L = (int64_t)d.S * d.P;
+    if (L < 2 || L > (1 << 28)) { why = "line length out of range"; return MPI_FFL_ERR_INVALID_ARG; }
+    d.L = (int)L;
+    d.Q = t->upsample_q;
+    d.D = (int)std::ceil(t->drive_amp_vox * d.Q - 1e-9);
+    d.Ne = (d.N - 1) * d.Q + 2 * d.D + 1;
+    d.K = hm->k_max - hm->k_min + 1;
+    d.hw = hm->half_width;
+    d.W = 2 * d.hw + 1;
+    d.nb = d.K * d.W;
+    d.kmin = hm->k_min;
+    if ((int64_t)hm->k_min * d.P - d.hw < 1 || (int64_t)hm->k_max * d.P + d.hw >= L / 2) {
+        why = "harmonic band must satisfy 1 <= k*P + delta < L/2";
+        return MPI_FFL_ERR_INVALID_ARG;
+    }
+    if (d.S > 1024 * 8) { why = "samples_per_period too large"; return MPI_FFL_ERR_INVALID_ARG; }
+    d.nseg = d.M * d.Nz;
+    d.nvox = (int64_t)d.Nz * d.N * d.N;
+    d.nproj = (int64_t)d.nseg * d.N;
+    d.nfine = (int64_t)d.nseg * d.Ne;
+    d.nsig = (int64_t)d.nseg * d.L;
+    d.ndata = (int64_t)2 * d.nseg * d.nb;
+    d.htab_off = (d.N - 1) * d.Q + d.D + d.Q * kPsfT;
+    d.htab_len = 2 * d.htab_off + 1;
+    d.n_par = t->zigzag ? 2 : 1;
+    // shared memory of the staged kernels
+    if ((size_t)(d.htab_len + 4 * (size_t)d.Ne) * 4 > 220 * 1024 || (size_t)d.P * d.W * 4 + (size_t)d.S * d.W * 8 > 220 * 1024) {
+        why = "problem too large for the staged kernels' shared memory";
+        return MPI_FFL_ERR_UNSUPPORTED;
+    }
+    return 0;
+}
+
+void angle_table(mpi_ffl_handle *h) {
+    const Dims &d = h->d;
+    std::vector<AngleParam> a(d.M);
+    for (int m = 0; m < d.M; ++m) {
+        const double th = h->angles[m];
+        const double c = std::cos(th), s = std::sin(th);
+        if (std::fabs(c) >= std::fabs(s) - 1e-9) {
+            a[m] = AngleParam{(float)(1.0 / c), (float)(s / c), (float)(1.0 / std::fabs(c)), 1};
+        } else {
+            a[m] = AngleParam{(float)(-1.0 / s), (float)(c / s), (float)(1.0 / std::fabs(s)), 0};
+        }
+    }
+    upload(h, &h->t_ang, a);
+}
+
+void trajectory_tables(mpi_ffl_handle *h) {
+    const Dims &d = h->d;
+    std::vector<TrajEntry> tr((size_t)d.n_par * d.L);
+    std::vector<int> ptr((size_t)d.n_par * (d.Ne + 1), 0);
+    std::vector<CsrEntry> csr((size_t)d.n_par * 2 * d.L);
+    const double slope = (double)(d.N - 1) / (double)(d.L - 1);
+    for (int par = 0; par < d.n_par; ++par) {
+        TrajEntry *T = tr.data() + (size_t)par * d.L;
+        for (int j = 0; j < d.L; ++j) {
+            const double slow = par ? (d.N - 1) - slope * j : slope * j;
+            const double dslow = par ? -slope : slope;
+            const double ph = 2.0 * kPi * (double)(j % d.S) / d.S + h->phase;
+            const double xi = slow + h->amp * std::sin(ph);
+            const double v = dslow + h->amp * (2.0 * kPi / d.S) * std::cos(ph);
+            const double tt = d.Q * xi + d.D;
+            int n = (int)std::floor(tt);
+            if (n > d.Ne - 2) n = d.Ne - 2;
+            if (n < 0 || tt > d.Ne - 1 + 1e-9) {
+                set_err(h, "trajectory leaves the fine grid");
+                throw Fail{MPI_FFL_ERR_INVALID_ARG};
+            }
+            const double f = tt - n;
+            T[j] = TrajEntry{n, (float)((1.0 - f) * v), (float)(f * v)};
+        }
+        // CSR of the transpose: cell n_j <- (j, w0), cell n_j + 1 <- (j, w1), j ascending
+        int *P = ptr.data() + (size_t)par * (d.Ne + 1);
+        for (int j = 0; j < d.L; ++j) {
+            P[T[j].n + 1]++;
+            P[T[j].n + 2]++;
+        }
+        for (int e = 0; e < d.Ne; ++e) P[e + 1] += P[e];
+        std::vector<int> fill(P, P + d.Ne);
+        CsrEntry *C = csr.data() + (size_t)par * 2 * d.L;
+        for (int e = 0; e < d.Ne; ++e) fill[e] = P[e];
+        // two passes keep entries of a cell in ascending j
+        for (int j = 0; j < d.L; ++j) {
+            C[fill[T[j].n]++] = CsrEntry{j, T[j].w0};
+            C[fill[T[j].n + 1]++] = CsrEntry{j, T[j].w1};
+        }
+    }
+    upload(h, &h->t_traj, tr);
+    upload(h, &h->t_csr_ptr, ptr);
+    upload(h, &h->t_csr, csr);
+}
+
+void dft_tables(mpi_ffl_handle *h) {
+    const Dims &d = h->d;
+    std::vector<float> tw1((size_t)d.P * d.W);
+    for (int p = 0; p < d.P; ++p) {
+        for (int k = 0; k <= d.hw; ++k) {
+            const double ang = 2.0 * kPi * (double)(((int64_t)k * p) % d.P) / d.P;
+            tw1[(size_t)p * d.W + k] = (float)std::cos(ang);
+            if (k > 0) tw1[(size_t)p * d.W + d.hw + k] = (float)std::sin(ang);
+        }
+    }
+    std::vector<float2> ro((size_t)d.S * d.nb), qr((size_t)d.nb * d.S);
+    for (int o = 0; o < d.nb; ++o) {
+        const int64_t w = (int64_t)(d.kmin + o / d.W) * d.P + (o % d.W - d.hw);
+        for (int r = 0; r < d.S; ++r) {
+            const double ang = 2.0 * kPi * (double)((w * r) % d.L) / d.L;
+            const float2 v = make_float2((float)std::cos(ang), (float)std::sin(ang));
+            ro[(size_t)r * d.nb + o] = v;
+            qr[(size_t)o * d.S + r] = v;
+        }
+    }
+    upload(h, &h->t_tw1, tw1);
+    upload(h, &h->t_tw2_ro, ro);
+    upload(h, &h->t_tw2_qr, qr);
+    std::vector<float2> dg(d.nb);
+    for (int o = 0; o < d.nb; ++o) dg[o] = make_float2(h->dgamma[2 * o], h->dgamma[2 * o + 1]);
+    upload(h, &h->t_dgam, dg);
+}
+
+void group_table(mpi_ffl_handle *h) {
+    const Dims &d = h->d;
+    std::vector<SegGroup> g;
+    for (int m = 0; m < d.M; ++m) {
+        for (int par = 0; par < d.n_par; ++par) {
+            const int stride = d.n_par;
+            for (int z0 = par; z0 < d.Nz; z0 += stride * kGroup) {
+                const int cnt = std::min(kGroup, (d.Nz - z0 + stride - 1) / stride);
+                g.push_back(SegGroup{m, par, z0, stride, cnt});
+            }
+        }
+    }
+    h->n_groups = (int)g.size();
+    upload(h, &h->t_groups, g);
+}
+
+void release(mpi_ffl_handle *h) {
+    void *ptrs[] = {h->t_ang, h->t_gain, h->t_unit_gain, h->t_htab, h->t_dhtab, h->t_traj, h->t_csr_ptr,
+                    h->t_csr, h->t_tw1, h->t_tw2_ro, h->t_tw2_qr, h->t_dgam, h->t_groups, h->w_volT,
+                    h->w_proj, h->w_fine, h->w_sig, h->w_data, h->w_vol2, h->w_red, h->w_scal,
+                    h->s_xp, h->s_y, h->s_g, h->s_r, h->s_hist, h->s_flags, h->tc_twb};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    for (auto &r : h->prof_rec) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (auto e : h->ev_pool) cudaEventDestroy(e);
+    tc_release(h);
+}
+
+cudaStream_t S(void *s) { return (cudaStream_t)s; }
+
+bool any_column_angle(const mpi_ffl_handle *h) {
+    for (double th : h->angles)
+        if (!(std::fabs(std::cos(th)) >= std::fabs(std::sin(th)) - 1e-9)) return true;
+    return false;
+}
+
+void ensure_sig(mpi_ffl_handle *h) {
+    if (!h->w_sig) dev_alloc(h, &h->w_sig, h->d.nsig);
+}
+
+// ------------------------------------------------------------ stages
+void stage_p(mpi_ffl_handle *h, const float *x, float *proj, cudaStream_t st) {
+    if (any_column_angle(h)) TIMED(MPI_FFL_K_TRANSPOSE, launch_transpose_xy(x, h->w_volT, h->d.N, h->d.Nz, st));
+    TIMED(MPI_FFL_K_PROJECT, launch_project(x, h->w_volT, h->t_ang, proj, h->d.N, h->d.Nz, h->d.M, st));
+    check_launch(h, "project");
+}
+
+void stage_pt(mpi_ffl_handle *h, const float *proj, float *x, cudaStream_t st) {
+    TIMED(MPI_FFL_K_BACKPROJECT, launch_backproject(proj, h->t_ang, x, h->d.N, h->d.Nz, h->d.M, st));
+    check_launch(h, "backproject");
+}
+
+void forward_impl(mpi_ffl_handle *h, const float *x, float *b, const float *htab, const float *gain,
+                  cudaStream_t st) {
+    const Dims &d = h->d;
+    stage_p(h, x, h->w_proj, st);
+    TIMED(MPI_FFL_K_PSF_FWD, launch_psf_fwd(h->w_proj, htab, h->w_fine, d, st));
+    check_launch(h, "psf_fwd");
+    if (h->precision != MPI_FFL_PREC_FP32 && tc_supported(h)) {
+        TIMED(MPI_FFL_K_TC_FWD, tc_forward_line(h, h->w_fine, gain, b, st));
+        check_launch(h, "tc_forward");
+        return;
+    }
+    ensure_sig(h);
+    TIMED(MPI_FFL_K_RESAMPLE_FWD, launch_resample_fwd(h->w_fine, h->t_traj, gain, h->t_groups, h->n_groups, h->w_sig, d, st));
+    check_launch(h, "resample_fwd");
+    TIMED(MPI_FFL_K_DFT_FWD, launch_dft_fwd(h->w_sig, h->t_tw1, h->t_tw2_ro, h->t_dgam, b, d, st));
+    check_launch(h, "dft_fwd");
+}
+
+void adjoint_impl(mpi_ffl_handle *h, const float *b, float *x, cudaStream_t st) {
+    const Dims &d = h->d;
+    if (h->precision != MPI_FFL_PREC_FP32 && tc_supported(h)) {
+        TIMED(MPI_FFL_K_TC_ADJ, tc_adjoint_line(h, b, h->t_gain, h->w_fine, st));
+        check_launch(h, "tc_adjoint");
+    } else {
+        ensure_sig(h);
+        TIMED(MPI_FFL_K_DFT_ADJ, launch_dft_adj(b, h->t_tw1, h->t_tw2_qr, h->t_dgam, h->w_sig, d, st));
+        check_launch(h, "dft_adj");
+        TIMED(MPI_FFL_K_RESAMPLE_ADJ, launch_resample_adj(h->w_sig, h->t_csr_ptr, h->t_csr, h->t_gain, h->t_groups, h->n_groups, h->w_fine, d, st));
+        check_launch(h, "resample_adj");
+    }
+    TIMED(MPI_FFL_K_PSF_ADJ, launch_psf_adj(h->w_fine, h->t_htab, h->w_proj, d, st));
+    check_launch(h, "psf_adj");
+    stage_pt(h, h->w_proj, x, st);
+}
+
+double dot_sync(mpi_ffl_handle *h, const float *a, const float *b, int64_t n, cudaStream_t st) {
+    const int nb = reduce_blocks(n);
+    TIMED(MPI_FFL_K_SOLVER, launch_dot(a, b, n, h->w_red, nb, st));
+    TIMED(MPI_FFL_K_SOLVER, launch_finalize(h->w_red, nb, h->w_scal + 7, st));
+    check_launch(h, "dot");
+    double v = 0;
+    CK(cudaMemcpyAsync(&v, h->w_scal + 7, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return v;
+}
+
+double power_norm_impl(mpi_ffl_handle *h, int n_iter, uint64_t seed, cudaStream_t st) {
+    const Dims &d = h->d;
+    float *v = h->w_vol2, *w = h->s_g;
+    const int nbv = reduce_blocks(d.nvox);
+    TIMED(MPI_FFL_K_SOLVER, launch_splitmix_fill(v, d.nvox, seed, st));
+    TIMED(MPI_FFL_K_SOLVER, launch_dot(v, v, d.nvox, h->w_red, nbv, st));
+    TIMED(MPI_FFL_K_SOLVER, launch_finalize(h->w_red, nbv, h->w_scal + 0, st));
+    TIMED(MPI_FFL_K_SOLVER, launch_scale_by_rsqrt(v, v, d.nvox, h->w_scal + 0, st));
+    check_launch(h, "power init");
+    for (int it = 0; it < n_iter; ++it) {
+        forward_impl(h, v, h->w_data, h->t_htab, h->t_gain, st);
+        adjoint_impl(h, h->w_data, w, st);
+        TIMED(MPI_FFL_K_SOLVER, launch_dot(v, w, d.nvox, h->w_red, nbv, st));
+        TIMED(MPI_FFL_K_SOLVER, launch_finalize(h->w_red, nbv, h->w_scal + 1, st));
+        TIMED(MPI_FFL_K_SOLVER, launch_dot(w, w, d.nvox, h->w_red, nbv, st));
+        TIMED(MPI_FFL_K_SOLVER, launch_finalize(h->w_red, nbv, h->w_scal + 0, st));
+        TIMED(MPI_FFL_K_SOLVER, launch_scale_by_rsqrt(w, v, d.nvox, h->w_scal + 0, st));
+        check_launch(h, "power step");
+    }
+    double mu = 0;
+    CK(cudaMemcpyAsync(&mu, h->w_scal + 1, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return mu;
+}
+
+double ttt_norm(const Dims &d) {
+    double s = 0;
+    const int ns[3] = {d.Nz, d.N, d.N};
+    for (int n : ns) {
+        const double v = std::sin(kPi * (n - 1) / (2.0 * n));
+        s += 4.0 * v * v;
+    }
+    return s;
+}
+
+template <class F>
+int guarded(mpi_ffl_handle *h, F &&f) {
+    if (!h) return MPI_FFL_ERR_INVALID_ARG;
+    try {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (dev != h->device) cudaSetDevice(h->device);
+        return f();
+    } catch (const Fail &e) {
+        return e.code;
+    } catch (const std::bad_alloc &) {
+        h->err = "host allocation failed";
+        return MPI_FFL_ERR_OOM;
+    } catch (...) {
+        h->err = "unexpected exception";
+        return MPI_FFL_ERR_CUDA;
+    }
+}
+
+}  // namespace
+
+// ============================================================ C ABI
+
+extern "C" int mpi_ffl_create(const mpi_ffl_geometry *geom, const mpi_ffl_trajectory *traj,
+                              const mpi_ffl_psf *psf, const mpi_ffl_harmonics *harm,
+                              mpi_ffl_handle **out) {
+    g_create_error.clear();
+    if (!out) {
+        g_create_error = "out is NULL";
+        return MPI_FFL_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    Dims d{};
+    std::string why;
+    int rc = compute_dims(geom, traj, harm, d, why);
+    if (rc) {
+        g_create_error = why;
+        return rc;
+    }
+    if (!psf || !(psf->fwhm_vox > 0.0)) {
+        g_create_error = "fwhm_vox must be > 0";
+        return MPI_FFL_ERR_INVALID_ARG;
+    }
+    mpi_ffl_handle *h = new (std::nothrow) mpi_ffl_handle();
+    if (!h) {
+        g_create_error = "host allocation failed";
+        return MPI_FFL_ERR_OOM;
+    }
+    h->d = d;
+    try {
+        CK(cudaGetDevice(&h->device));
+        h->angles.resize(d.M);
+        h->gains.resize(d.M);
+        for (int m = 0; m < d.M; ++m) {
+            h->angles[m] = geom->angles_rad ? geom->angles_rad[m] : m * kPi / d.M;
+            h->gains[m] = geom->gain ? geom->gain[m] : 1.0f;
+            if (!std::isfinite(h->angles[m]) || !std::isfinite(h->gains[m])) {
+                set_err(nullptr, "non-finite angle or gain");
+                throw Fail{MPI_FFL_ERR_INVALID_ARG};
+            }
+        }
+        h->fwhm = psf->fwhm_vox;
+        h->amp = traj->drive_amp_vox;
+        h->phase = traj->drive_phase;
+        h->zigzag = traj->zigzag ? 1 : 0;
+        h->dgamma.assign(2 * d.nb, 0.f);
+        for (int o = 0; o < d.nb; ++o) {
+            h->dgamma[2 * o] = harm->d_gamma_ri ? harm->d_gamma_ri[2 * o] : 1.f;
+            h->dgamma[2 * o + 1] = harm->d_gamma_ri ? harm->d_gamma_ri[2 * o + 1] : 0.f;
+        }
+        angle_table(h);
+        upload(h, &h->t_gain, h->gains);
+        upload(h, &h->t_unit_gain, std::vector<float>(d.M, 1.f));
+        std::vector<float> ht, dht;
+        psf_tables(d, h->fwhm, ht, dht);
+        upload(h, &h->t_htab, ht);
+        upload(h, &h->t_dhtab, dht);
+        trajectory_tables(h);
+        dft_tables(h);
+        group_table(h);
+        dev_alloc(h, &h->w_volT, d.nvox);
+        dev_alloc(h, &h->w_proj, d.nproj);
+        dev_alloc(h, &h->w_fine, d.nfine);
+        dev_alloc(h, &h->w_data, d.ndata);
+        dev_alloc(h, &h->w_vol2, d.nvox);
+        h->w_red_len = std::max(reduce_blocks(std::max(d.nvox, d.ndata)) + 16, 1024 * std::max(d.M, 1));
+        dev_alloc(h, &h->w_red, (size_t)h->w_red_len);
+        dev_alloc(h, &h->w_scal, 16);
+        dev_alloc(h, &h->s_xp, d.nvox);
+        dev_alloc(h, &h->s_y, d.nvox);
+        dev_alloc(h, &h->s_g, d.nvox);
+        dev_alloc(h, &h->s_r, d.ndata);
+        dev_alloc(h, &h->s_flags, 4);
+        tc_init(h);
+        CK(cudaDeviceSynchronize());
+    } catch (const Fail &e) {
+        if (g_create_error.empty()) g_create_error = h->err.empty() ? "create failed" : h->err;
+        release(h);
+        delete h;
+        return e.code;
+    } catch (...) {
+        g_create_error = "create failed (host exception)";
+        release(h);
+        delete h;
+        return MPI_FFL_ERR_OOM;
+    }
+    *out = h;
+    return MPI_FFL_OK;
+}
+
+extern "C" int mpi_ffl_destroy(mpi_ffl_handle *h) {
+    if (!h) return MPI_FFL_OK;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev != h->device) cudaSetDevice(h->device);
+    const int own = h->device;
+    cudaDeviceSynchronize();
+    release(h);
+    delete h;
+    if (dev != own) cudaSetDevice(dev);
+    return MPI_FFL_OK;
+}
+
+extern "C" const char *mpi_ffl_last_error(const mpi_ffl_handle *h) {
+    return h ? h->err.c_str() : g_create_error.c_str();
+}
+
+extern "C" int mpi_ffl_get_sizes(const mpi_ffl_handle *h, mpi_ffl_sizes *o) {
+    if (!h || !o) return MPI_FFL_ERR_INVALID_ARG;
+    o->n_vox = h->d.nvox;
+    o->n_data = h->d.ndata;
+    o->n_proj = h->d.nproj;
+    o->n_fine = h->d.nfine;
+    o->n_sig = h->d.nsig;
+    o->n_bins = h->d.nb;
+    o->fine_len = h->d.Ne;
+    o->line_len = h->d.L;
+    o->workspace_bytes = h->bytes;
+    return MPI_FFL_OK;
+}
+
+extern "C" int mpi_ffl_set_precision(mpi_ffl_handle *h, int32_t precision) {
+    if (!h) return MPI_FFL_ERR_INVALID_ARG;
+    if (precision < MPI_FFL_PREC_FP32 || precision > MPI_FFL_PREC_TF32) {
+        h->err = "unknown precision";
+        return MPI_FFL_ERR_INVALID_ARG;
+    }
+    if (precision != MPI_FFL_PREC_FP32 && !tc_supported(h)) {
+        h->err = "tensor-core path does not support this problem shape";
+        return MPI_FFL_ERR_UNSUPPORTED;
+    }
+    h->precision = precision;
+    return MPI_FFL_OK;
+}
+
+extern "C" int mpi_ffl_set_gain(mpi_ffl_handle *h, const float *gain) {
+    return guarded(h, [&]() {
+        if (!gain) {
+            h->err = "gain is NULL";
+            return MPI_FFL_ERR_INVALID_ARG;
+        }
+        for (int m = 0; m < h->d.M; ++m) h->gains[m] = gain[m];
+        CK(cudaDeviceSynchronize());
+        CK(cudaMemcpy(h->t_gain, h->gains.data(), sizeof(float) * h->d.M, cudaMemcpyHostToDevice));
+        return MPI_FFL_OK;
+    });
+}
+
+extern "C" int mpi_ffl_set_psf_fwhm(mpi_ffl_handle *h, double fwhm) {
+    return guarded(h, [&]() {
+        if (!(fwhm > 0.0)) {
+            h->err = "fwhm must be > 0";
+            return MPI_FFL_ERR_INVALID_ARG;
+        }
+        h->fwhm = fwhm;
+        std::vector<float> ht, dht;
+        psf_tables(h->d, fwhm, ht, dht);
+        CK(cudaDeviceSynchronize());
+        CK(cudaMemcpy(h->t_htab, ht.data(), sizeof(float) * ht.size(), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(h->t_dhtab, dht.data(), sizeof(float) * dht.size(), cudaMemcpyHostToDevice));
+        tc_tables_changed(h);
+        return MPI_FFL_OK;
+    });
+}
+
+extern "C" int mpi_ffl_forward(mpi_ffl_handle *h, const float *d_x, float *d_b, void *stream) {
+    return guarded(h, [&]() {
+        if (!d_x || !d_b) {
+            h->err = "NULL buffer";
+            return MPI_FFL_ERR_INVALID_ARG;
+        }
+        forward_impl(h, d_x, d_b, h->t_htab, h->t_gain, S(stream));
+        return MPI_FFL_OK;
+    });
+}
+
+extern "C" int mpi_ffl_adjoint(mpi_ffl_handle *h, const float *d_b, float *d_x, void *stream) {
+    return guarded(h, [&]() {
+        if (!d_x || !d_b) {
+            h->err = "NULL buffer";
+            return MPI_FFL_ERR_INVALID_ARG;
+        }
+        adjoint_impl(h, d_b, d_x, S(stream));
+        return MPI_FFL_OK;
+    });
+}
+
+extern "C" int mpi_ffl_apply_stage(mpi_ffl_handle *h, int32_t stage, int32_t transpose, const float *in,
+                                   float *out, void *stream) {
+    return guarded(h, [&]() {
+        if (!in || !out || stage < 0 || stage > 3) {
+            h->err = "bad stage or NULL buffer";
+            return MPI_FFL_ERR_INVALID_ARG;
+        }
+        const Dims &d = h->d;
+        cudaStream_t st = S(stream);
+        switch (stage * 2 + (transpose ? 1 : 0)) {
+            case 0: stage_p(h, in, out, st); break;
+            case 1: stage_pt(h, in, out, st); break;
+            case 2: TIMED(MPI_FFL_K_PSF_FWD, launch_psf_fwd(in, h->t_htab, out, d, st)); break;
+            case 3: TIMED(MPI_FFL_K_PSF_ADJ, launch_psf_adj(in, h->t_htab, out, d, st)); break;
+            case 4: TIMED(MPI_FFL_K_RESAMPLE_FWD, launch_resample_fwd(in, h->t_traj, h->t_gain, h->t_groups, h->n_groups, out, d, st)); break;
+            case 5: TIMED(MPI_FFL_K_RESAMPLE_ADJ, launch_resample_adj(in, h->t_csr_ptr, h->t_csr, h->t_gain, h->t_groups, h->n_groups, out, d, st)); break;
+            case 6: TIMED(MPI_FFL_K_DFT_FWD, launch_dft_fwd(in, h->t_tw1, h->t_tw2_ro, h->t_dgam, out, d, st)); break;
+            case 7: TIMED(MPI_FFL_K_DFT_ADJ, launch_dft_adj(in, h->t_tw1, h->t_tw2_qr, h->t_dgam, out, d, st)); break;
+        }
+        check_launch(h, "apply_stage");
+        return MPI_FFL_OK;
+    });
+}
+
+extern "C" int mpi_ffl_param_grad(mpi_ffl_handle *h, const float *d_x, const float *d_gb, float *d_g_gain,
+                                  float *d_g_fwhm, void *stream) {
+    return guarded(h, [&]() {
+        if (!d_x || !d_gb) {
+            h->err = "NULL buffer";
+            return MPI_FFL_ERR_INVALID_ARG;
+        }
+        const Dims &d = h->d;
+        cudaStream_t st = S(stream);
+        if (d_g_gain) {
+            // d loss / d g_m = <g_b[m], A_m x |_{g_m = 1}>
+            forward_impl(h, d_x, h->s_r, h->t_htab, h->t_unit_gain, st);
+            const int64_t per = (int64_t)2 * d.Nz * d.nb;
+            const int nbk = std::min(1024, std::max(1, (int)((per + 1023) / 1024)));
+            TIMED(MPI_FFL_K_SOLVER, launch_angle_dots(h->s_r, d_gb, d.M, per, h->w_red, nbk, st));
+            TIMED(MPI_FFL_K_SOLVER, launch_angle_finalize(h->w_red, d.M, nbk, d_g_gain, st));
+            check_launch(h, "gain grad");
+        }
+        if (d_g_fwhm) {
+            forward_impl(h, d_x, h->s_r, h->t_dhtab, h->t_gain, st);
+            const int nbk = reduce_blocks(d.ndata);
+            TIMED(MPI_FFL_K_SOLVER, launch_dot(h->s_r, d_gb, d.ndata, h->w_red, nbk, st));
+            TIMED(MPI_FFL_K_SOLVER, launch_finalize_to_float(h->w_red, nbk, d_g_fwhm, st));
+            check_launch(h, "fwhm grad");
+        }
+        return MPI_FFL_OK;
+    });
+}
+
+extern "C" int mpi_ffl_apply_ttt(mpi_ffl_handle *h, const float *d_x, float *d_out, void *stream) {
+    return guarded(h, [&]() {
+        if (!d_x || !d_out) {
+            h->err = "NULL buffer";
+            return MPI_FFL_ERR_INVALID_ARG;
+        }
+        cudaStream_t st = S(stream);
+        TIMED(MPI_FFL_K_SOLVER, launch_ttt(d_x, d_out, h->d.N, h->d.Nz, st));
+        check_launch(h, "ttt");
+        return MPI_FFL_OK;
+    });
+}
+
+extern "C" int mpi_ffl_power_norm(mpi_ffl_handle *h, int32_t n_iter, uint64_t seed, double *out, void *stream) {
+    return guarded(h, [&]() {
+        if (!out || n_iter < 1) {
+            h->err = "bad power-iteration arguments";
+            return MPI_FFL_ERR_INVALID_ARG;
+        }
+        *out = power_norm_impl(h, n_iter, seed, S(stream));
+        return MPI_FFL_OK;
+    });
+}
+
+extern "C" int mpi_ffl_solve(mpi_ffl_handle *h, const float *d_b, float *d_x, const mpi_ffl_solve_params *p,
+                             mpi_ffl_solve_report *rep, void *stream) {
+    return guarded(h, [&]() {
+        if (!d_b || !d_x || !p || p->iters < 0) {
+            h->err = "bad solve arguments";
+            return MPI_FFL_ERR_INVALID_ARG;
+        }
+        const Dims &d = h->d;
+        cudaStream_t st = S(stream);
+        const double tn = ttt_norm(d);
+        double ata = p->ata_norm;
+        if ((p->tau <= 0.0 || p->lambda < 0.0) && !(ata > 0.0)) {
+            ata = power_norm_impl(h, p->n_power > 0 ? p->n_power : 50, p->seed, st);
+        }
+        const double lam = p->lambda >= 0.0 ? p->lambda : 1e-3 * ata / tn;
+        const double tau = p->tau > 0.0 ? p->tau : 1.0 / (ata + lam * tn);
+        if (h->s_hist_len < p->iters + 1) {
+            if (h->s_hist) cudaFree(h->s_hist);
+            h->s_hist = nullptr;
+            dev_alloc(h, &h->s_hist, (size_t)p->iters + 1);
+            h->s_hist_len = p->iters + 1;
+        }
+        int *flags = h->s_flags;  // [0] stop flag, [1] iterations done
+        CK(cudaMemsetAsync(flags, 0, 4 * sizeof(int), st));
+        CK(cudaMemcpyAsync(h->s_xp, d_x, sizeof(float) * d.nvox, cudaMemcpyDeviceToDevice, st));
+        float *xc = d_x, *xp = h->s_xp;
+        const int nbd = reduce_blocks(d.ndata);
+        int done_host = 0, k_run = 0;
+        for (int k = 1; k <= p->iters; ++k) {
+            const double beta = (k - 1.0) / (k + 2.0);
+            TIMED(MPI_FFL_K_SOLVER, launch_momentum(xc, xp, h->s_y, beta, k, d.nvox, nullptr, st));
+            forward_impl(h, h->s_y, h->s_r, h->t_htab, h->t_gain, st);
+            TIMED(MPI_FFL_K_SOLVER, launch_sub_norm(h->s_r, d_b, d.ndata, h->w_red, nbd, nullptr, st));
+            TIMED(MPI_FFL_K_SOLVER, launch_finalize(h->w_red, nbd, h->s_hist + (k - 1), st));
+            TIMED(MPI_FFL_K_SOLVER, launch_stop_check(h->s_hist, k - 1, p->stop_rel, flags, flags + 1, st));
+            adjoint_impl(h, h->s_r, h->s_g, st);
+            TIMED(MPI_FFL_K_SOLVER, launch_update(h->s_y, h->s_g, xp, (float)tau, (float)lam, p->nonneg ? 1 : 0, d.N, d.Nz, nullptr, st));
+            check_launch(h, "solve iteration");
+            std::swap(xc, xp);
+            k_run = k;
+            if (p->stop_rel > 0.0) {
+                CK(cudaMemcpyAsync(&done_host, flags, sizeof(int), cudaMemcpyDeviceToHost, st));
+                CK(cudaStreamSynchronize(st));
+                if (done_host) break;
+            }
+        }
+        if (xc != d_x) CK(cudaMemcpyAsync(d_x, xc, sizeof(float) * d.nvox, cudaMemcpyDeviceToDevice, st));
+        if (rep || p->stop_rel > 0.0) {
+            int fl[2] = {0, 0};
+            CK(cudaMemcpyAsync(fl, flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+            double first = 0, last = 0;
+            if (k_run > 0) {
+                CK(cudaMemcpyAsync(&first, h->s_hist, sizeof(double), cudaMemcpyDeviceToHost, st));
+                CK(cudaMemcpyAsync(&last, h->s_hist + (k_run - 1), sizeof(double), cudaMemcpyDeviceToHost, st));
+            }
+            const double bn = std::sqrt(dot_sync(h, d_b, d_b, d.ndata, st));
+            if (rep) {
+                rep->iters_done = k_run;
+                rep->tau = tau;
+                rep->lambda = lam;
+                rep->ata_norm = ata;
+                rep->residual_first = first;
+                rep->residual_last = last;
+                rep->b_norm = bn;
+            }
+            if (fl[0] == 2) {
+                h->err = "non-finite residual";
+                return MPI_FFL_ERR_NONFINITE;
+            }
+        }
+        return MPI_FFL_OK;
+    });
+}
+
+extern "C" int mpi_ffl_profile_enable(mpi_ffl_handle *h, int32_t enable) {
+    if (!h) return MPI_FFL_ERR_INVALID_ARG;
+    h->prof_on = enable ? 1 : 0;
+    return MPI_FFL_OK;
+}
+
+extern "C" int mpi_ffl_profile_read(mpi_ffl_handle *h, double *ms, int64_t *launches) {
+    return guarded(h, [&]() {
+        if (!ms || !launches) {
+            h->err = "NULL output";
+            return MPI_FFL_ERR_INVALID_ARG;
+        }
+        for (int k = 0; k < MPI_FFL_N_KERNEL_KINDS; ++k) {
+            ms[k] = 0.0;
+            launches[k] = 0;
+        }
+        for (auto &r : h->prof_rec) {
+            CK(cudaEventSynchronize(r.b));
+            float t = 0.f;
+            CK(cudaEventElapsedTime(&t, r.a, r.b));
+            if (r.kind >= 0 && r.kind < MPI_FFL_N_KERNEL_KINDS) {
+                ms[r.kind] += t;
+                launches[r.kind] += 1;
+            }
+            h->ev_pool.push_back(r.a);
+            h->ev_pool.push_back(r.b);
+        }
+        h->prof_rec.clear();
+        return MPI_FFL_OK;
+    });
+}
+
+extern "C" int64_t mpi_ffl_launch_count(const mpi_ffl_handle *h) { return h ? h->launches : -1; }

@@ -1,0 +1,167 @@
+// Internal declarations shared by the library's translation units: the handle,
+// table layouts and the kernel launchers of each stage.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/mpi_ffl.h"
+
+namespace mpiffl {
+
+// Per-angle ray-march parameters of the projector (Sec. 2.2, Eqs. (16)-(19)).
+// Along march step s (a row when row_major, else a column) ray i samples the
+// voxel line at position f = inv_c * (i - c) + slope * (s - c) + c, c = (N-1)/2,
+// and the sum is multiplied by scale.
+struct AngleParam {
+    float inv_c;   // 1/cos (rows) or -1/sin (columns)
+    float slope;   // tan (rows) or cot (columns)
+    float scale;   // 1/|cos| or 1/|sin|
+    int row_major; // 1: march rows of x[z][y][:], 0: columns
+};
+
+// One time sample of a raster line: fine-grid cell n and the velocity-weighted
+// interpolation weights w0 = (1-f) v, w1 = f v (Sec. 1.2, Eq. (7)).
+struct TrajEntry {
+    int n;
+    float w0;
+    float w1;
+};
+
+// One entry of the transposed resampling (fine cell <- sample j with weight w).
+struct CsrEntry {
+    int j;
+    float w;
+};
+
+// A group of raster lines of one angle that share a trajectory (same parity).
+struct SegGroup {
+    int m;       // angle
+    int parity;  // trajectory index (line parity when zig-zag, else 0)
+    int z0;      // first line
+    int zstride; // 2 with zig-zag, else 1
+    int count;   // lines in the group
+};
+
+struct Dims {
+    int N, Nz, M, S, P, L, Q, D, Ne, K, W, nb, kmin, hw;
+    int nseg;                      // M * Nz
+    int64_t nvox, nproj, nfine, nsig, ndata;
+    int htab_off, htab_len;        // htab[d + htab_off] = h(d / Q), |d| <= htab_off + pad
+    int n_par;                     // trajectories: 2 with zig-zag, else 1
+};
+
+constexpr int kGroup = 8;          // lines per SegGroup in the staged kernels
+constexpr int kPsfT = 8;           // outputs per thread in the PSF kernels
+constexpr int kMaxHw = 8;          // largest supported half-width
+
+}  // namespace mpiffl
+
+struct mpi_ffl_handle {
+    mpiffl::Dims d{};
+    int device = 0;
+    int precision = MPI_FFL_PREC_FP32;
+    std::string err;
+
+    // host copies of the description
+    std::vector<double> angles;
+    std::vector<float> gains;
+    double fwhm = 0, amp = 0, phase = 0;
+    int zigzag = 1;
+    std::vector<float> dgamma;  // nb complex
+
+    // device tables
+    mpiffl::AngleParam *t_ang = nullptr;
+    float *t_gain = nullptr;       // M
+    float *t_unit_gain = nullptr;  // M ones
+    float *t_htab = nullptr;       // PSF taps
+    float *t_dhtab = nullptr;      // d h / d fwhm taps
+    mpiffl::TrajEntry *t_traj = nullptr;  // n_par * L
+    int *t_csr_ptr = nullptr;             // n_par * (Ne + 1)
+    mpiffl::CsrEntry *t_csr = nullptr;    // n_par * 2L
+    float *t_tw1 = nullptr;               // P * W: cos(2 pi d p / P) d=0..hw, sin d=1..hw
+    float2 *t_tw2_ro = nullptr;           // [r][q]: exp(+2 pi i w_q r / L)
+    float2 *t_tw2_qr = nullptr;           // [q][r]
+    float2 *t_dgam = nullptr;             // nb
+    mpiffl::SegGroup *t_groups = nullptr;
+    int n_groups = 0;
+
+    // workspace
+    float *w_volT = nullptr;   // nvox
+    float *w_proj = nullptr;   // nproj
+    float *w_fine = nullptr;   // nfine
+    float *w_sig = nullptr;    // nsig
+    float *w_data = nullptr;   // ndata
+    float *w_vol2 = nullptr;   // nvox
+    double *w_red = nullptr;   // reduction partials
+    double *w_scal = nullptr;  // device scalars
+    int w_red_len = 0;
+    // solver state
+    float *s_xp = nullptr, *s_y = nullptr, *s_g = nullptr, *s_r = nullptr;
+    double *s_hist = nullptr;
+    int s_hist_len = 0;
+    int *s_flags = nullptr;
+    // measurement hooks
+    int prof_on = 0;
+    int64_t launches = 0;
+    struct ProfRec {
+        int kind;
+        cudaEvent_t a, b;
+    };
+    std::vector<ProfRec> prof_rec;
+    std::vector<cudaEvent_t> ev_pool;
+    // tensor-core path state (tc.cu)
+    void *tc_twb = nullptr;
+    void *tc_state = nullptr;
+    int64_t bytes = 0;
+};
+
+namespace mpiffl {
+
+// ---------------------------------------------------------------- launchers
+// Projector (k_projector.cu)
+void launch_transpose_xy(const float *vol, float *volT, int N, int Nz, cudaStream_t st);
+void launch_project(const float *vol, const float *volT, const AngleParam *ang, float *proj,
+                    int N, int Nz, int M, cudaStream_t st);
+void launch_backproject(const float *proj, const AngleParam *ang, float *vol, int N, int Nz,
+                        int M, cudaStream_t st);
+
+// Staged line kernels (k_line.cu)
+void launch_psf_fwd(const float *proj, const float *htab, float *fine, const Dims &d, cudaStream_t st);
+void launch_psf_adj(const float *fine, const float *htab, float *proj, const Dims &d, cudaStream_t st);
+void launch_resample_fwd(const float *fine, const TrajEntry *traj, const float *gain,
+                         const SegGroup *groups, int n_groups, float *sig, const Dims &d,
+                         cudaStream_t st);
+void launch_resample_adj(const float *sig, const int *csr_ptr, const CsrEntry *csr,
+                         const float *gain, const SegGroup *groups, int n_groups, float *fine,
+                         const Dims &d, cudaStream_t st);
+void launch_dft_fwd(const float *sig, const float *tw1, const float2 *tw2_ro, const float2 *dgam,
+                    float *data, const Dims &d, cudaStream_t st);
+void launch_dft_adj(const float *data, const float *tw1, const float2 *tw2_qr, const float2 *dgam,
+                    float *sig, const Dims &d, cudaStream_t st);
+
+// Solver and reductions (k_solver.cu)
+int reduce_blocks(int64_t n);
+void launch_momentum(const float *x, const float *xp, float *y, double beta_num, int k,
+                     int64_t n, const int *done, cudaStream_t st);
+void launch_sub_norm(float *r, const float *b, int64_t n, double *partials, int nblk,
+                     const int *done, cudaStream_t st);
+void launch_dot(const float *a, const float *b, int64_t n, double *partials, int nblk, cudaStream_t st);
+void launch_finalize(const double *partials, int nblk, double *out, cudaStream_t st);
+void launch_update(const float *y, const float *g, float *xout, float tau, float lam, int nonneg,
+                   int N, int Nz, const int *done, cudaStream_t st);
+void launch_ttt(const float *x, float *out, int N, int Nz, cudaStream_t st);
+void launch_splitmix_fill(float *v, int64_t n, uint64_t seed, cudaStream_t st);
+void launch_scale_by_rsqrt(const float *in, float *out, int64_t n, const double *n2, cudaStream_t st);
+void launch_stop_check(double *hist, int k, double stop_rel, int *done, int *iters_done,
+                       cudaStream_t st);
+void launch_angle_dots(const float *a, const float *b, int M, int64_t per_angle, double *partials,
+                       int nblk_per_angle, cudaStream_t st);
+void launch_angle_finalize(const double *partials, int M, int nblk_per_angle, float *out,
+                           cudaStream_t st);
+void launch_finalize_to_float(const double *partials, int nblk, float *out, cudaStream_t st);
+
+}  // namespace mpiffl

@@ -1,0 +1,213 @@
+"""Python front end of the library: argument marshalling around the C ABI.
+
+Every step of A, A^T and the solve runs in the library's CUDA kernels; PyTorch
+only supplies device memory and the current stream. Tensors are float32 on the
+handle's CUDA device: volumes [N_z, N, N] (x fastest), data [M, N_z, n_bins, 2]
+(complex interleaved, bins k-major with delta ascending).
+"""
+
+import ctypes as C
+import math
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import check
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class FFLOperator:
+    """A handle on the compressed 3D FFL-MPI operator of one scan description.
+
+    Parameters follow include/mpi_ffl.h: volume nx x nx x nz, n_angles FFL angles
+    (default m*pi/M), S samples per drive period, P periods per raster line,
+    drive amplitude A (voxels) and phase phi0, zig-zag raster, fine-grid factor Q,
+    PSF FWHM (voxels), kept harmonics k_min..k_max with half-width `half_width`.
+    """
+
+    def __init__(self, nx, nz, n_angles, S, P, A=6.0, phi0=0.0, zigzag=1, Q=8, fwhm=2.0,
+                 k_min=1, k_max=8, half_width=2, angles=None, gains=None, d_gamma=None,
+                 precision=_lib.PREC_FP32):
+        lib = _lib.load()
+        if not torch.cuda.is_available():
+            raise RuntimeError("FFLOperator needs a CUDA device")
+        self.nx, self.nz, self.n_angles = nx, nz, n_angles
+        self._ang = None if angles is None else (C.c_double * n_angles)(*[float(a) for a in angles])
+        self._gain = None if gains is None else (C.c_float * n_angles)(*[float(g) for g in gains])
+        geom = _lib.Geometry(nx, nx, nz, n_angles,
+                             C.cast(self._ang, C.POINTER(C.c_double)) if self._ang is not None else None,
+                             C.cast(self._gain, C.POINTER(C.c_float)) if self._gain is not None else None)
+        traj = _lib.Trajectory(S, P, float(A), float(phi0), int(zigzag), int(Q))
+        psf = _lib.Psf(float(fwhm))
+        nb = (k_max - k_min + 1) * (2 * half_width + 1)
+        dg = None
+        if d_gamma is not None:
+            d = np.asarray(d_gamma, dtype=np.complex64).reshape(nb)
+            dg = (C.c_float * (2 * nb))(*np.stack([d.real, d.imag], -1).reshape(-1).tolist())
+        harm = _lib.Harmonics(k_min, k_max, half_width, C.cast(dg, C.POINTER(C.c_float)) if dg is not None else None)
+        h = C.c_void_p()
+        with torch.cuda.device(torch.cuda.current_device()):
+            rc = lib.mpi_ffl_create(C.byref(geom), C.byref(traj), C.byref(psf), C.byref(harm), C.byref(h))
+        if rc != _lib.OK:
+            raise _lib.MpiFflError(rc, lib.mpi_ffl_last_error(None).decode())
+        self._h = h
+        self._lib = lib
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        sz = _lib.Sizes()
+        check(lib.mpi_ffl_get_sizes(h, C.byref(sz)), h)
+        self.sizes = sz
+        self.n_bins = sz.n_bins
+        self.L = sz.line_len
+        self.fine_len = sz.fine_len
+        self.S, self.P, self.Q = S, P, Q
+        self.fwhm = fwhm
+        self.params = dict(nx=nx, nz=nz, n_angles=n_angles, S=S, P=P, A=A, phi0=phi0, zigzag=zigzag,
+                           Q=Q, fwhm=fwhm, k_min=k_min, k_max=k_max, half_width=half_width)
+        if precision != _lib.PREC_FP32:
+            self.set_precision(precision)
+
+    @classmethod
+    def from_config(cls, cfg, **kw):
+        keys = ("nx", "nz", "n_angles", "S", "P", "A", "phi0", "zigzag", "Q", "fwhm", "k_min", "k_max",
+                "half_width")
+        args = {k: cfg[k] for k in keys if k in cfg}
+        args.update(kw)
+        return cls(**args)
+
+    # ---------------------------------------------------------------- shapes
+    @property
+    def vol_shape(self):
+        return (self.nz, self.nx, self.nx)
+
+    @property
+    def data_shape(self):
+        return (self.n_angles, self.nz, self.n_bins, 2)
+
+    def _check(self, t, shape, name):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+            raise TypeError(f"{name} must be a contiguous float32 CUDA tensor")
+        if t.numel() != math.prod(shape):
+            raise ValueError(f"{name} has {t.numel()} elements, expected {math.prod(shape)}")
+
+    def new_volume(self):
+        return torch.empty(self.vol_shape, device=self.device, dtype=torch.float32)
+
+    def new_data(self):
+        return torch.empty(self.data_shape, device=self.device, dtype=torch.float32)
+
+    # ---------------------------------------------------------------- operator
+    def forward(self, x, out=None):
+        self._check(x, self.vol_shape, "x")
+        out = self.new_data() if out is None else out
+        self._check(out, self.data_shape, "out")
+        check(self._lib.mpi_ffl_forward(self._h, _ptr(x), _ptr(out), _stream()), self._h)
+        return out
+
+    def adjoint(self, b, out=None):
+        self._check(b, self.data_shape, "b")
+        out = self.new_volume() if out is None else out
+        self._check(out, self.vol_shape, "out")
+        check(self._lib.mpi_ffl_adjoint(self._h, _ptr(b), _ptr(out), _stream()), self._h)
+        return out
+
+    def stage_shapes(self):
+        M, nz = self.n_angles, self.nz
+        return [self.vol_shape, (M, nz, self.nx), (M, nz, self.fine_len), (M, nz, self.L), self.data_shape]
+
+    def apply_stage(self, stage, inp, transpose=False):
+        shapes = self.stage_shapes()
+        sin, sout = (shapes[stage + 1], shapes[stage]) if transpose else (shapes[stage], shapes[stage + 1])
+        self._check(inp, sin, "input")
+        out = torch.empty(sout, device=self.device, dtype=torch.float32)
+        check(self._lib.mpi_ffl_apply_stage(self._h, int(stage), int(bool(transpose)), _ptr(inp), _ptr(out),
+                                            _stream()), self._h)
+        return out
+
+    def apply_ttt(self, x):
+        self._check(x, self.vol_shape, "x")
+        out = self.new_volume()
+        check(self._lib.mpi_ffl_apply_ttt(self._h, _ptr(x), _ptr(out), _stream()), self._h)
+        return out
+
+    def param_grad(self, x, grad_b, want_gain=True, want_fwhm=True):
+        """(d loss/d gain [M], d loss/d fwhm [1]) for loss gradient grad_b at b = A x."""
+        self._check(x, self.vol_shape, "x")
+        self._check(grad_b, self.data_shape, "grad_b")
+        gg = torch.empty(self.n_angles, device=self.device, dtype=torch.float32) if want_gain else None
+        gf = torch.empty(1, device=self.device, dtype=torch.float32) if want_fwhm else None
+        check(self._lib.mpi_ffl_param_grad(self._h, _ptr(x), _ptr(grad_b), _ptr(gg) if gg is not None else None,
+                                           _ptr(gf) if gf is not None else None, _stream()), self._h)
+        return gg, gf
+
+    def power_norm(self, n_iter=50, seed=1234):
+        out = C.c_double()
+        check(self._lib.mpi_ffl_power_norm(self._h, int(n_iter), C.c_uint64(seed), C.byref(out), _stream()), self._h)
+        return out.value
+
+    def solve(self, b, x0=None, iters=50, lam=-1.0, tau=0.0, n_power=50, seed=1234, nonneg=True,
+              stop_rel=0.0, ata_norm=0.0, report=True):
+        """Run Eq. (26); returns (x, report dict or None)."""
+        self._check(b, self.data_shape, "b")
+        x = torch.zeros(self.vol_shape, device=self.device, dtype=torch.float32) if x0 is None else x0.clone()
+        self._check(x, self.vol_shape, "x0")
+        p = _lib.SolveParams(int(iters), float(lam), float(tau), int(n_power), C.c_uint64(seed), int(bool(nonneg)),
+                             float(stop_rel), float(ata_norm))
+        rep = _lib.SolveReport()
+        check(self._lib.mpi_ffl_solve(self._h, _ptr(b), _ptr(x), C.byref(p), C.byref(rep) if report else None,
+                                      _stream()), self._h)
+        if not report:
+            return x, None
+        return x, dict(iters_done=rep.iters_done, tau=rep.tau, lam=rep.lambda_, ata_norm=rep.ata_norm,
+                       residual_first=rep.residual_first, residual_last=rep.residual_last, b_norm=rep.b_norm)
+
+    # ---------------------------------------------------------------- measurement
+    def profile(self, enable=True):
+        check(self._lib.mpi_ffl_profile_enable(self._h, int(bool(enable))), self._h)
+
+    def profile_read(self):
+        """{kernel kind: (ms, launches)} since the last read (waits for the GPU)."""
+        n = len(_lib.KERNEL_KINDS)
+        ms = (C.c_double * n)()
+        ln = (C.c_int64 * n)()
+        check(self._lib.mpi_ffl_profile_read(self._h, ms, ln), self._h)
+        return {k: (ms[i], ln[i]) for i, k in enumerate(_lib.KERNEL_KINDS)}
+
+    def launch_count(self):
+        return int(self._lib.mpi_ffl_launch_count(self._h))
+
+    # ---------------------------------------------------------------- settings
+    def set_precision(self, precision):
+        check(self._lib.mpi_ffl_set_precision(self._h, int(precision)), self._h)
+
+    def set_gain(self, gains):
+        arr = (C.c_float * self.n_angles)(*[float(g) for g in gains])
+        check(self._lib.mpi_ffl_set_gain(self._h, arr), self._h)
+
+    def set_fwhm(self, fwhm):
+        check(self._lib.mpi_ffl_set_psf_fwhm(self._h, float(fwhm)), self._h)
+        self.fwhm = float(fwhm)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.mpi_ffl_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
