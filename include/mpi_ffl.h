@@ -179,6 +179,14 @@ int mpi_ffl_apply_stage(mpi_ffl_handle *h, int32_t stage, int32_t transpose,
 int mpi_ffl_param_grad(mpi_ffl_handle *h, const float *d_x, const float *d_gb_ri,
                        float *d_g_gain, float *d_g_fwhm, void *stream);
 
+/* Real inner product <a, b> = sum_i a_i b_i of two float arrays of n elements
+ * (volumes, or interleaved complex data, whose real inner product is the one of
+ * Sec. 3.3, Eq. (26)), accumulated in FP64 with a fixed summation order and written
+ * to d_out (one double, device memory). Uses the handle's reduction scratch, so calls
+ * on one handle must not overlap on the GPU. n >= 0. */
+int mpi_ffl_dot_f64(mpi_ffl_handle *h, const float *d_a, const float *d_b, int64_t n, double *d_out,
+                    void *stream);
+
 /* T^T T x (Sec. 3.3, Eq. (25)) on a volume. */
 int mpi_ffl_apply_ttt(mpi_ffl_handle *h, const float *d_x, float *d_out, void *stream);
 

@@ -81,6 +81,7 @@ PROTOTYPES = {
     "mpi_ffl_apply_stage": (C.c_int, [H, C.c_int32, C.c_int32, FP, FP, ST]),
     "mpi_ffl_param_grad": (C.c_int, [H, FP, FP, FP, FP, ST]),
     "mpi_ffl_apply_ttt": (C.c_int, [H, FP, FP, ST]),
+    "mpi_ffl_dot_f64": (C.c_int, [H, FP, FP, C.c_int64, FP, ST]),
     "mpi_ffl_power_norm": (C.c_int, [H, C.c_int32, C.c_uint64, C.POINTER(C.c_double), ST]),
     "mpi_ffl_solve": (C.c_int, [H, FP, FP, C.POINTER(SolveParams), C.POINTER(SolveReport), ST]),
     "mpi_ffl_profile_enable": (C.c_int, [H, C.c_int32]),

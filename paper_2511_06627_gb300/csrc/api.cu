@@ -685,6 +685,22 @@ extern "C" int mpi_ffl_param_grad(mpi_ffl_handle *h, const float *d_x, const flo
     });
 }
 
+extern "C" int mpi_ffl_dot_f64(mpi_ffl_handle *h, const float *d_a, const float *d_b, int64_t n, double *d_out,
+                               void *stream) {
+    return guarded(h, [&]() {
+        if (!d_out || n < 0 || (n > 0 && (!d_a || !d_b))) {
+            h->err = "bad dot arguments";
+            return MPI_FFL_ERR_INVALID_ARG;
+        }
+        cudaStream_t st = S(stream);
+        const int nb = reduce_blocks(n);
+        TIMED(MPI_FFL_K_SOLVER, launch_dot(d_a, d_b, n, h->w_red, nb, st));
+        TIMED(MPI_FFL_K_SOLVER, launch_finalize(h->w_red, nb, d_out, st));
+        check_launch(h, "dot");
+        return MPI_FFL_OK;
+    });
+}
+
 extern "C" int mpi_ffl_apply_ttt(mpi_ffl_handle *h, const float *d_x, float *d_out, void *stream) {
     return guarded(h, [&]() {
         if (!d_x || !d_out) {

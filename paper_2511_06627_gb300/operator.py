@@ -137,6 +137,17 @@ class FFLOperator:
         check(self._lib.mpi_ffl_apply_ttt(self._h, _ptr(x), _ptr(out), _stream()), self._h)
         return out
 
+    def dot(self, a, b):
+        """FP64 real inner product of two float32 CUDA tensors of equal size (a 0-d float64 tensor)."""
+        if a.numel() != b.numel():
+            raise ValueError("size mismatch")
+        for t, nm in ((a, "a"), (b, "b")):
+            self._check(t, (t.numel(),), nm)
+        out = torch.empty((), device=self.device, dtype=torch.float64)
+        check(self._lib.mpi_ffl_dot_f64(self._h, _ptr(a), _ptr(b), C.c_int64(a.numel()), _ptr(out), _stream()),
+              self._h)
+        return out
+
     def param_grad(self, x, grad_b, want_gain=True, want_fwhm=True):
         """(d loss/d gain [M], d loss/d fwhm [1]) for loss gradient grad_b at b = A x."""
         self._check(x, self.vol_shape, "x")

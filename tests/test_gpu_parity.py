@@ -144,3 +144,14 @@ def test_ttt_matches_oracle():
     st, op = _make("ragged")
     x = random_volume(st.nz, st.nx, seed=15).astype(np.float32)
     assert rel_l2(_n(op.apply_ttt(_t(x))), regularizer.ttt(x)) < OP_TOL
+
+
+def test_dot_f64_matches_numpy():
+    st, op = _make("ragged")
+    rng = np.random.default_rng(16)
+    a = rng.standard_normal(100003).astype(np.float32)
+    b = rng.standard_normal(100003).astype(np.float32)
+    got = float(op.dot(_t(a), _t(b)).cpu())
+    ref = float(np.dot(a.astype(np.float64), b.astype(np.float64)))
+    assert abs(got - ref) <= 1e-12 * np.linalg.norm(a) * np.linalg.norm(b)
+    assert float(op.dot(_t(a[:0]), _t(b[:0])).cpu()) == 0.0
