@@ -141,7 +141,8 @@ int mpi_ffl_create(const mpi_ffl_geometry *geom, const mpi_ffl_trajectory *traj,
  * device to finish work that uses the handle's memory. */
 int mpi_ffl_destroy(mpi_ffl_handle *h);
 
-/* Message of the last failure of h (NULL: of the last create on this thread). */
+/* Message of the last failure of h (NULL: of the last failed create or handle-free
+ * call on this thread). */
 const char *mpi_ffl_last_error(const mpi_ffl_handle *h);
 
 int mpi_ffl_get_sizes(const mpi_ffl_handle *h, mpi_ffl_sizes *out);
@@ -202,6 +203,33 @@ int mpi_ffl_power_norm(mpi_ffl_handle *h, int32_t n_iter, uint64_t seed, double 
 int mpi_ffl_solve(mpi_ffl_handle *h, const float *d_b_ri, float *d_x_inout,
                   const mpi_ffl_solve_params *params, mpi_ffl_solve_report *report,
                   void *stream);
+
+/* ---- Handle-free entry point that allocates nothing -----------------------------
+ * The paper has no counterpart to this call; it serves callers that cannot call
+ * cudaMalloc (or mpi_ffl_create, which allocates): for example code running while a
+ * framework's caching allocator has reserved the device memory, code that must not
+ * risk the implicit device synchronisation of an allocation, or real-time loops
+ * that forbid allocation latency.
+ *
+ * <a, b> = sum_i a_i b_i of two float arrays of n elements (device memory), summed
+ * in FP64 in a fixed order and written to d_out (one double, device memory). It is
+ * the computation of mpi_ffl_dot_f64 without a handle: its scratch is a file-scope
+ * device array of MPI_FFL_NOALLOC_MAX_PARTIALS doubles (512 KiB, held by every GPU
+ * that loads the library until the process exits), one partial sum per block of
+ * 1024 elements, so n <= MPI_FFL_NOALLOC_MAX_N; larger n returns
+ * MPI_FFL_ERR_INVALID_ARG with a message and launches nothing. It calls no
+ * cudaMalloc, cudaFree or allocating library routine.
+ *
+ * The first call on a device looks up the array's device address on the current
+ * device (cudaGetSymbolAddress) once; make that first call before any stream
+ * capture. Every call on a device shares the array and leaves its partial sums
+ * there; each call writes all the partials it reads before reading them, so nothing
+ * has to be cleared between calls. Calls whose work overlaps on the GPU (on
+ * different streams, unordered) race on the array and give wrong results: order
+ * them on one stream or with events. Asynchronous on `stream`. */
+#define MPI_FFL_NOALLOC_MAX_PARTIALS 65536
+#define MPI_FFL_NOALLOC_MAX_N ((int64_t)MPI_FFL_NOALLOC_MAX_PARTIALS * 1024)
+int mpi_ffl_dot_f64_noalloc(const float *d_a, const float *d_b, int64_t n, double *d_out, void *stream);
 
 /* ---- Measurement hooks (not part of the method) ----------------------------------
  * Kernel kinds for the per-kernel timers below. */

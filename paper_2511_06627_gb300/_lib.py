@@ -18,6 +18,9 @@ ERR_NONFINITE = -4
 ERR_TIMEOUT = -5
 ERR_UNSUPPORTED = -6
 
+NOALLOC_MAX_PARTIALS = 65536
+NOALLOC_MAX_N = NOALLOC_MAX_PARTIALS * 1024
+
 PREC_FP32 = 0
 PREC_BF16X3 = 1
 PREC_TF32 = 2
@@ -82,6 +85,7 @@ PROTOTYPES = {
     "mpi_ffl_param_grad": (C.c_int, [H, FP, FP, FP, FP, ST]),
     "mpi_ffl_apply_ttt": (C.c_int, [H, FP, FP, ST]),
     "mpi_ffl_dot_f64": (C.c_int, [H, FP, FP, C.c_int64, FP, ST]),
+    "mpi_ffl_dot_f64_noalloc": (C.c_int, [FP, FP, C.c_int64, FP, ST]),
     "mpi_ffl_power_norm": (C.c_int, [H, C.c_int32, C.c_uint64, C.POINTER(C.c_double), ST]),
     "mpi_ffl_solve": (C.c_int, [H, FP, FP, C.POINTER(SolveParams), C.POINTER(SolveReport), ST]),
     "mpi_ffl_profile_enable": (C.c_int, [H, C.c_int32]),

@@ -446,6 +446,10 @@ int guarded(mpi_ffl_handle *h, F &&f) {
 
 }  // namespace
 
+namespace mpiffl {
+void set_thread_error(const std::string &msg) { g_create_error = msg; }
+}  // namespace mpiffl
+
 // ============================================================ C ABI
 
 extern "C" int mpi_ffl_create(const mpi_ffl_geometry *geom, const mpi_ffl_trajectory *traj,

@@ -121,6 +121,9 @@ struct mpi_ffl_handle {
 
 namespace mpiffl {
 
+// Message returned by mpi_ffl_last_error(NULL) on this thread.
+void set_thread_error(const std::string &msg);
+
 // ---------------------------------------------------------------- launchers
 // Projector (k_projector.cu)
 void launch_transpose_xy(const float *vol, float *volT, int N, int Nz, cudaStream_t st);
