@@ -80,7 +80,7 @@ typedef struct {
     double drive_amp_vox;       /* A >= 0, in detector bins (= voxels)            */
     double drive_phase;         /* phi0, radians                                  */
     int32_t zigzag;             /* 1: odd lines run backwards                     */
-    int32_t upsample_q;         /* Q >= 1, fine-grid factor of the PSF stage      */
+    int32_t upsample_q;         /* Q in {1,2,4,...,32}, fine-grid factor of H      */
 } mpi_ffl_trajectory;
 
 /* Langevin-derivative PSF width (Appendix B, Eq. (31)). */
@@ -155,6 +155,11 @@ int mpi_ffl_set_precision(mpi_ffl_handle *h, int32_t precision);
  * before touching tables that queued work may still read. */
 int mpi_ffl_set_gain(mpi_ffl_handle *h, const float *gain);
 int mpi_ffl_set_psf_fwhm(mpi_ffl_handle *h, double fwhm_vox);
+
+/* Waits for the stream, then reports whether a kernel of the handle gave up on a
+ * bounded wait since the last check (MPI_FFL_ERR_TIMEOUT; the flag is cleared) or
+ * the stream holds a CUDA error (MPI_FFL_ERR_CUDA). */
+int mpi_ffl_sync_check(mpi_ffl_handle *h, void *stream);
 
 /* b = A x (Sec. 2.2, Eq. (23)). d_x: n_vox floats; d_b_ri: n_data floats (written). */
 int mpi_ffl_forward(mpi_ffl_handle *h, const float *d_x, float *d_b_ri, void *stream);

@@ -79,6 +79,7 @@ PROTOTYPES = {
     "mpi_ffl_set_precision": (C.c_int, [H, C.c_int32]),
     "mpi_ffl_set_gain": (C.c_int, [H, C.POINTER(C.c_float)]),
     "mpi_ffl_set_psf_fwhm": (C.c_int, [H, C.c_double]),
+    "mpi_ffl_sync_check": (C.c_int, [H, ST]),
     "mpi_ffl_forward": (C.c_int, [H, FP, FP, ST]),
     "mpi_ffl_adjoint": (C.c_int, [H, FP, FP, ST]),
     "mpi_ffl_apply_stage": (C.c_int, [H, C.c_int32, C.c_int32, FP, FP, ST]),

@@ -155,8 +155,10 @@ int compute_dims(const mpi_ffl_geometry *g, const mpi_ffl_trajectory *t, const m
     if (!g || !t || !hm) { why = "NULL description"; return MPI_FFL_ERR_INVALID_ARG; }
     if (g->nx != g->ny) { why = "nx must equal ny"; return MPI_FFL_ERR_INVALID_ARG; }
     if (g->nx < 2 || g->nz < 1 || g->n_angles < 1) { why = "bad volume or angle count"; return MPI_FFL_ERR_INVALID_ARG; }
-    if (t->samples_per_period < 2 || t->periods_per_line < 1 || t->upsample_q < 1 || !(t->drive_amp_vox >= 0.0)) {
-        why = "bad trajectory";
+    if (g->nx > 512) { why = "nx > 512 is not supported by the projector kernels"; return MPI_FFL_ERR_UNSUPPORTED; }
+    if (t->samples_per_period < 2 || t->periods_per_line < 1 || t->upsample_q < 1 || t->upsample_q > 32 ||
+        (t->upsample_q & (t->upsample_q - 1)) != 0 || !(t->drive_amp_vox >= 0.0)) {
+        why = "bad trajectory (S >= 2, P >= 1, A >= 0, Q a power of two <= 32)";
         return MPI_FFL_ERR_INVALID_ARG;
     }
     if (hm->half_width < 0 || hm->half_width > kMaxHw || hm->k_min < 0 || hm->k_max < hm->k_min) {
@@ -214,6 +216,18 @@ void angle_table(mpi_ffl_handle *h) {
         }
     }
     upload(h, &h->t_ang, a);
+    // projector blocks hold kProjAnglesPerBlock angles of one orientation
+    std::vector<int> groups;
+    for (int orient = 1; orient >= 0; --orient) {
+        std::vector<int> ms;
+        for (int m = 0; m < d.M; ++m)
+            if (a[m].row_major == orient) ms.push_back(m);
+        for (size_t k = 0; k < ms.size(); k += kProjAnglesPerBlock)
+            for (int u = 0; u < kProjAnglesPerBlock; ++u)
+                groups.push_back(k + u < ms.size() ? ms[k + u] : -1);
+    }
+    h->n_agroups = (int)(groups.size() / kProjAnglesPerBlock);
+    upload(h, &h->t_agroups, groups);
 }
 
 void trajectory_tables(mpi_ffl_handle *h) {
@@ -309,7 +323,7 @@ void release(mpi_ffl_handle *h) {
     void *ptrs[] = {h->t_ang, h->t_gain, h->t_unit_gain, h->t_htab, h->t_dhtab, h->t_traj, h->t_csr_ptr,
                     h->t_csr, h->t_tw1, h->t_tw2_ro, h->t_tw2_qr, h->t_dgam, h->t_groups, h->w_volT,
                     h->w_proj, h->w_fine, h->w_sig, h->w_data, h->w_vol2, h->w_red, h->w_scal,
-                    h->s_xp, h->s_y, h->s_g, h->s_r, h->s_hist, h->s_flags, h->tc_twb};
+                    h->s_xp, h->s_y, h->s_g, h->s_r, h->s_hist, h->s_flags, h->tc_twb, h->t_agroups};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (auto &r : h->prof_rec) {
@@ -335,7 +349,7 @@ void ensure_sig(mpi_ffl_handle *h) {
 // ------------------------------------------------------------ stages
 void stage_p(mpi_ffl_handle *h, const float *x, float *proj, cudaStream_t st) {
     if (any_column_angle(h)) TIMED(MPI_FFL_K_TRANSPOSE, launch_transpose_xy(x, h->w_volT, h->d.N, h->d.Nz, st));
-    TIMED(MPI_FFL_K_PROJECT, launch_project(x, h->w_volT, h->t_ang, proj, h->d.N, h->d.Nz, h->d.M, st));
+    TIMED(MPI_FFL_K_PROJECT, launch_project(x, h->w_volT, h->t_ang, h->t_agroups, h->n_agroups, proj, h->d.N, h->d.Nz, st));
     check_launch(h, "project");
 }
 
@@ -576,6 +590,10 @@ extern "C" int mpi_ffl_set_precision(mpi_ffl_handle *h, int32_t precision) {
         h->err = "unknown precision";
         return MPI_FFL_ERR_INVALID_ARG;
     }
+    if (precision == MPI_FFL_PREC_TF32) {
+        h->err = "TF32 line kernels are not built in this version";
+        return MPI_FFL_ERR_UNSUPPORTED;
+    }
     if (precision != MPI_FFL_PREC_FP32 && !tc_supported(h)) {
         h->err = "tensor-core path does not support this problem shape";
         return MPI_FFL_ERR_UNSUPPORTED;
@@ -610,6 +628,17 @@ extern "C" int mpi_ffl_set_psf_fwhm(mpi_ffl_handle *h, double fwhm) {
         CK(cudaMemcpy(h->t_htab, ht.data(), sizeof(float) * ht.size(), cudaMemcpyHostToDevice));
         CK(cudaMemcpy(h->t_dhtab, dht.data(), sizeof(float) * dht.size(), cudaMemcpyHostToDevice));
         tc_tables_changed(h);
+        return MPI_FFL_OK;
+    });
+}
+
+extern "C" int mpi_ffl_sync_check(mpi_ffl_handle *h, void *stream) {
+    return guarded(h, [&]() {
+        CK(cudaStreamSynchronize(S(stream)));
+        if (tc_take_error(h)) {
+            h->err = "a tensor-core kernel gave up on a bounded wait";
+            return MPI_FFL_ERR_TIMEOUT;
+        }
         return MPI_FFL_OK;
     });
 }

@@ -88,6 +88,8 @@ struct mpi_ffl_handle {
     float2 *t_dgam = nullptr;             // nb
     mpiffl::SegGroup *t_groups = nullptr;
     int n_groups = 0;
+    int *t_agroups = nullptr;  // projector angle groups: kProjAnglesPerBlock indices, -1 = empty
+    int n_agroups = 0;
 
     // workspace
     float *w_volT = nullptr;   // nvox
@@ -127,8 +129,9 @@ void set_thread_error(const std::string &msg);
 // ---------------------------------------------------------------- launchers
 // Projector (k_projector.cu)
 void launch_transpose_xy(const float *vol, float *volT, int N, int Nz, cudaStream_t st);
-void launch_project(const float *vol, const float *volT, const AngleParam *ang, float *proj,
-                    int N, int Nz, int M, cudaStream_t st);
+void launch_project(const float *vol, const float *volT, const AngleParam *ang, const int *agroups,
+                    int n_agroups, float *proj, int N, int Nz, cudaStream_t st);
+constexpr int kProjAnglesPerBlock = 2;  // angle slots per projector block (k_projector.cu)
 void launch_backproject(const float *proj, const AngleParam *ang, float *vol, int N, int Nz,
                         int M, cudaStream_t st);
 

@@ -65,54 +65,75 @@ void launch_psf_fwd(const float *proj, const float *htab, float *fine, const Dim
     k_psf_fwd<<<d.nseg, 256, smem, st>>>(proj, htab, fine, d);
 }
 
-constexpr int kPsfAdjSegs = 4;
+// H^T: proj[i] = sum_e fine[e] h((e - D)/Q - i). Lanes of a warp are
+// (segment s = lane / Q, phase q = lane % Q): each owns kPsfT outputs i0..i0+T-1 of its
+// segment and sums the fine points of its phase with a sliding tap window; the Q
+// phase partials are then added with shuffles. Rows sit kPsfRowPad floats apart
+// modulo 32 so that the lanes' row reads fall in distinct banks, and the tap
+// reads of different segments coincide (broadcast).
+constexpr int kPsfAdjThreads = 256;
 
-__global__ void __launch_bounds__(128) k_psf_adj(const float *__restrict__ fine,
-                                                 const float *__restrict__ htab,
-                                                 float *__restrict__ proj, Dims d) {
+__global__ void __launch_bounds__(kPsfAdjThreads) k_psf_adj(const float *__restrict__ fine,
+                                                            const float *__restrict__ htab,
+                                                            float *__restrict__ proj, Dims d, int row_stride,
+                                                            int segs_per_block) {
     extern __shared__ float sm[];
     float *sh = sm;                      // htab_len
-    float *sf = sm + d.htab_len;         // kPsfAdjSegs * Ne
-    const int seg0 = blockIdx.x * kPsfAdjSegs;
-    const int nsg = min(kPsfAdjSegs, d.nseg - seg0);
+    float *sf = sm + d.htab_len;         // segs_per_block rows of row_stride floats
+    const int seg0 = blockIdx.x * segs_per_block;
+    const int nsg = min(segs_per_block, d.nseg - seg0);
     for (int i = threadIdx.x; i < d.htab_len; i += blockDim.x) sh[i] = htab[i];
-    for (int i = threadIdx.x; i < nsg * d.Ne; i += blockDim.x) sf[i] = fine[(size_t)seg0 * d.Ne + i];
+    for (int sl = 0; sl < nsg; ++sl)
+        for (int e = threadIdx.x; e < d.Ne; e += blockDim.x)
+            sf[sl * row_stride + e] = fine[(size_t)(seg0 + sl) * d.Ne + e];
     __syncthreads();
     const int Q = d.Q;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    const int q = lane % Q;
+    const int sl = lane / Q;               // segment within the block handled by this lane
     const int n_ib = (d.N + kPsfT - 1) / kPsfT;
-    for (int task = threadIdx.x; task < nsg * n_ib; task += blockDim.x) {
-        const int sl = task / n_ib;
-        const int i0 = (task % n_ib) * kPsfT;
-        const float *row = sf + sl * d.Ne;
+    const bool active_seg = sl < nsg;
+    const float *row = sf + (active_seg ? sl : 0) * row_stride;
+    for (int ib = warp; ib < n_ib; ib += nwarps) {
+        const int i0 = ib * kPsfT;
         float acc[kPsfT];
 #pragma unroll
         for (int t = 0; t < kPsfT; ++t) acc[t] = 0.f;
-        for (int q = 0; q < Q; ++q) {
-            const int baseq = q - d.D - Q * i0 + d.htab_off;
-            float w[kPsfT];
+        const int baseq = q - d.D - Q * i0 + d.htab_off;
+        float w[kPsfT];
 #pragma unroll
-            for (int t = 0; t < kPsfT; ++t) w[t] = sh[baseq - Q * t];
-            for (int a = 0, e = q; e < d.Ne; ++a, e += Q) {
-                const float c = row[e];
+        for (int t = 0; t < kPsfT; ++t) w[t] = sh[baseq - Q * t];
+        for (int a = 0, e = q; e < d.Ne; ++a, e += Q) {
+            const float c = row[e];
 #pragma unroll
-                for (int t = 0; t < kPsfT; ++t) acc[t] = fmaf(c, w[t], acc[t]);
+            for (int t = 0; t < kPsfT; ++t) acc[t] = fmaf(c, w[t], acc[t]);
 #pragma unroll
-                for (int t = kPsfT - 1; t > 0; --t) w[t] = w[t - 1];
-                w[0] = sh[baseq + Q * (a + 1)];
-            }
+            for (int t = kPsfT - 1; t > 0; --t) w[t] = w[t - 1];
+            w[0] = sh[baseq + Q * (a + 1)];
         }
-        float *out = proj + (size_t)(seg0 + sl) * d.N;
+        // add the Q phase partials (lanes sl*Q .. sl*Q+Q-1)
 #pragma unroll
         for (int t = 0; t < kPsfT; ++t)
-            if (i0 + t < d.N) out[i0 + t] = acc[t];
+            for (int o = 1; o < Q; o <<= 1) acc[t] += __shfl_xor_sync(0xffffffffu, acc[t], o);
+        if (active_seg && q == 0) {
+            float *out = proj + (size_t)(seg0 + sl) * d.N;
+#pragma unroll
+            for (int t = 0; t < kPsfT; ++t)
+                if (i0 + t < d.N) out[i0 + t] = acc[t];
+        }
     }
 }
 
 void launch_psf_adj(const float *fine, const float *htab, float *proj, const Dims &d, cudaStream_t st) {
-    const size_t smem = sizeof(float) * (d.htab_len + kPsfAdjSegs * d.Ne);
+    // lanes = (segment, phase); Q must be a power of two dividing 32 for the shuffle tree
+    const int segs = 32 / d.Q;
+    const int stride = d.Ne + (((d.Q - d.Ne) % 32) + 32) % 32;  // stride = Q (mod 32)
+    const size_t smem = sizeof(float) * (d.htab_len + (size_t)segs * stride);
     if (smem > 48 * 1024)
         cudaFuncSetAttribute(k_psf_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_psf_adj<<<(d.nseg + kPsfAdjSegs - 1) / kPsfAdjSegs, 128, smem, st>>>(fine, htab, proj, d);
+    k_psf_adj<<<(d.nseg + segs - 1) / segs, kPsfAdjThreads, smem, st>>>(fine, htab, proj, d, stride, segs);
 }
 
 // ----------------------------------------------------------------------------- E V B

@@ -1,13 +1,10 @@
 // Parallel-beam projector P_theta and its gather-form transpose
 // (Sec. 2.2, Eqs. (16)-(19); Joseph interpolation, see AngleParam).
 //
-// Forward: one thread per ray (angle m, slice z, detector bin i) marches the
-// N steps of its ray; rays of one warp are adjacent bins, so at every step they
-// read neighbouring addresses of one voxel line. Column-marched angles read a
-// transposed copy of the volume so that their voxel lines are contiguous too.
-// Transpose: one thread per voxel gathers, for every angle, the (at most two)
-// rays whose interpolation touches it, with the forward's exact weights. No
-// atomics.
+// Both directions process kZc z slices per thread: every slice shares the ray
+// geometry, so the interpolation weights are computed once per kZc samples.
+// Column-marched angles read a transposed copy of the volume, so that every
+// staged voxel line is contiguous.
 #include "internal.h"
 
 namespace mpiffl {
@@ -35,79 +32,144 @@ void launch_transpose_xy(const float *vol, float *volT, int N, int Nz, cudaStrea
     k_transpose_xy<<<grid, block, 0, st>>>(vol, volT, N);
 }
 
-__global__ void __launch_bounds__(128) k_project(const float *__restrict__ vol, const float *__restrict__ volT,
-                                                 const AngleParam *__restrict__ ang,
-                                                 float *__restrict__ proj, int N, int Nz) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int z = blockIdx.y;
-    const int m = blockIdx.z;
-    if (i >= N) return;
-    const AngleParam a = ang[m];
-    const float *base = (a.row_major ? vol : volT) + (size_t)z * N * N;
+// Forward: a block owns kProjAnglesPerBlock angles of one orientation and kZc slices. At
+// march step s the block stages voxel line s of its kZc slices in shared memory
+// (double-buffered, loads for step s+1 in flight while step s is summed); each
+// thread is one ray (angle, bin i) and adds its interpolated sample for all kZc
+// slices at once, so the interpolation weights are computed once per kZc samples.
+constexpr int kZc = 8;
+constexpr int kMaxLd = 4;  // staged floats per thread and step
+
+__global__ void __launch_bounds__(1024) k_project(const float *__restrict__ vol, const float *__restrict__ volT,
+                                                  const AngleParam *__restrict__ ang,
+                                                  const int *__restrict__ agroups, float *__restrict__ proj,
+                                                  int N, int Nz, int rays_per_angle) {
+    extern __shared__ float sm[];  // 2 x kZc x N
+    const int z0 = blockIdx.y * kZc;
+    const int nz = min(kZc, Nz - z0);
+    const int slot = threadIdx.x / rays_per_angle;
+    const int i = threadIdx.x % rays_per_angle;
+    const int m = agroups[blockIdx.x * kProjAnglesPerBlock + slot];
+    const bool active = (m >= 0) && (i < N);
+    const AngleParam ap = ang[m >= 0 ? m : agroups[blockIdx.x * kProjAnglesPerBlock]];
+    const float *src = ap.row_major ? vol : volT;  // one orientation per block
     const float c = 0.5f * (float)(N - 1);
-    const float fi = fmaf(a.inv_c, (float)i - c, c);
-    float acc = 0.f;
+    const float fi = fmaf(ap.inv_c, (float)i - c, c);
+    const int nld = kZc * N;
+    float acc[kZc];
+#pragma unroll
+    for (int zz = 0; zz < kZc; ++zz) acc[zz] = 0.f;
+    float reg[kMaxLd];
+    auto fetch = [&](int s) {
+#pragma unroll
+        for (int u = 0; u < kMaxLd; ++u) {
+            const int t = threadIdx.x + u * blockDim.x;
+            const int zz = t / N, x = t - zz * N;
+            reg[u] = (t < nld && zz < nz) ? __ldg(src + ((size_t)(z0 + zz) * N + s) * N + x) : 0.f;
+        }
+    };
+    auto stash = [&](float *dst) {
+#pragma unroll
+        for (int u = 0; u < kMaxLd; ++u) {
+            const int t = threadIdx.x + u * blockDim.x;
+            if (t < nld) dst[t] = reg[u];
+        }
+    };
+    fetch(0);
+    stash(sm);
+    __syncthreads();
     for (int s = 0; s < N; ++s) {
-        const float f = fmaf(a.slope, (float)s - c, fi);
-        const float fl = floorf(f);
-        const int k = (int)fl;
-        const float t = f - fl;
-        const float *line = base + (size_t)s * N;
-        const float v0 = (k >= 0 && k < N) ? __ldg(line + k) : 0.f;
-        const float v1 = (k + 1 >= 0 && k + 1 < N) ? __ldg(line + k + 1) : 0.f;
-        acc = fmaf(1.f - t, v0, fmaf(t, v1, acc));
+        const float *cur = sm + (s & 1) * nld;
+        if (s + 1 < N) fetch(s + 1);
+        if (active) {
+            const float f = fmaf(ap.slope, (float)s - c, fi);
+            const float fl = floorf(f);
+            const int k = (int)fl;
+            const float t = f - fl;
+            const float w0 = (k >= 0 && k < N) ? 1.f - t : 0.f;
+            const float w1 = (k + 1 >= 0 && k + 1 < N) ? t : 0.f;
+            const int k0 = min(max(k, 0), N - 1);
+            const int k1 = min(max(k + 1, 0), N - 1);
+#pragma unroll
+            for (int zz = 0; zz < kZc; ++zz) acc[zz] = fmaf(w0, cur[zz * N + k0], fmaf(w1, cur[zz * N + k1], acc[zz]));
+        }
+        if (s + 1 < N) stash(sm + ((s + 1) & 1) * nld);
+        __syncthreads();
     }
-    proj[((size_t)m * Nz + z) * N + i] = acc * a.scale;
+    if (active) {
+#pragma unroll
+        for (int zz = 0; zz < kZc; ++zz)
+            if (zz < nz) proj[((size_t)m * Nz + z0 + zz) * N + i] = acc[zz] * ap.scale;
+    }
 }
 
-void launch_project(const float *vol, const float *volT, const AngleParam *ang, float *proj,
-                    int N, int Nz, int M, cudaStream_t st) {
-    dim3 grid((N + 127) / 128, Nz, M);
-    k_project<<<grid, 128, 0, st>>>(vol, volT, ang, proj, N, Nz);
+void launch_project(const float *vol, const float *volT, const AngleParam *ang, const int *agroups,
+                    int n_agroups, float *proj, int N, int Nz, cudaStream_t st) {
+    const int rays = (N + 31) / 32 * 32;
+    const int threads = rays * kProjAnglesPerBlock;
+    const size_t smem = sizeof(float) * 2 * kZc * N;
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(k_project, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    dim3 grid(n_agroups, (Nz + kZc - 1) / kZc);
+    k_project<<<grid, threads, smem, st>>>(vol, volT, ang, agroups, proj, N, Nz, rays);
 }
 
-__global__ void __launch_bounds__(128) k_backproject(const float *__restrict__ proj,
+// Transpose: a thread owns one voxel column (x, y) and kZc slices. For every angle
+// it finds the (at most two) rays whose interpolation touches the voxel, with the
+// forward's exact weights, and gathers their kZc projection values. No atomics.
+__global__ void __launch_bounds__(256) k_backproject(const float *__restrict__ proj,
                                                      const AngleParam *__restrict__ ang,
                                                      float *__restrict__ vol, int N, int Nz, int M) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y;
-    const int z = blockIdx.z;
-    if (x >= N) return;
+    const int x = blockIdx.x * 32 + threadIdx.x;
+    const int y = blockIdx.y * 8 + threadIdx.y;
+    const int z0 = blockIdx.z * kZc;
+    const int nz = min(kZc, Nz - z0);
+    if (x >= N || y >= N) return;
     const float c = 0.5f * (float)(N - 1);
-    float acc = 0.f;
+    float acc[kZc];
+#pragma unroll
+    for (int zz = 0; zz < kZc; ++zz) acc[zz] = 0.f;
     for (int m = 0; m < M; ++m) {
         const AngleParam a = ang[m];
-        const int s = a.row_major ? y : x;          // march step holding this voxel
-        const float q = (float)(a.row_major ? x : y);  // its position along the step's line
-        const float off = a.slope * ((float)s - c);
-        // ray i samples f_i = inv_c (i - c) + off + c; voxel q gets weight 1 - |f_i - q|
-        const float ir = (q - off - c) / a.inv_c + c;
-        const int i0 = (int)floorf(ir);
-        const float *pr = proj + ((size_t)m * Nz + z) * N;
-        float sum = 0.f;
+        const int s = a.row_major ? y : x;             // march step holding this voxel
+        const int qi = a.row_major ? x : y;            // its index along the step's line
+        const float q = (float)qi;
+        const float off = fmaf(a.slope, (float)s - c, c);
+        const float ir = (q - off) / a.inv_c + c;      // ray whose sample lands on q (approx.)
+        const int i1 = __float2int_rn(ir);
+        int iA = 0, iB = 0;
+        float wA = 0.f, wB = 0.f;
 #pragma unroll
-        for (int di = -1; di <= 2; ++di) {
-            const int i = i0 + di;
+        for (int di = -1; di <= 1; ++di) {
+            const int i = i1 + di;
             if (i < 0 || i >= N) continue;
+            // the forward's sample position of ray i at step s, bit for bit
             const float f = fmaf(a.slope, (float)s - c, fmaf(a.inv_c, (float)i - c, c));
             const float fl = floorf(f);
             const int k = (int)fl;
             const float t = f - fl;
-            // identical weights to the forward: (1-t) on k, t on k+1
-            float w = 0.f;
-            if (k == (int)q) w = 1.f - t;
-            else if (k + 1 == (int)q) w = t;
-            if (w != 0.f) sum = fmaf(w, __ldg(pr + i), sum);
+            const float w = (k == qi) ? 1.f - t : ((k + 1 == qi) ? t : 0.f);
+            if (w != 0.f) {
+                if (wA == 0.f) { iA = i; wA = w; }
+                else { iB = i; wB = w; }
+            }
         }
-        acc = fmaf(sum, a.scale, acc);
+        wA *= a.scale;
+        wB *= a.scale;
+        const float *pm = proj + ((size_t)m * Nz + z0) * N;
+#pragma unroll
+        for (int zz = 0; zz < kZc; ++zz)
+            if (zz < nz) acc[zz] = fmaf(wA, __ldg(pm + zz * N + iA), fmaf(wB, __ldg(pm + zz * N + iB), acc[zz]));
     }
-    vol[((size_t)z * N + y) * N + x] = acc;
+#pragma unroll
+    for (int zz = 0; zz < kZc; ++zz)
+        if (zz < nz) vol[((size_t)(z0 + zz) * N + y) * N + x] = acc[zz];
 }
 
 void launch_backproject(const float *proj, const AngleParam *ang, float *vol, int N, int Nz,
                         int M, cudaStream_t st) {
-    dim3 grid((N + 127) / 128, N, Nz);
-    k_backproject<<<grid, 128, 0, st>>>(proj, ang, vol, N, Nz, M);
+    dim3 grid((N + 31) / 32, (N + 7) / 8, (Nz + kZc - 1) / kZc), block(32, 8);
+    k_backproject<<<grid, block, 0, st>>>(proj, ang, vol, N, Nz, M);
 }
 
 }  // namespace mpiffl

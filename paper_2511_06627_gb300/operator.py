@@ -191,6 +191,10 @@ class FFLOperator:
         check(self._lib.mpi_ffl_profile_read(self._h, ms, ln), self._h)
         return {k: (ms[i], ln[i]) for i, k in enumerate(_lib.KERNEL_KINDS)}
 
+    def sync_check(self):
+        """Wait for the stream; raise if a kernel gave up on a bounded wait or the stream failed."""
+        check(self._lib.mpi_ffl_sync_check(self._h, _stream()), self._h)
+
     def launch_count(self):
         return int(self._lib.mpi_ffl_launch_count(self._h))
 
