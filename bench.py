@@ -174,6 +174,8 @@ ALGO_BYTES = {
     "tc_fwd": lambda d: 4 * (d["nfine"] + d["ndata"]),
     "tc_adj": lambda d: 4 * (d["nfine"] + d["ndata"]),
     "transpose": lambda d: 8 * d["nvox"],
+    "gemm_fwd": lambda d: 4 * (d["nfine"] + d["ndata"]),
+    "gemm_adj": lambda d: 4 * (d["nfine"] + d["ndata"]),
 }
 
 
@@ -190,6 +192,8 @@ def run_ours(args, cfg, rank, world, local_rank):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     prec = {"fp32": PREC_FP32, "bf16x3": PREC_BF16X3, "tf32": PREC_TF32}[args.precision]
     op = FFLOperator.from_config(cfg, precision=prec)
+    if args.path:
+        op.set_path(args.path)
     sz = op.sizes
     dims = dict(nvox=sz.n_vox, nproj=sz.n_proj, nfine=sz.n_fine, nsig=sz.n_sig, ndata=sz.n_data)
     x_host = torch.from_numpy(phantom_for(cfg)).pin_memory()
@@ -314,6 +318,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16x3", "tf32"])
+    ap.add_argument("--path", default=None, choices=["staged", "fused", "line_gemm", "full_gemm"])
     ap.add_argument("--workload", default="invivo", choices=["invivo", "phantom", "tiny"])
     ap.add_argument("--oracle-angles", type=int, default=1)
     ap.add_argument("--recon-iters", type=int, default=100)

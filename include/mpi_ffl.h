@@ -61,6 +61,22 @@ extern "C" {
 #define MPI_FFL_PREC_BF16X3 1 /* tensor cores: bf16 hi+lo split, 3 products, FP32 acc  */
 #define MPI_FFL_PREC_TF32 2   /* tensor cores: tf32 operands, FP32 accumulate          */
 
+/* How A and A^T are evaluated (the operator is the same; only the order of evaluation
+ * and the arithmetic differ):
+ *   STAGED     P, H, E V B and S D_Gamma F as separate FP32 CUDA-core kernels; the
+ *              time signal (L floats per line) passes through HBM. Precision FP32.
+ *   FUSED      P and H as above; E V B fused with the band DFT on tensor cores
+ *              (tcgen05, BF16x3): the time signal stays on chip.
+ *   LINE_GEMM  P and H as above; S D_Gamma F V E, identical for every line of one
+ *              trajectory, precomputed in double precision as one matrix per
+ *              trajectory (the reassociation of Sec. 2.1, Eq. (13)) and applied as a
+ *              tensor-core GEMM (BF16x3).
+ *   FULL_GEMM  P, then S D_Gamma F V E H as one matrix per trajectory (BF16x3). */
+#define MPI_FFL_PATH_STAGED 0
+#define MPI_FFL_PATH_FUSED 1
+#define MPI_FFL_PATH_LINE_GEMM 2
+#define MPI_FFL_PATH_FULL_GEMM 3
+
 typedef struct mpi_ffl_handle mpi_ffl_handle;
 
 /* Volume and FFL angles (Sec. 2.2; Sec. 3.1: angles equally spaced over 180 deg). */
@@ -147,8 +163,15 @@ const char *mpi_ffl_last_error(const mpi_ffl_handle *h);
 
 int mpi_ffl_get_sizes(const mpi_ffl_handle *h, mpi_ffl_sizes *out);
 
-/* Arithmetic of the DFT stage for forward/adjoint/solve (MPI_FFL_PREC_*). */
+/* Arithmetic of the line stages for forward/adjoint/solve (MPI_FFL_PREC_*). FP32
+ * selects the STAGED path; BF16X3 keeps a tensor-core path, or selects FUSED when the
+ * path was STAGED. TF32 returns MPI_FFL_ERR_UNSUPPORTED in this version. */
 int mpi_ffl_set_precision(mpi_ffl_handle *h, int32_t precision);
+
+/* Evaluation path (MPI_FFL_PATH_*); returns MPI_FFL_ERR_UNSUPPORTED when the shape is
+ * outside what the path's kernels accept (the handle keeps its previous path). */
+int mpi_ffl_set_path(mpi_ffl_handle *h, int32_t path);
+int mpi_ffl_get_path(const mpi_ffl_handle *h);
 
 /* Replace the per-angle gains (host array of n_angles) or the PSF width. Both take
  * effect for work enqueued after the call returns; the call synchronises the device
@@ -250,7 +273,9 @@ int mpi_ffl_dot_f64_noalloc(const float *d_a, const float *d_b, int64_t n, doubl
 #define MPI_FFL_K_TC_FWD 9        /* E V B fused with S D_Gamma F (tensor cores)    */
 #define MPI_FFL_K_TC_ADJ 10       /* its transpose (tensor cores)                   */
 #define MPI_FFL_K_SOLVER 11       /* momentum, residual, update and reductions      */
-#define MPI_FFL_N_KERNEL_KINDS 12
+#define MPI_FFL_K_GEMM_FWD 12     /* collapsed line operator, forward GEMM          */
+#define MPI_FFL_K_GEMM_ADJ 13     /* collapsed line operator, adjoint GEMM          */
+#define MPI_FFL_N_KERNEL_KINDS 14
 
 /* enable != 0: record a CUDA event pair around every kernel the handle launches (on
  * the launching stream) until disabled; enable == 0 stops recording. */

@@ -8,6 +8,11 @@ This package is the thin Python binding over that ABI.
 
 from . import _lib  # noqa: F401
 from ._lib import (  # noqa: F401
+    PATH_FULL_GEMM,
+    PATH_FUSED,
+    PATH_LINE_GEMM,
+    PATH_STAGED,
+    PATHS,
     PREC_BF16X3,
     PREC_FP32,
     PREC_TF32,

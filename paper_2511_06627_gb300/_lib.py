@@ -27,6 +27,9 @@ PREC_TF32 = 2
 
 STAGE_P, STAGE_H, STAGE_EVB, STAGE_F = 0, 1, 2, 3
 
+PATH_STAGED, PATH_FUSED, PATH_LINE_GEMM, PATH_FULL_GEMM = 0, 1, 2, 3
+PATHS = {"staged": PATH_STAGED, "fused": PATH_FUSED, "line_gemm": PATH_LINE_GEMM, "full_gemm": PATH_FULL_GEMM}
+
 
 class Geometry(C.Structure):
     _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("n_angles", C.c_int32),
@@ -77,6 +80,8 @@ PROTOTYPES = {
     "mpi_ffl_last_error": (C.c_char_p, [H]),
     "mpi_ffl_get_sizes": (C.c_int, [H, C.POINTER(Sizes)]),
     "mpi_ffl_set_precision": (C.c_int, [H, C.c_int32]),
+    "mpi_ffl_set_path": (C.c_int, [H, C.c_int32]),
+    "mpi_ffl_get_path": (C.c_int, [H]),
     "mpi_ffl_set_gain": (C.c_int, [H, C.POINTER(C.c_float)]),
     "mpi_ffl_set_psf_fwhm": (C.c_int, [H, C.c_double]),
     "mpi_ffl_sync_check": (C.c_int, [H, ST]),
@@ -95,7 +100,7 @@ PROTOTYPES = {
 }
 
 KERNEL_KINDS = ["transpose", "project", "backproject", "psf_fwd", "psf_adj", "resample_fwd", "resample_adj",
-                "dft_fwd", "dft_adj", "tc_fwd", "tc_adj", "solver"]
+                "dft_fwd", "dft_adj", "tc_fwd", "tc_adj", "solver", "gemm_fwd", "gemm_adj"]
 
 _lib = None
 

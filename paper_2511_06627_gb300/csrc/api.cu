@@ -8,6 +8,7 @@
 #include <new>
 
 #include "internal.h"
+#include "collapsed.h"
 #include "tc.h"
 
 using namespace mpiffl;
@@ -136,6 +137,30 @@ double langevin_half_point() {
     return 0.5 * (lo + hi);
 }
 
+}  // namespace
+
+namespace mpiffl {
+double langevin_d1_host(double x) { return langevin_d1(x); }
+double langevin_half_point_host() { return langevin_half_point(); }
+// FFL sample j of a line with the given trajectory (parity): fine cell n, fraction f, velocity v
+void traj_point_host(const mpi_ffl_handle *h, int par, int j, int &n, double &f, double &v) {
+    const Dims &d = h->d;
+    const double kPi = 3.14159265358979323846;
+    const double slope = (double)(d.N - 1) / (double)(d.L - 1);
+    const double slow = par ? (d.N - 1) - slope * j : slope * j;
+    const double dslow = par ? -slope : slope;
+    const double ph = 2.0 * kPi * (double)(j % d.S) / d.S + h->phase;
+    const double xi = slow + h->amp * std::sin(ph);
+    v = dslow + h->amp * (2.0 * kPi / d.S) * std::cos(ph);
+    const double tt = d.Q * xi + d.D;
+    n = (int)std::floor(tt);
+    if (n > d.Ne - 2) n = d.Ne - 2;
+    f = tt - n;
+}
+}  // namespace mpiffl
+
+namespace {
+
 void psf_tables(const Dims &d, double fwhm, std::vector<float> &h, std::vector<float> &dh) {
     const double a = fwhm / (2.0 * langevin_half_point());
     h.resize(d.htab_len);
@@ -233,26 +258,29 @@ void angle_table(mpi_ffl_handle *h) {
 void trajectory_tables(mpi_ffl_handle *h) {
     const Dims &d = h->d;
     std::vector<TrajEntry> tr((size_t)d.n_par * d.L);
+    std::vector<int2> tnf((size_t)d.n_par * d.L);
+    h->traj_n.assign((size_t)d.n_par * d.L, 0);
+    std::vector<float> vr((size_t)d.n_par * d.S);
     std::vector<int> ptr((size_t)d.n_par * (d.Ne + 1), 0);
     std::vector<CsrEntry> csr((size_t)d.n_par * 2 * d.L);
     const double slope = (double)(d.N - 1) / (double)(d.L - 1);
     for (int par = 0; par < d.n_par; ++par) {
         TrajEntry *T = tr.data() + (size_t)par * d.L;
         for (int j = 0; j < d.L; ++j) {
-            const double slow = par ? (d.N - 1) - slope * j : slope * j;
-            const double dslow = par ? -slope : slope;
-            const double ph = 2.0 * kPi * (double)(j % d.S) / d.S + h->phase;
-            const double xi = slow + h->amp * std::sin(ph);
-            const double v = dslow + h->amp * (2.0 * kPi / d.S) * std::cos(ph);
-            const double tt = d.Q * xi + d.D;
-            int n = (int)std::floor(tt);
-            if (n > d.Ne - 2) n = d.Ne - 2;
-            if (n < 0 || tt > d.Ne - 1 + 1e-9) {
+            int n;
+            double f, v;
+            traj_point_host(h, par, j, n, f, v);
+            if (n < 0 || f > 1.0 + 1e-9) {
                 set_err(h, "trajectory leaves the fine grid");
                 throw Fail{MPI_FFL_ERR_INVALID_ARG};
             }
-            const double f = tt - n;
             T[j] = TrajEntry{n, (float)((1.0 - f) * v), (float)(f * v)};
+            const float ff = (float)f;
+            int fb;
+            std::memcpy(&fb, &ff, 4);
+            tnf[(size_t)par * d.L + j] = make_int2(n, fb);
+            h->traj_n[(size_t)par * d.L + j] = n;
+            if (j < d.S) vr[(size_t)par * d.S + j] = (float)v;  // v_j = v_{j mod S}
         }
         // CSR of the transpose: cell n_j <- (j, w0), cell n_j + 1 <- (j, w1), j ascending
         int *P = ptr.data() + (size_t)par * (d.Ne + 1);
@@ -271,6 +299,8 @@ void trajectory_tables(mpi_ffl_handle *h) {
         }
     }
     upload(h, &h->t_traj, tr);
+    upload(h, &h->t_tnf, tnf);
+    upload(h, &h->t_vr, vr);
     upload(h, &h->t_csr_ptr, ptr);
     upload(h, &h->t_csr, csr);
 }
@@ -323,7 +353,8 @@ void release(mpi_ffl_handle *h) {
     void *ptrs[] = {h->t_ang, h->t_gain, h->t_unit_gain, h->t_htab, h->t_dhtab, h->t_traj, h->t_csr_ptr,
                     h->t_csr, h->t_tw1, h->t_tw2_ro, h->t_tw2_qr, h->t_dgam, h->t_groups, h->w_volT,
                     h->w_proj, h->w_fine, h->w_sig, h->w_data, h->w_vol2, h->w_red, h->w_scal,
-                    h->s_xp, h->s_y, h->s_g, h->s_r, h->s_hist, h->s_flags, h->tc_twb, h->t_agroups};
+                    h->s_xp, h->s_y, h->s_g, h->s_r, h->s_hist, h->s_flags, h->tc_twb, h->t_agroups,
+                    h->t_tnf, h->t_vr};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (auto &r : h->prof_rec) {
@@ -332,6 +363,7 @@ void release(mpi_ffl_handle *h) {
     }
     for (auto e : h->ev_pool) cudaEventDestroy(e);
     tc_release(h);
+    col_release(h);
 }
 
 cudaStream_t S(void *s) { return (cudaStream_t)s; }
@@ -361,10 +393,22 @@ void stage_pt(mpi_ffl_handle *h, const float *proj, float *x, cudaStream_t st) {
 void forward_impl(mpi_ffl_handle *h, const float *x, float *b, const float *htab, const float *gain,
                   cudaStream_t st) {
     const Dims &d = h->d;
+    int path = h->path;
+    if (path == MPI_FFL_PATH_FULL_GEMM && htab != h->t_htab) path = MPI_FFL_PATH_LINE_GEMM;  // other taps
     stage_p(h, x, h->w_proj, st);
+    if (path == MPI_FFL_PATH_FULL_GEMM) {
+        TIMED(MPI_FFL_K_GEMM_FWD, col_forward(h, h->w_proj, true, gain, b, st));
+        check_launch(h, "gemm_fwd");
+        return;
+    }
     TIMED(MPI_FFL_K_PSF_FWD, launch_psf_fwd(h->w_proj, htab, h->w_fine, d, st));
     check_launch(h, "psf_fwd");
-    if (h->precision != MPI_FFL_PREC_FP32 && tc_supported(h)) {
+    if (path == MPI_FFL_PATH_LINE_GEMM) {
+        TIMED(MPI_FFL_K_GEMM_FWD, col_forward(h, h->w_fine, false, gain, b, st));
+        check_launch(h, "gemm_fwd");
+        return;
+    }
+    if (path == MPI_FFL_PATH_FUSED) {
         TIMED(MPI_FFL_K_TC_FWD, tc_forward_line(h, h->w_fine, gain, b, st));
         check_launch(h, "tc_forward");
         return;
@@ -378,7 +422,16 @@ void forward_impl(mpi_ffl_handle *h, const float *x, float *b, const float *htab
 
 void adjoint_impl(mpi_ffl_handle *h, const float *b, float *x, cudaStream_t st) {
     const Dims &d = h->d;
-    if (h->precision != MPI_FFL_PREC_FP32 && tc_supported(h)) {
+    if (h->path == MPI_FFL_PATH_FULL_GEMM) {
+        TIMED(MPI_FFL_K_GEMM_ADJ, col_adjoint(h, b, true, h->t_gain, h->w_proj, st));
+        check_launch(h, "gemm_adj");
+        stage_pt(h, h->w_proj, x, st);
+        return;
+    }
+    if (h->path == MPI_FFL_PATH_LINE_GEMM) {
+        TIMED(MPI_FFL_K_GEMM_ADJ, col_adjoint(h, b, false, h->t_gain, h->w_fine, st));
+        check_launch(h, "gemm_adj");
+    } else if (h->path == MPI_FFL_PATH_FUSED) {
         TIMED(MPI_FFL_K_TC_ADJ, tc_adjoint_line(h, b, h->t_gain, h->w_fine, st));
         check_launch(h, "tc_adjoint");
     } else {
@@ -537,6 +590,7 @@ extern "C" int mpi_ffl_create(const mpi_ffl_geometry *geom, const mpi_ffl_trajec
         dev_alloc(h, &h->s_r, d.ndata);
         dev_alloc(h, &h->s_flags, 4);
         tc_init(h);
+        col_init(h);
         CK(cudaDeviceSynchronize());
     } catch (const Fail &e) {
         if (g_create_error.empty()) g_create_error = h->err.empty() ? "create failed" : h->err;
@@ -594,13 +648,39 @@ extern "C" int mpi_ffl_set_precision(mpi_ffl_handle *h, int32_t precision) {
         h->err = "TF32 line kernels are not built in this version";
         return MPI_FFL_ERR_UNSUPPORTED;
     }
-    if (precision != MPI_FFL_PREC_FP32 && !tc_supported(h)) {
-        h->err = "tensor-core path does not support this problem shape";
-        return MPI_FFL_ERR_UNSUPPORTED;
+    if (precision == MPI_FFL_PREC_FP32) {
+        h->precision = precision;
+        h->path = MPI_FFL_PATH_STAGED;
+        return MPI_FFL_OK;
+    }
+    if (h->path == MPI_FFL_PATH_STAGED) {
+        if (!tc_supported(h)) {
+            h->err = "tensor-core path does not support this problem shape";
+            return MPI_FFL_ERR_UNSUPPORTED;
+        }
+        h->path = MPI_FFL_PATH_FUSED;
     }
     h->precision = precision;
     return MPI_FFL_OK;
 }
+
+extern "C" int mpi_ffl_set_path(mpi_ffl_handle *h, int32_t path) {
+    if (!h) return MPI_FFL_ERR_INVALID_ARG;
+    if (path < MPI_FFL_PATH_STAGED || path > MPI_FFL_PATH_FULL_GEMM) {
+        h->err = "unknown path";
+        return MPI_FFL_ERR_INVALID_ARG;
+    }
+    if ((path == MPI_FFL_PATH_FUSED && !tc_supported(h)) ||
+        ((path == MPI_FFL_PATH_LINE_GEMM || path == MPI_FFL_PATH_FULL_GEMM) && !col_supported(h))) {
+        h->err = "this path does not support the problem shape";
+        return MPI_FFL_ERR_UNSUPPORTED;
+    }
+    h->path = path;
+    h->precision = path == MPI_FFL_PATH_STAGED ? MPI_FFL_PREC_FP32 : MPI_FFL_PREC_BF16X3;
+    return MPI_FFL_OK;
+}
+
+extern "C" int mpi_ffl_get_path(const mpi_ffl_handle *h) { return h ? h->path : MPI_FFL_ERR_INVALID_ARG; }
 
 extern "C" int mpi_ffl_set_gain(mpi_ffl_handle *h, const float *gain) {
     return guarded(h, [&]() {
@@ -635,7 +715,7 @@ extern "C" int mpi_ffl_set_psf_fwhm(mpi_ffl_handle *h, double fwhm) {
 extern "C" int mpi_ffl_sync_check(mpi_ffl_handle *h, void *stream) {
     return guarded(h, [&]() {
         CK(cudaStreamSynchronize(S(stream)));
-        if (tc_take_error(h)) {
+        if (tc_take_error(h) | col_take_error(h)) {
             h->err = "a tensor-core kernel gave up on a bounded wait";
             return MPI_FFL_ERR_TIMEOUT;
         }

@@ -1,0 +1,449 @@
+// Collapsed line operator on tensor cores.
+//
+// Every raster line of one trajectory (line parity) sees the same E, V and the
+// same band DFT, so S D_Gamma F V E (Sec. 2.1, Eq. (13), without the per-angle
+// gain) is one fixed complex matrix W of n_bins x N_e per trajectory -- the same
+// reassociation of the operator chain that lets the paper apply one FFT instead of
+// three. W is built once on the host in double precision from the trajectory
+// (W[o][e] = D_o L^-1/2 sum_j e^{2 pi i w_o j / L} (w0_j [n_j = e] + w1_j [n_j + 1 = e])),
+// and optionally folded with H into W H (n_bins x N). A line stage then is
+//     data[line] = g_m W fine[line]          (forward)
+//     fine[line] = g_m Re(W^H data[line])    (adjoint, real inner product)
+// i.e. one dense GEMM per trajectory, with W stored as a real matrix whose rows
+// alternate Re and Im, so the data stay in their interleaved complex layout.
+//
+// GEMM kernel: C[row] = scale[row] * sum_k A[row][k] B[n][k] on tcgen05 with the
+// FP32 operands split into bf16 hi + lo (hi*hi + hi*lo + lo*hi, FP32 accumulate).
+// Warps 0-3 convert A rows (gathered by an index list) into the canonical K-major
+// shared-memory layout and run the epilogue; warp 4 issues the MMAs; warp 5 streams
+// the pre-split B operand with bulk copies. Stages are handed over with mbarriers.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "collapsed.h"
+#include "tc_ptx.cuh"
+
+namespace mpiffl {
+
+namespace {
+
+constexpr int kBM = 128;     // rows per tile (MMA M)
+constexpr int kBK = 64;      // K per pipeline stage
+constexpr int kProd = 128;   // producer threads (one per row)
+constexpr uint32_t kWait = 1u << 24;
+
+struct GemmArgs {
+    const float *A;
+    int64_t lda;
+    const int *arow;     // M row indices into A
+    int M, Ka;           // rows, valid K
+    const uint8_t *B;    // per N tile, per K chunk: hi then lo blocks of BN x kBK bf16 (canonical)
+    int BN, nkc;         // N tile width, K chunks
+    float *C;
+    int64_t ldc;
+    const int *crow;     // M row indices into C
+    int Nc;              // valid N
+    const float *rscale; // per-row scale: scale[arow / rdiv]
+    int rdiv;
+    int prec;
+    int stages;
+    uint32_t tmem_cols;
+    int *err;
+};
+
+__device__ __forceinline__ void split8(const float (&v)[8], uint4 &hi, uint4 &lo) {
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        __nv_bfloat162 h2 = __float22bfloat162_rn(make_float2(v[2 * i], v[2 * i + 1]));
+        const uint32_t hb = *reinterpret_cast<uint32_t *>(&h2);
+        const float h0 = __uint_as_float(hb << 16), h1 = __uint_as_float(hb & 0xFFFF0000u);
+        __nv_bfloat162 l2 = __float22bfloat162_rn(make_float2(v[2 * i] - h0, v[2 * i + 1] - h1));
+        h[i] = hb;
+        l[i] = *reinterpret_cast<uint32_t *>(&l2);
+    }
+    hi = make_uint4(h[0], h[1], h[2], h[3]);
+    lo = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+__global__ void __launch_bounds__(192, 1) k_gemm_split(GemmArgs g) {
+    extern __shared__ __align__(128) uint8_t sm[];
+    const uint32_t bytesA = kBM * kBK * 2;          // one of hi | lo
+    const uint32_t bytesB = (uint32_t)g.BN * kBK * 2;
+    const uint32_t stage = 2 * bytesA + 2 * bytesB;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + g.stages * stage);  // full[S], empty[S], done
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 2 * g.stages + 1);
+    int *flag = reinterpret_cast<int *>(tslot + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int mt = blockIdx.x, nt = blockIdx.y;
+
+    if (tid == 0) {
+        for (int s = 0; s < g.stages; ++s) {
+            ptx::mbar_init(&bars[s], 4 + 1);       // 4 producer warps + the B copy
+            ptx::mbar_init(&bars[g.stages + s], 1);
+        }
+        ptx::mbar_init(&bars[2 * g.stages], 1);
+        ptx::fence_mbar_init();
+        *flag = 0;
+    }
+    if (warp == 0) {
+        ptx::tmem_alloc(tslot, g.tmem_cols);
+        ptx::tmem_relinquish();
+    }
+    ptx::tc_fence_before();
+    __syncthreads();
+    ptx::tc_fence_after();
+    const uint32_t tmem = *tslot;
+
+    if (warp < 4) {
+        // ------------------------------------------------------------ A producers
+        const int row = tid;
+        const int gm = mt * kBM + row;
+        const int ar = gm < g.M ? __ldg(g.arow + gm) : -1;
+        const float *arow = ar >= 0 ? g.A + (size_t)ar * g.lda : nullptr;
+        bool ok = true;
+        for (int kc = 0; kc < g.nkc; ++kc) {
+            const int s = kc % g.stages;
+            if (kc >= g.stages && !ptx::mbar_wait_bounded(&bars[g.stages + s], ((kc / g.stages) - 1) & 1, kWait)) {
+                ok = false;
+                break;
+            }
+            uint8_t *sa = sm + s * stage;
+            const int k0 = kc * kBK;
+#pragma unroll 2
+            for (int kb = 0; kb < kBK / 8; ++kb) {
+                float v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int k = k0 + kb * 8 + u;
+                    v[u] = (arow && k < g.Ka) ? __ldg(arow + k) : 0.f;
+                }
+                uint4 hi, lo;
+                split8(v, hi, lo);
+                const uint32_t off = (row / 8) * 1024u + kb * 128u + (row % 8) * 16u;
+                *reinterpret_cast<uint4 *>(sa + off) = hi;
+                *reinterpret_cast<uint4 *>(sa + bytesA + off) = lo;
+            }
+            ptx::fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) ptx::mbar_arrive(&bars[s]);
+        }
+        // ------------------------------------------------------------ epilogue
+        if (ok && ptx::mbar_wait_bounded(&bars[2 * g.stages], 0, kWait)) {
+            ptx::tc_fence_after();
+            const int cr = gm < g.M ? __ldg(g.crow + gm) : -1;
+            const float sc = (cr >= 0 && g.rscale) ? __ldg(g.rscale + ar / g.rdiv) : 1.f;
+            float *crow = cr >= 0 ? g.C + (size_t)cr * g.ldc : nullptr;
+            for (int c0 = 0; c0 < g.BN; c0 += 16) {
+                float v[16];
+                ptx::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + c0, v);
+                const int n0 = nt * g.BN + c0;
+                if (crow) {
+#pragma unroll
+                    for (int u = 0; u < 16; ++u)
+                        if (n0 + u < g.Nc) crow[n0 + u] = sc * v[u];
+                }
+            }
+        } else {
+            atomicExch(flag, 1);
+        }
+    } else if (warp == 4) {
+        // ------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            const uint32_t idesc = ptx::instr_desc(1, kBM, (uint32_t)g.BN);
+            bool ok = true;
+            for (int kc = 0; kc < g.nkc && ok; ++kc) {
+                const int s = kc % g.stages;
+                if (!ptx::mbar_wait_bounded(&bars[s], (kc / g.stages) & 1, kWait)) {
+                    ok = false;
+                    break;
+                }
+                ptx::tc_fence_after();
+                const uint32_t a0 = ptx::smem_u32(sm + s * stage);
+                const uint32_t b0 = a0 + 2 * bytesA;
+                for (int ks = 0; ks < kBK / 16; ++ks) {
+                    const uint64_t dAh = ptx::smem_desc(a0 + ks * 256, 128, 1024);
+                    const uint64_t dAl = ptx::smem_desc(a0 + bytesA + ks * 256, 128, 1024);
+                    const uint64_t dBh = ptx::smem_desc(b0 + ks * 256, 128, 1024);
+                    const uint64_t dBl = ptx::smem_desc(b0 + bytesB + ks * 256, 128, 1024);
+                    ptx::mma_bf16(tmem, dAh, dBh, idesc, (kc > 0 || ks > 0) ? 1u : 0u);
+                    if (g.prec == MPI_FFL_PREC_BF16X3) {
+                        ptx::mma_bf16(tmem, dAh, dBl, idesc, 1u);
+                        ptx::mma_bf16(tmem, dAl, dBh, idesc, 1u);
+                    }
+                }
+                ptx::mma_commit(&bars[g.stages + s]);
+            }
+            if (ok) ptx::mma_commit(&bars[2 * g.stages]);
+            else atomicExch(flag, 1);
+        }
+        __syncwarp();
+    } else {
+        // ------------------------------------------------------------ B loader
+        if (lane == 0) {
+            const uint8_t *bt = g.B + (size_t)nt * g.nkc * 2 * bytesB;
+            for (int kc = 0; kc < g.nkc; ++kc) {
+                const int s = kc % g.stages;
+                if (kc >= g.stages && !ptx::mbar_wait_bounded(&bars[g.stages + s], ((kc / g.stages) - 1) & 1, kWait)) {
+                    atomicExch(flag, 1);
+                    break;
+                }
+                uint8_t *sb = sm + s * stage + 2 * bytesA;
+                ptx::mbar_arrive_expect_tx(&bars[s], 2 * bytesB);
+                ptx::bulk_g2s(sb, bt + (size_t)kc * 2 * bytesB, 2 * bytesB, &bars[s]);
+            }
+        }
+        __syncwarp();
+    }
+    ptx::tc_fence_before();
+    __syncthreads();
+    if (tid == 0 && *flag) atomicExch(g.err, 1);
+    if (warp == 0) ptx::tmem_dealloc(tmem, g.tmem_cols);
+}
+
+uint16_t bf16_bits(double x) {
+    const float f = (float)x;
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    const uint32_t rounding = 0x7FFFu + ((u >> 16) & 1u);
+    return (uint16_t)((u + rounding) >> 16);
+}
+double bf16_value(uint16_t b) {
+    const uint32_t u = (uint32_t)b << 16;
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+}
+
+// Pre-split B operand for k_gemm_split: Bm is Nv x Kv (row-major, double); padded to
+// ntile*BN x nkc*kBK; blocks [tile][chunk][hi, lo] of BN x kBK in the canonical layout.
+std::vector<uint8_t> pack_b(const std::vector<double> &Bm, int Nv, int Kv, int BN, int &ntile, int &nkc) {
+    ntile = (Nv + BN - 1) / BN;
+    nkc = (Kv + kBK - 1) / kBK;
+    const size_t blk = (size_t)BN * kBK * 2;
+    std::vector<uint8_t> out((size_t)ntile * nkc * 2 * blk, 0);
+    for (int t = 0; t < ntile; ++t)
+        for (int kc = 0; kc < nkc; ++kc) {
+            uint8_t *hi = out.data() + ((size_t)t * nkc + kc) * 2 * blk;
+            uint8_t *lo = hi + blk;
+            for (int nl = 0; nl < BN; ++nl) {
+                const int n = t * BN + nl;
+                for (int kl = 0; kl < kBK; ++kl) {
+                    const int k = kc * kBK + kl;
+                    const double v = (n < Nv && k < Kv) ? Bm[(size_t)n * Kv + k] : 0.0;
+                    const uint16_t hb = bf16_bits(v);
+                    const uint16_t lb = bf16_bits(v - bf16_value(hb));
+                    const size_t off = (size_t)(nl / 8) * 1024 + (kl / 8) * 128 + (nl % 8) * 16 + (kl % 8) * 2;
+                    std::memcpy(hi + off, &hb, 2);
+                    std::memcpy(lo + off, &lb, 2);
+                }
+            }
+        }
+    return out;
+}
+
+struct Packed {
+    uint8_t *dev = nullptr;
+    int BN = 0, ntile = 0, nkc = 0;
+};
+
+struct ColState {
+    bool ok = false;
+    // per trajectory: forward / adjoint operands of W (EVF) and W H (full)
+    Packed evf_f[2], evf_a[2], full_f[2], full_a[2];
+    int *rows[2] = {nullptr, nullptr};  // line indices of each trajectory
+    int nrows[2] = {0, 0};
+    int *err = nullptr;
+    int n_par = 1;
+};
+
+ColState *cs(const mpi_ffl_handle *h) { return reinterpret_cast<ColState *>(h->col_state); }
+
+bool upload_packed(Packed &p, const std::vector<uint8_t> &v) {
+    if (cudaMalloc((void **)&p.dev, v.size()) != cudaSuccess) {
+        p.dev = nullptr;
+        return false;
+    }
+    return cudaMemcpy(p.dev, v.data(), v.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+}
+
+size_t smem_for(int BN, int &stages) {
+    const size_t stage = 2u * kBM * kBK * 2 + 2u * BN * kBK * 2;
+    stages = (int)std::min<size_t>(4, (220u * 1024u - 256u) / stage);
+    return stages * stage + 256;
+}
+
+void launch(const mpi_ffl_handle *h, const float *A, int64_t lda, int Ka, const int *arow, int M, const Packed &B,
+            float *C, int64_t ldc, const int *crow, int Nc, const float *rscale, int rdiv, cudaStream_t st) {
+    GemmArgs g{};
+    g.A = A;
+    g.lda = lda;
+    g.arow = arow;
+    g.M = M;
+    g.Ka = Ka;
+    g.B = B.dev;
+    g.BN = B.BN;
+    g.nkc = B.nkc;
+    g.C = C;
+    g.ldc = ldc;
+    g.crow = crow;
+    g.Nc = Nc;
+    g.rscale = rscale;
+    g.rdiv = rdiv;
+    g.prec = h->precision;
+    const size_t smem = smem_for(B.BN, g.stages);
+    g.tmem_cols = B.BN <= 32 ? 32 : B.BN <= 64 ? 64 : B.BN <= 128 ? 128 : 256;
+    g.err = cs(h)->err;
+    dim3 grid((M + kBM - 1) / kBM, B.ntile);
+    k_gemm_split<<<grid, 192, smem, st>>>(g);
+}
+
+}  // namespace
+
+bool col_supported(const mpi_ffl_handle *h) {
+    const ColState *s = cs(h);
+    return s && s->ok;
+}
+
+// W per trajectory (real rows: Re then Im of each kept bin), from the double-precision
+// trajectory; then W H with the PSF taps h(u_lo + e/Q - i).
+void col_init(mpi_ffl_handle *h) {
+    ColState *s = new ColState();
+    h->col_state = s;
+    const Dims &d = h->d;
+    if ((size_t)d.N * 2 * d.nb * 8 > (size_t)1 << 31) return;
+    s->n_par = d.n_par;
+    const double kPi = 3.14159265358979323846;
+    const int R = 2 * d.nb;
+    // PSF matrix H[e][i] in double
+    const double a = h->fwhm / (2.0 * langevin_half_point_host());
+    std::vector<double> Hm((size_t)d.Ne * d.N);
+    for (int e = 0; e < d.Ne; ++e)
+        for (int i = 0; i < d.N; ++i) {
+            const double u = (double)(e - d.D) / d.Q - i;
+            Hm[(size_t)e * d.N + i] = 3.0 * langevin_d1_host(u / a);
+        }
+    // e^{2 pi i k r / S} and e^{2 pi i delta j / L}
+    std::vector<double> ckr(d.S), skr(d.S);
+    for (int m = 0; m < d.S; ++m) {
+        ckr[m] = std::cos(2.0 * kPi * m / d.S);
+        skr[m] = std::sin(2.0 * kPi * m / d.S);
+    }
+    const double isl = 1.0 / std::sqrt((double)d.L);
+    for (int par = 0; par < d.n_par; ++par) {
+        std::vector<double> Wr((size_t)R * d.Ne, 0.0);
+        for (int j = 0; j < d.L; ++j) {
+            int n;
+            double f, v;
+            traj_point_host(h, par, j, n, f, v);
+            const int r = j % d.S;
+            for (int di = 0; di < d.W; ++di) {
+                const int64_t dl = di - d.hw;
+                const int64_t num = ((dl * j) % d.L + d.L) % d.L;
+                const double ang = 2.0 * kPi * (double)num / d.L;
+                const double cd = std::cos(ang), sd = std::sin(ang);
+                for (int k = 0; k < d.K; ++k) {
+                    const int o = k * d.W + di;
+                    const int m = (int)(((int64_t)(d.kmin + k) * r) % d.S);
+                    // e^{2 pi i (kP + delta) j / L} = e^{2 pi i k r / S} e^{2 pi i delta j / L}
+                    const double er = ckr[m] * cd - skr[m] * sd, ei = ckr[m] * sd + skr[m] * cd;
+                    const double gr = h->dgamma[2 * o], gi = h->dgamma[2 * o + 1];
+                    const double wr = (gr * er - gi * ei) * isl, wi = (gr * ei + gi * er) * isl;
+                    const double w0 = (1.0 - f) * v, w1 = f * v;
+                    Wr[(size_t)(2 * o) * d.Ne + n] += w0 * wr;
+                    Wr[(size_t)(2 * o + 1) * d.Ne + n] += w0 * wi;
+                    Wr[(size_t)(2 * o) * d.Ne + n + 1] += w1 * wr;
+                    Wr[(size_t)(2 * o + 1) * d.Ne + n + 1] += w1 * wi;
+                }
+            }
+        }
+        // transposed W (Ne x R), W H (R x N) and its transpose (N x R)
+        std::vector<double> Wt((size_t)d.Ne * R), WH((size_t)R * d.N, 0.0), WHt((size_t)d.N * R);
+        for (int o = 0; o < R; ++o)
+            for (int e = 0; e < d.Ne; ++e) Wt[(size_t)e * R + o] = Wr[(size_t)o * d.Ne + e];
+        for (int o = 0; o < R; ++o) {
+            double *out = WH.data() + (size_t)o * d.N;
+            const double *wrow = Wr.data() + (size_t)o * d.Ne;
+            for (int e = 0; e < d.Ne; ++e) {
+                const double w = wrow[e];
+                if (w == 0.0) continue;
+                const double *hrow = Hm.data() + (size_t)e * d.N;
+                for (int i = 0; i < d.N; ++i) out[i] += w * hrow[i];
+            }
+        }
+        for (int o = 0; o < R; ++o)
+            for (int i = 0; i < d.N; ++i) WHt[(size_t)i * R + o] = WH[(size_t)o * d.N + i];
+        auto mk = [&](Packed &p, const std::vector<double> &m, int Nv, int Kv, int BN) {
+            p.BN = BN;
+            return upload_packed(p, pack_b(m, Nv, Kv, BN, p.ntile, p.nkc));
+        };
+        const int bnf = R <= 256 ? (R + 15) / 16 * 16 : 144;
+        if (!mk(s->evf_f[par], Wr, R, d.Ne, bnf) || !mk(s->evf_a[par], Wt, d.Ne, R, 256) ||
+            !mk(s->full_f[par], WH, R, d.N, bnf) || !mk(s->full_a[par], WHt, d.N, R, d.N <= 256 ? (d.N + 15) / 16 * 16 : 256))
+            return;
+        // lines of this trajectory
+        std::vector<int> rows;
+        for (int m = 0; m < d.M; ++m)
+            for (int z = 0; z < d.Nz; ++z)
+                if ((d.n_par == 1 ? 0 : (z & 1)) == par) rows.push_back(m * d.Nz + z);
+        s->nrows[par] = (int)rows.size();
+        if (cudaMalloc((void **)&s->rows[par], rows.size() * sizeof(int)) != cudaSuccess) return;
+        cudaMemcpy(s->rows[par], rows.data(), rows.size() * sizeof(int), cudaMemcpyHostToDevice);
+    }
+    if (cudaMalloc((void **)&s->err, sizeof(int)) != cudaSuccess) return;
+    cudaMemset(s->err, 0, sizeof(int));
+    cudaFuncSetAttribute(k_gemm_split, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaGetLastError();
+    s->ok = true;
+}
+
+void col_release(mpi_ffl_handle *h) {
+    ColState *s = cs(h);
+    if (!s) return;
+    for (int p = 0; p < 2; ++p) {
+        for (Packed *pk : {&s->evf_f[p], &s->evf_a[p], &s->full_f[p], &s->full_a[p]})
+            if (pk->dev) cudaFree(pk->dev);
+        if (s->rows[p]) cudaFree(s->rows[p]);
+    }
+    if (s->err) cudaFree(s->err);
+    delete s;
+    h->col_state = nullptr;
+}
+
+int col_take_error(mpi_ffl_handle *h) {
+    ColState *s = cs(h);
+    if (!s || !s->err) return 0;
+    int v = 0;
+    cudaMemcpy(&v, s->err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (v) cudaMemset(s->err, 0, sizeof(int));
+    return v;
+}
+
+// fine -> data (W) or proj -> data (W H), gain per line
+void col_forward(mpi_ffl_handle *h, const float *in, bool full, const float *gain, float *data, cudaStream_t st) {
+    ColState *s = cs(h);
+    const Dims &d = h->d;
+    for (int par = 0; par < s->n_par; ++par) {
+        const Packed &B = full ? s->full_f[par] : s->evf_f[par];
+        launch(h, in, full ? d.N : d.Ne, full ? d.N : d.Ne, s->rows[par], s->nrows[par], B, data, 2 * d.nb,
+               s->rows[par], 2 * d.nb, gain, d.Nz, st);
+    }
+}
+
+// data -> fine (W^T) or data -> proj ((W H)^T), gain per line
+void col_adjoint(mpi_ffl_handle *h, const float *data, bool full, const float *gain, float *out, cudaStream_t st) {
+    ColState *s = cs(h);
+    const Dims &d = h->d;
+    for (int par = 0; par < s->n_par; ++par) {
+        const Packed &B = full ? s->full_a[par] : s->evf_a[par];
+        const int nout = full ? d.N : d.Ne;
+        launch(h, data, 2 * d.nb, 2 * d.nb, s->rows[par], s->nrows[par], B, out, nout, s->rows[par], nout, gain,
+               d.Nz, st);
+    }
+}
+
+}  // namespace mpiffl

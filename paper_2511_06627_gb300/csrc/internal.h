@@ -80,6 +80,9 @@ struct mpi_ffl_handle {
     float *t_htab = nullptr;       // PSF taps
     float *t_dhtab = nullptr;      // d h / d fwhm taps
     mpiffl::TrajEntry *t_traj = nullptr;  // n_par * L
+    int2 *t_tnf = nullptr;                // n_par * L: (cell n, fraction f as float bits)
+    std::vector<int> traj_n;              // host copy of the cells n, n_par * L
+    float *t_vr = nullptr;                // n_par * S: velocity v_j, which depends on j mod S only
     int *t_csr_ptr = nullptr;             // n_par * (Ne + 1)
     mpiffl::CsrEntry *t_csr = nullptr;    // n_par * 2L
     float *t_tw1 = nullptr;               // P * W: cos(2 pi d p / P) d=0..hw, sin d=1..hw
@@ -118,6 +121,8 @@ struct mpi_ffl_handle {
     // tensor-core path state (tc.cu)
     void *tc_twb = nullptr;
     void *tc_state = nullptr;
+    void *col_state = nullptr;  // collapsed line operator (collapsed.cu)
+    int path = 0;               // MPI_FFL_PATH_*
     int64_t bytes = 0;
 };
 

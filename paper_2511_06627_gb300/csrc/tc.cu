@@ -34,8 +34,8 @@ namespace mpiffl {
 namespace {
 
 constexpr int kTcMaxSeg = 8;       // lines per job
-constexpr int kFwdThreads = 128;   // one thread per MMA row
-constexpr int kAdjThreads = 256;
+constexpr int kFwdThreads = 512;   // 4 threads per MMA row
+constexpr int kAdjThreads = 512;   // 4 TMEM lane quadrants x 4 period groups
 constexpr int kAdjChunk = 128;     // periods per adjoint MMA (M)
 constexpr uint32_t kWaitLimit = 1u << 24;
 
@@ -55,9 +55,12 @@ struct TcCfg {
     int ncols_adj;  // MMA N of the adjoint = nseg_adj * S
     uint32_t tmem_fwd, tmem_adj;
     // forward shared-memory carve-up (bytes)
-    uint32_t f_fine, f_B, f_A, f_tw, f_bar, f_total;
+    uint32_t f_fine, f_B, f_A, f_tw, f_T, f_bar, f_total;
     // adjoint carve-up
-    uint32_t a_fine, a_A, a_B, a_tw, a_y, a_bar, a_total;
+    uint32_t a_fine, a_A, a_B, a_tw, a_y, a_coef, a_win, a_bar, a_total;
+    int win_len;    // floats per warp window in the adjoint
+    int wide_step;  // cells of one r move by >= 2 per period: n and n+1 updates never collide
+    uint32_t a_vr;
     int prec;
 };
 
@@ -69,6 +72,8 @@ struct TcState {
     uint8_t *twA = nullptr;   // adjoint A operand (hi, lo)
     float2 *tw2 = nullptr;    // [S] e^{2 pi i m / S}, then [W][S] e^{2 pi i d r / L}
     int *err = nullptr;
+    int *wbase = nullptr;   // adjoint window base cell per (trajectory, 32-period block)
+    int n_sm = 1;
     bool ok = false;
 };
 
@@ -105,21 +110,291 @@ __device__ __forceinline__ void split8(const float (&v)[8], uint4 &hi, uint4 &lo
 
 // ============================================================================ forward
 
-__global__ void __launch_bounds__(kFwdThreads, 1)
-    k_tc_fwd(const float *__restrict__ fine, const TrajEntry *__restrict__ traj, const float *__restrict__ gain,
-             const TcJob *__restrict__ jobs, const uint8_t *__restrict__ twB, const float2 *__restrict__ tw2,
-             const float2 *__restrict__ dgam, float *__restrict__ data, Dims d, TcCfg c, int *err) {
+// bf16 hi/lo split of 8 floats, two at a time: hi = bf16(v), lo = bf16(v - hi).
+__device__ __forceinline__ void split8x2(const float (&v)[8], uint4 &hi, uint4 &lo) {
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        __nv_bfloat162 h2 = __float22bfloat162_rn(make_float2(v[2 * i], v[2 * i + 1]));
+        const uint32_t hb = *reinterpret_cast<uint32_t *>(&h2);
+        const float h0 = __uint_as_float(hb << 16), h1 = __uint_as_float(hb & 0xFFFF0000u);
+        __nv_bfloat162 l2 = __float22bfloat162_rn(make_float2(v[2 * i] - h0, v[2 * i + 1] - h1));
+        h[i] = hb;
+        l[i] = *reinterpret_cast<uint32_t *>(&l2);
+    }
+    hi = make_uint4(h[0], h[1], h[2], h[3]);
+    lo = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+// Persistent: each block loops over jobs. Warps 0..15 produce the A operand (row =
+// tid % 128 of the MMA tile, part = tid / 128 selects the 8-period groups of a stage)
+// and run the epilogue; warp 16 only issues the MMAs. Stage handoff uses mbarriers:
+// full[st] (one arrival per producer warp) and empty[st] (MMA completion), so
+// producers never wait for the MMA issue. Fine rows are staged as c[n] and
+// c[n+1] - c[n], so a sample is s = g v (c[n] + f (c[n+1] - c[n])).
+__global__ void __launch_bounds__(kFwdThreads + 32, 1)
+    k_tc_fwd(const float *__restrict__ fine, const int2 *__restrict__ tnf, const float *__restrict__ vr,
+             const float *__restrict__ gain, const TcJob *__restrict__ jobs, int njobs,
+             const uint8_t *__restrict__ twB, const float2 *__restrict__ tw2, const float2 *__restrict__ dgam,
+             float *__restrict__ data, Dims d, TcCfg c, int *err) {
     extern __shared__ __align__(128) uint8_t sm[];
-    const TcJob job = jobs[blockIdx.x];
-    float *sfine = reinterpret_cast<float *>(sm + c.f_fine);
+    float *sf0 = reinterpret_cast<float *>(sm + c.f_fine);
+    float *sf1 = sf0 + c.G * c.spt * c.ne_pad;
     uint8_t *sB = sm + c.f_B;
     uint8_t *sA = sm + c.f_A;
     float2 *stw = reinterpret_cast<float2 *>(sm + c.f_tw);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + c.f_bar);
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + c.f_bar + 16);
-    const int tid = threadIdx.x, warp = tid >> 5;
+    float *sT = reinterpret_cast<float *>(sm + c.f_T);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + c.f_bar);  // full[2], empty[2], done
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + c.f_bar + 48);
+    int *sflag = reinterpret_cast<int *>(sm + c.f_bar + 52);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int S = d.S;
     const int nsegc = c.G * c.spt;
+    const int nprod_warps = kFwdThreads / 32;
+    const bool mma_warp = warp == nprod_warps;
+
+    if (tid == 0) {
+        for (int i = 0; i < 2; ++i) {
+            ptx::mbar_init(&bars[i], nprod_warps);  // full
+            ptx::mbar_init(&bars[2 + i], 1);        // empty
+        }
+        ptx::mbar_init(&bars[4], 1);                // done
+        ptx::fence_mbar_init();
+        *sflag = 0;
+    }
+    if (warp == 0) {
+        ptx::tmem_alloc(tslot, c.tmem_fwd);
+        ptx::tmem_relinquish();
+    }
+    {
+        const uint4 *src = reinterpret_cast<const uint4 *>(twB);
+        uint4 *dst = reinterpret_cast<uint4 *>(sB);
+        const int n16 = (64 * d.P) / 16;
+        for (int i = tid; i < n16; i += blockDim.x) dst[i] = __ldg(src + i);
+        for (int i = tid; i < S + d.W * S; i += blockDim.x) stw[i] = __ldg(tw2 + i);
+    }
+    ptx::fence_proxy_async_smem();
+    ptx::tc_fence_before();
+    __syncthreads();
+    ptx::tc_fence_after();
+    const uint32_t tmem = *tslot;
+    const int nchunks = d.P / c.Kc;
+    const uint32_t tileA = 128u * c.Kc * 2u;
+    const uint32_t stageA = tileA * 2u * c.G;
+    const uint32_t sboA = (c.Kc / 8) * 128u;
+
+    if (mma_warp) {
+        // ---------------------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            const uint32_t sboB = (d.P / 8) * 128u;
+            const uint32_t halfB = 32u * d.P;
+            const uint32_t idesc = ptx::instr_desc(1, 128, 16);
+            uint32_t it = 0;
+            bool ok = true;
+            for (int jb = blockIdx.x; jb < njobs && ok; jb += gridDim.x) {
+                for (int q = 0; q < nchunks; ++q, ++it) {
+                    const int st = it & 1;
+                    if (!ptx::mbar_wait_bounded(&bars[st], (it >> 1) & 1, kWaitLimit)) {
+                        ok = false;
+                        break;
+                    }
+                    ptx::tc_fence_after();
+                    const uint8_t *A = sA + st * stageA;
+                    for (int g = 0; g < c.G; ++g) {
+                        const uint32_t ahi = ptx::smem_u32(A + (2 * g) * tileA);
+                        const uint32_t alo = ptx::smem_u32(A + (2 * g + 1) * tileA);
+                        for (int ks = 0; ks < c.Kc / 16; ++ks) {
+                            const uint32_t kg = q * c.Kc + ks * 16;
+                            const uint64_t dAh = ptx::smem_desc(ahi + ks * 256, 128, sboA);
+                            const uint64_t dAl = ptx::smem_desc(alo + ks * 256, 128, sboA);
+                            const uint64_t dBh = ptx::smem_desc(ptx::smem_u32(sB) + (kg / 8) * 128, 128, sboB);
+                            const uint64_t dBl = ptx::smem_desc(ptx::smem_u32(sB) + halfB + (kg / 8) * 128, 128, sboB);
+                            const uint32_t dt = tmem + g * 16;
+                            ptx::mma_bf16(dt, dAh, dBh, idesc, (q > 0 || ks > 0) ? 1u : 0u);
+                            if (c.prec == MPI_FFL_PREC_BF16X3) {
+                                ptx::mma_bf16(dt, dAh, dBl, idesc, 1u);
+                                ptx::mma_bf16(dt, dAl, dBh, idesc, 1u);
+                            }
+                        }
+                    }
+                    ptx::mma_commit(&bars[2 + st]);
+                    if (q == nchunks - 1) ptx::mma_commit(&bars[4]);
+                }
+            }
+            if (!ok) atomicExch(sflag, 1);
+        }
+        __syncwarp();
+    } else {
+        // ---------------------------------------------------------------- producers + epilogue
+        const int row = tid & 127, part = tid >> 7, nparts = kFwdThreads / 128;
+        const int sg = row / S, r = row % S;
+        const float inv_sqrt_l = rsqrtf((float)d.L);
+        uint32_t it = 0, njob_done = 0;
+        bool good = true;
+        for (int jb = blockIdx.x; jb < njobs && good; jb += gridDim.x, ++njob_done) {
+            const TcJob job = jobs[jb];
+            for (int sl = 0; sl < nsegc; ++sl) {
+                float *d0 = sf0 + sl * c.ne_pad, *d1 = sf1 + sl * c.ne_pad;
+                if (sl < job.nseg) {
+                    const float *src = fine + (size_t)job.seg[sl] * d.Ne;
+                    for (int e = tid; e < d.Ne - 1; e += kFwdThreads) {
+                        const float c0 = __ldg(src + e), c1 = __ldg(src + e + 1);
+                        d0[e] = c0;
+                        d1[e] = c1 - c0;
+                    }
+                } else {
+                    for (int e = tid; e < d.Ne - 1; e += kFwdThreads) d0[e] = d1[e] = 0.f;
+                }
+            }
+            ptx::named_sync(1, kFwdThreads);
+            const int2 *tr = tnf + (size_t)job.parity * d.L;
+            const float vrow = __ldg(vr + job.parity * S + r);
+            int foff[2];
+            float gl[2];
+#pragma unroll
+            for (int g = 0; g < 2; ++g) {
+                const int sl = g * c.spt + sg;
+                foff[g] = (g < c.G ? sl : 0) * c.ne_pad;
+                gl[g] = (g < c.G && sl < job.nseg) ? __ldg(gain + job.seg[sl] / d.Nz) * vrow : 0.f;
+            }
+            for (int q = 0; q < nchunks; ++q, ++it) {
+                const int st = it & 1;
+                if (it >= 2 && !ptx::mbar_wait_bounded(&bars[2 + st], ((it - 2) >> 1) & 1, kWaitLimit)) {
+                    good = false;
+                    break;
+                }
+                uint8_t *A = sA + st * stageA;
+                for (int p8 = part; p8 < c.Kc / 8; p8 += nparts) {
+                    int n8[8];
+                    float f8[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int2 e = __ldg(tr + (size_t)(q * c.Kc + p8 * 8 + u) * S + r);
+                        n8[u] = e.x;
+                        f8[u] = __int_as_float(e.y);
+                    }
+                    const uint32_t off = (row / 8) * sboA + p8 * 128 + (row % 8) * 16;
+#pragma unroll
+                    for (int g = 0; g < 2; ++g) {
+                        if (g >= c.G) break;
+                        float v[8];
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            const int ix = foff[g] + n8[u];
+                            v[u] = gl[g] * fmaf(f8[u], sf1[ix], sf0[ix]);
+                        }
+                        uint4 hi, lo;
+                        split8x2(v, hi, lo);
+                        *reinterpret_cast<uint4 *>(A + (2 * g) * tileA + off) = hi;
+                        *reinterpret_cast<uint4 *>(A + (2 * g + 1) * tileA + off) = lo;
+                    }
+                }
+                ptx::fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) ptx::mbar_arrive(&bars[st]);
+            }
+            if (!good) break;
+            if (!ptx::mbar_wait_bounded(&bars[4], njob_done & 1, kWaitLimit)) {
+                good = false;
+                break;
+            }
+            ptx::tc_fence_after();
+            if (warp < 4) {
+                for (int g = 0; g < c.G; ++g) {
+                    float v[16];
+                    ptx::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + g * 16, v);
+#pragma unroll
+                    for (int cc = 0; cc < 16; ++cc)
+                        if (cc < d.W) sT[(g * 128 + tid) * d.W + cc] = v[cc];
+                }
+            }
+            ptx::tc_fence_before();
+            ptx::named_sync(1, kFwdThreads);
+            // b[k, d] = D L^-1/2 sum_r T[r, d] e^{2 pi i k r / S} e^{2 pi i d r / L}; the sum over
+            // r is split over the 4 adjacent lanes of a task and added with shuffles
+            const int quarter = tid & 3, rq = S / 4;
+            const int ntask = job.nseg * d.nb;
+            for (int t0 = 0; t0 < ntask; t0 += kFwdThreads / 4) {
+                const int task = t0 + (tid >> 2);
+                const bool act = task < ntask;
+                const int tk = act ? task : 0;
+                const int sl = tk / d.nb, o = tk % d.nb;
+                const int di = o % d.W, dl = di - d.hw, ad = dl < 0 ? -dl : dl;
+                const int kmod = (d.kmin + o / d.W) % S;
+                const float sgn = dl < 0 ? -1.f : 1.f;
+                const float *rowT = sT + ((sl / c.spt) * 128 + (sl % c.spt) * S) * d.W;
+                const float2 *twd = stw + S + di * S;
+                float re = 0.f, im = 0.f;
+                const int r0 = quarter * rq;
+                int idx = (kmod * r0) % S;
+                for (int rr = r0; rr < r0 + rq; ++rr) {
+                    const float tre = rowT[rr * d.W + ad];
+                    const float tim = ad == 0 ? 0.f : sgn * rowT[rr * d.W + d.hw + ad];
+                    const float2 a = stw[idx], b = twd[rr];
+                    const float wr = a.x * b.x - a.y * b.y, wi = a.x * b.y + a.y * b.x;
+                    re = fmaf(tre, wr, fmaf(-tim, wi, re));
+                    im = fmaf(tre, wi, fmaf(tim, wr, im));
+                    idx += kmod;
+                    if (idx >= S) idx -= S;
+                }
+                re += __shfl_xor_sync(0xffffffffu, re, 1);
+                im += __shfl_xor_sync(0xffffffffu, im, 1);
+                re += __shfl_xor_sync(0xffffffffu, re, 2);
+                im += __shfl_xor_sync(0xffffffffu, im, 2);
+                if (act && quarter == 0) {
+                    re *= inv_sqrt_l;
+                    im *= inv_sqrt_l;
+                    const float2 gd = __ldg(dgam + o);
+                    reinterpret_cast<float2 *>(data)[(size_t)job.seg[sl] * d.nb + o] =
+                        make_float2(gd.x * re - gd.y * im, gd.x * im + gd.y * re);
+                }
+            }
+            ptx::named_sync(1, kFwdThreads);  // sT and the fine rows are reused by the next job
+        }
+        if (!good) atomicExch(sflag, 1);
+    }
+    ptx::tc_fence_before();
+    __syncthreads();
+    if (tid == 0 && *sflag) atomicExch(err, 1);
+    if (warp == 0) ptx::tmem_dealloc(tmem, c.tmem_fwd);
+}
+
+// ============================================================================ adjoint
+
+// Persistent. The MMA gives D[p][(line, r)] for a chunk of 128 periods, TMEM lane = p.
+// Warp w reads lanes 32 (w % 4)..+31 (32 consecutive periods) and 64 columns
+// (64 r of one line). At a fixed r the fine-grid cell of a sample is strictly
+// monotone in p (checked on the host), so the 32 lanes of one update touch 32
+// distinct cells: every warp accumulates into its own window of the fine row with
+// plain shared-memory read-modify-writes, and the windows are then added into the
+// line accumulators by cell, in a fixed order (no atomics, deterministic).
+__global__ void __launch_bounds__(kAdjThreads, 1)
+    k_tc_adj(const float *__restrict__ data, const int2 *__restrict__ tnf, const float *__restrict__ vr,
+             const float *__restrict__ gain, const TcJob *__restrict__ jobs, int njobs,
+             const uint8_t *__restrict__ twA, const float2 *__restrict__ tw2, const float2 *__restrict__ dgam,
+             const int *__restrict__ wbase, float *__restrict__ fine, Dims d, TcCfg c, int *err) {
+    extern __shared__ __align__(128) uint8_t sm[];
+    float *sacc = reinterpret_cast<float *>(sm + c.a_fine);
+    uint8_t *sTw = sm + c.a_A;   // Tw: rows p, K = 16 (hi, lo) -- the MMA's A operand
+    uint8_t *sC = sm + c.a_B;    // coefficients: rows (line, r), K = 16 (hi, lo) -- the B operand
+    float2 *stw = reinterpret_cast<float2 *>(sm + c.a_tw);
+    float2 *sy = reinterpret_cast<float2 *>(sm + c.a_y);
+    float *scoef = reinterpret_cast<float *>(sm + c.a_coef);
+    float *swin = reinterpret_cast<float *>(sm + c.a_win);
+    float *svr = reinterpret_cast<float *>(sm + c.a_vr);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + c.a_bar);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + c.a_bar + 16);
+    int *sbase = reinterpret_cast<int *>(sm + c.a_bar + 32);  // window bases of the current chunk
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int S = d.S;
+    const int nsegc = c.nseg_adj;
+    const int ncols = nsegc * S;  // 256
+    const int quad = warp & 3, cgrp = warp >> 2;  // period quadrant, 64-column group
+    const int col0 = cgrp * 64;
+    const int wline = col0 / S;                   // line of this warp's columns
+    const int wstride = c.win_len + (c.win_len >> 5);  // windows are stored with one pad word per 32
+    float *win = swin + warp * wstride;
+    const int nwin_per_line = 4 * (S / 64);       // warps sharing a line
 
     if (tid == 0) {
         ptx::mbar_init(&bars[0], 1);
@@ -127,301 +402,170 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
         ptx::fence_mbar_init();
     }
     if (warp == 0) {
-        ptx::tmem_alloc(tslot, c.tmem_fwd);
-        ptx::tmem_relinquish();
-    }
-    // stage the jobs' fine rows (zero rows for empty slots), the twiddle operand and tables
-    for (int sl = 0; sl < nsegc; ++sl) {
-        float *dst = sfine + sl * c.ne_pad;
-        if (sl < job.nseg) {
-            const float *src = fine + (size_t)job.seg[sl] * d.Ne;
-            for (int e = tid; e < d.Ne; e += kFwdThreads) dst[e] = __ldg(src + e);
-        } else {
-            for (int e = tid; e < d.Ne; e += kFwdThreads) dst[e] = 0.f;
-        }
-    }
-    {
-        const uint4 *src = reinterpret_cast<const uint4 *>(twB);
-        uint4 *dst = reinterpret_cast<uint4 *>(sB);
-        const int n16 = (64 * d.P) / 16;
-        for (int i = tid; i < n16; i += kFwdThreads) dst[i] = __ldg(src + i);
-        for (int i = tid; i < S + d.W * S; i += kFwdThreads) stw[i] = __ldg(tw2 + i);
-    }
-    ptx::tc_fence_before();
-    __syncthreads();
-    ptx::tc_fence_after();
-    const uint32_t tmem = *tslot;
-
-    const int sg = tid / S, r = tid % S;
-    const TrajEntry *tr = traj + (size_t)job.parity * d.L;
-    const float *frow[2];
-    float gl[2];
-#pragma unroll
-    for (int g = 0; g < 2; ++g) {
-        const int sl = g * c.spt + sg;
-        frow[g] = sfine + (g < c.G ? sl : 0) * c.ne_pad;
-        gl[g] = (g < c.G && sl < job.nseg) ? __ldg(gain + job.seg[sl] / d.Nz) : 0.f;
-    }
-    const int nchunks = d.P / c.Kc;
-    const uint32_t tileA = 128u * c.Kc * 2u;  // bytes of one (tile, hi|lo) A buffer
-    const uint32_t stageA = tileA * 2u * c.G;
-    const uint32_t sboA = (c.Kc / 8) * 128u;
-    const uint32_t sboB = (d.P / 8) * 128u;
-    const uint32_t halfB = 32u * d.P;
-    const uint32_t idesc = ptx::instr_desc(1, 128, 16);
-    bool good = true;
-    for (int q = 0; q < nchunks && good; ++q) {
-        const int st = q & 1;
-        if (q >= 2) {
-            const bool w = ptx::mbar_wait_bounded(&bars[st], ((q - 2) >> 1) & 1, kWaitLimit);
-            good = __syncthreads_and(w);
-            if (!good) break;
-        }
-        uint8_t *A = sA + st * stageA;
-        for (int p8 = 0; p8 < c.Kc / 8; ++p8) {
-            TrajEntry te[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) te[u] = load_te(tr + (size_t)(q * c.Kc + p8 * 8 + u) * S + r);
-            const uint32_t off = (tid / 8) * sboA + p8 * 128 + (tid % 8) * 16;
-#pragma unroll
-            for (int g = 0; g < 2; ++g) {
-                if (g >= c.G) break;
-                float v[8];
-#pragma unroll
-                for (int u = 0; u < 8; ++u)
-                    v[u] = gl[g] * fmaf(te[u].w0, frow[g][te[u].n], te[u].w1 * frow[g][te[u].n + 1]);
-                uint4 hi, lo;
-                split8(v, hi, lo);
-                *reinterpret_cast<uint4 *>(A + (2 * g) * tileA + off) = hi;
-                *reinterpret_cast<uint4 *>(A + (2 * g + 1) * tileA + off) = lo;
-            }
-        }
-        ptx::fence_proxy_async_smem();
-        __syncthreads();
-        if (tid == 0) {
-            ptx::tc_fence_after();
-            for (int g = 0; g < c.G; ++g) {
-                const uint32_t ahi = ptx::smem_u32(A + (2 * g) * tileA);
-                const uint32_t alo = ptx::smem_u32(A + (2 * g + 1) * tileA);
-                for (int ks = 0; ks < c.Kc / 16; ++ks) {
-                    const uint32_t kg = q * c.Kc + ks * 16;
-                    const uint64_t dAh = ptx::smem_desc(ahi + ks * 256, 128, sboA);
-                    const uint64_t dAl = ptx::smem_desc(alo + ks * 256, 128, sboA);
-                    const uint64_t dBh = ptx::smem_desc(ptx::smem_u32(sB) + (kg / 8) * 128, 128, sboB);
-                    const uint64_t dBl = ptx::smem_desc(ptx::smem_u32(sB) + halfB + (kg / 8) * 128, 128, sboB);
-                    const uint32_t dt = tmem + g * 16;
-                    ptx::mma_bf16(dt, dAh, dBh, idesc, (q > 0 || ks > 0) ? 1u : 0u);
-                    if (c.prec == MPI_FFL_PREC_BF16X3) {
-                        ptx::mma_bf16(dt, dAh, dBl, idesc, 1u);
-                        ptx::mma_bf16(dt, dAl, dBh, idesc, 1u);
-                    }
-                }
-            }
-            ptx::mma_commit(&bars[st]);
-        }
-    }
-    if (good) {
-        const int ql = nchunks - 1;
-        const bool w = ptx::mbar_wait_bounded(&bars[ql & 1], (ql >> 1) & 1, kWaitLimit);
-        good = __syncthreads_and(w);
-    }
-    ptx::tc_fence_after();
-    if (good) {
-        // T[row][c] from TMEM into shared memory (reusing the A buffers)
-        float *sT = reinterpret_cast<float *>(sA);
-        for (int g = 0; g < c.G; ++g) {
-            float v[16];
-            ptx::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + g * 16, v);
-#pragma unroll
-            for (int cc = 0; cc < 16; ++cc)
-                if (cc < d.W) sT[(g * 128 + tid) * d.W + cc] = v[cc];
-        }
-        ptx::tc_fence_before();
-        __syncthreads();
-        const float inv_sqrt_l = rsqrtf((float)d.L);
-        for (int task = tid; task < job.nseg * d.nb; task += kFwdThreads) {
-            const int sl = task / d.nb, o = task % d.nb;
-            const int di = o % d.W, dl = di - d.hw, ad = dl < 0 ? -dl : dl;
-            const int kmod = (d.kmin + o / d.W) % S;
-            const float sgn = dl < 0 ? -1.f : 1.f;
-            const float *rowT = sT + ((sl / c.spt) * 128 + (sl % c.spt) * S) * d.W;
-            const float2 *twd = stw + S + di * S;
-            float re = 0.f, im = 0.f;
-            int idx = 0;
-            for (int rr = 0; rr < S; ++rr) {
-                const float tre = rowT[rr * d.W + ad];
-                const float tim = ad == 0 ? 0.f : sgn * rowT[rr * d.W + d.hw + ad];
-                const float2 a = stw[idx], b = twd[rr];
-                const float wr = a.x * b.x - a.y * b.y, wi = a.x * b.y + a.y * b.x;
-                re = fmaf(tre, wr, fmaf(-tim, wi, re));
-                im = fmaf(tre, wi, fmaf(tim, wr, im));
-                idx += kmod;
-                if (idx >= S) idx -= S;
-            }
-            re *= inv_sqrt_l;
-            im *= inv_sqrt_l;
-            const float2 gd = __ldg(dgam + o);
-            reinterpret_cast<float2 *>(data)[(size_t)job.seg[sl] * d.nb + o] =
-                make_float2(gd.x * re - gd.y * im, gd.x * im + gd.y * re);
-        }
-    } else if (tid == 0) {
-        atomicExch(err, 1);
-    }
-    ptx::tc_fence_before();
-    __syncthreads();
-    if (warp == 0) ptx::tmem_dealloc(tmem, c.tmem_fwd);
-}
-
-// ============================================================================ adjoint
-
-__device__ __forceinline__ int padx(int e) { return e + (e >> 5); }
-
-__global__ void __launch_bounds__(kAdjThreads, 1)
-    k_tc_adj(const float *__restrict__ data, const TrajEntry *__restrict__ traj, const float *__restrict__ gain,
-             const TcJob *__restrict__ jobs, const uint8_t *__restrict__ twA, const float2 *__restrict__ tw2,
-             const float2 *__restrict__ dgam, float *__restrict__ fine, Dims d, TcCfg c, int *err) {
-    extern __shared__ __align__(128) uint8_t sm[];
-    const TcJob job = jobs[blockIdx.x];
-    float *sacc = reinterpret_cast<float *>(sm + c.a_fine);
-    uint8_t *sA = sm + c.a_A;
-    uint8_t *sB = sm + c.a_B;
-    float2 *stw = reinterpret_cast<float2 *>(sm + c.a_tw);
-    float2 *sy = reinterpret_cast<float2 *>(sm + c.a_y);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + c.a_bar);
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + c.a_bar + 16);
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int S = d.S;
-    const int nsegc = c.nseg_adj;
-    const int ncols = c.ncols_adj;
-
-    if (tid == 0) {
-        ptx::mbar_init(bar, 1);
-        ptx::fence_mbar_init();
-    }
-    if (warp == 0) {
         ptx::tmem_alloc(tslot, c.tmem_adj);
         ptx::tmem_relinquish();
     }
-    for (int i = tid; i < nsegc * c.ne_adj; i += kAdjThreads) sacc[i] = 0.f;
     {
         const uint4 *src = reinterpret_cast<const uint4 *>(twA);
-        uint4 *dst = reinterpret_cast<uint4 *>(sA);
+        uint4 *dst = reinterpret_cast<uint4 *>(sTw);
         const int n16 = (64 * d.P) / 16;
         for (int i = tid; i < n16; i += kAdjThreads) dst[i] = __ldg(src + i);
         for (int i = tid; i < S + d.W * S; i += kAdjThreads) stw[i] = __ldg(tw2 + i);
     }
-    const float inv_sqrt_l = rsqrtf((float)d.L);
-    for (int i = tid; i < nsegc * d.nb; i += kAdjThreads) {
-        const int sl = i / d.nb, o = i % d.nb;
-        float2 y = make_float2(0.f, 0.f);
-        if (sl < job.nseg) {
-            const float2 v = reinterpret_cast<const float2 *>(data)[(size_t)job.seg[sl] * d.nb + o];
-            const float2 g = __ldg(dgam + o);
-            y = make_float2((g.x * v.x + g.y * v.y) * inv_sqrt_l, (g.x * v.y - g.y * v.x) * inv_sqrt_l);
-        }
-        sy[i] = y;
-    }
-    __syncthreads();
-    // per column n = (line, r): U[d] = sum_k y'[k, d] conj(e^{2 pi i k r/S} e^{2 pi i d r/L}),
-    // coefficients A_0 = Re U[0], A_d = Re U[d] + Re U[-d], B_d = Im U[d] - Im U[-d]
-    for (int n = tid; n < ncols; n += kAdjThreads) {
-        const int sl = n / S, rr = n % S;
-        float ur[2 * kMaxHw + 1], ui[2 * kMaxHw + 1];
-#pragma unroll
-        for (int di = 0; di < 2 * kMaxHw + 1; ++di) ur[di] = ui[di] = 0.f;
-        for (int k = 0; k < d.K; ++k) {
-            const float2 a = stw[((d.kmin + k) % S) * rr % S];
-#pragma unroll
-            for (int di = 0; di < 2 * kMaxHw + 1; ++di) {
-                if (di >= d.W) break;
-                const float2 b = stw[S + di * S + rr];
-                const float wr = a.x * b.x - a.y * b.y, wi = a.x * b.y + a.y * b.x;  // e^{+i phi}
-                const float2 y = sy[sl * d.nb + k * d.W + di];
-                // y * e^{-i phi}
-                ur[di] = fmaf(y.x, wr, fmaf(y.y, wi, ur[di]));
-                ui[di] = fmaf(y.y, wr, fmaf(-y.x, wi, ui[di]));
-            }
-        }
-        float coef[16];
-#pragma unroll
-        for (int cc = 0; cc < 16; ++cc) coef[cc] = 0.f;
-        coef[0] = ur[d.hw];
-        for (int a = 1; a <= d.hw; ++a) {
-            coef[a] = ur[d.hw + a] + ur[d.hw - a];
-            coef[d.hw + a] = ui[d.hw + a] - ui[d.hw - a];
-        }
-        for (int h = 0; h < 2; ++h) {
-            float v[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) v[u] = coef[h * 8 + u];
-            uint4 hi4, lo4;
-            split8(v, hi4, lo4);
-            const uint32_t off = canon_off(n, h * 8, 256);
-            *reinterpret_cast<uint4 *>(sB + off) = hi4;
-            *reinterpret_cast<uint4 *>(sB + (uint32_t)ncols * 32u + off) = lo4;
-        }
-    }
-    ptx::fence_proxy_async_smem();
     ptx::tc_fence_before();
     __syncthreads();
     ptx::tc_fence_after();
     const uint32_t tmem = *tslot;
-    const TrajEntry *tr = traj + (size_t)job.parity * d.L;
     const uint32_t idesc = ptx::instr_desc(1, 128, (uint32_t)ncols);
-    const uint32_t halfA = 32u * d.P;
-    const uint32_t halfB = (uint32_t)ncols * 32u;
+    const uint32_t halfTw = 32u * d.P;
+    const uint32_t halfC = (uint32_t)ncols * 32u;
     const int nchunks = d.P / kAdjChunk;
-    const int quad = warp & 3, colhalf = warp >> 2;
-    const int seg_lo = colhalf * (nsegc / 2), seg_hi = (colhalf + 1) * (nsegc / 2);
+    const float inv_sqrt_l = rsqrtf((float)d.L);
+    uint32_t it = 0;  // MMA batches committed by this block
     bool good = true;
-    for (int q = 0; q < nchunks; ++q) {
-        if (tid == 0) {
-            ptx::tc_fence_after();
-            const uint32_t a0 = ptx::smem_u32(sA) + q * (kAdjChunk * 16 * 2);
-            const uint64_t dAh = ptx::smem_desc(a0, 128, 256);
-            const uint64_t dAl = ptx::smem_desc(a0 + halfA, 128, 256);
-            const uint64_t dBh = ptx::smem_desc(ptx::smem_u32(sB), 128, 256);
-            const uint64_t dBl = ptx::smem_desc(ptx::smem_u32(sB) + halfB, 128, 256);
-            ptx::mma_bf16(tmem, dAh, dBh, idesc, 0u);
-            if (c.prec == MPI_FFL_PREC_BF16X3) {
-                ptx::mma_bf16(tmem, dAh, dBl, idesc, 1u);
-                ptx::mma_bf16(tmem, dAl, dBh, idesc, 1u);
-            }
-            ptx::mma_commit(bar);
-        }
-        const bool w = ptx::mbar_wait_bounded(bar, q & 1, kWaitLimit);
-        good = __syncthreads_and(w);
-        if (!good) break;
+
+    auto issue = [&](int q, int buf) {  // D[buf] = Tw(chunk q) x C^T
         ptx::tc_fence_after();
-        const int p = q * kAdjChunk + quad * 32 + lane;  // this thread's period
-        for (int rb = 0; rb < S; rb += 16) {
-            TrajEntry te[16];
-#pragma unroll
-            for (int u = 0; u < 16; ++u) te[u] = load_te(tr + (size_t)p * S + rb + u);
-            for (int sl = seg_lo; sl < seg_hi; ++sl) {
-                float v[16];
-                ptx::tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(sl * S + rb), v);
-                float *acc = sacc + sl * c.ne_adj;
-#pragma unroll
-                for (int u = 0; u < 16; ++u) {
-                    atomicAdd(acc + padx(te[u].n), te[u].w0 * v[u]);
-                    atomicAdd(acc + padx(te[u].n + 1), te[u].w1 * v[u]);
+        const uint32_t a0 = ptx::smem_u32(sTw) + q * (kAdjChunk * 16 * 2);
+        const uint64_t dAh = ptx::smem_desc(a0, 128, 256);
+        const uint64_t dAl = ptx::smem_desc(a0 + halfTw, 128, 256);
+        const uint64_t dBh = ptx::smem_desc(ptx::smem_u32(sC), 128, 256);
+        const uint64_t dBl = ptx::smem_desc(ptx::smem_u32(sC) + halfC, 128, 256);
+        const uint32_t dt = tmem + (uint32_t)(buf * ncols);
+        ptx::mma_bf16(dt, dAh, dBh, idesc, 0u);
+        if (c.prec == MPI_FFL_PREC_BF16X3) {
+            ptx::mma_bf16(dt, dAh, dBl, idesc, 1u);
+            ptx::mma_bf16(dt, dAl, dBh, idesc, 1u);
+        }
+        ptx::mma_commit(&bars[buf]);
+    };
+
+    for (int jb = blockIdx.x; jb < njobs && good; jb += gridDim.x) {
+        const TcJob job = jobs[jb];
+        for (int i = tid; i < nsegc * d.Ne; i += kAdjThreads) sacc[i] = 0.f;
+        for (int i = tid; i < nsegc * d.nb; i += kAdjThreads) {
+            const int sl = i / d.nb, o = i % d.nb;
+            float2 y = make_float2(0.f, 0.f);
+            if (sl < job.nseg) {
+                const float2 v = reinterpret_cast<const float2 *>(data)[(size_t)job.seg[sl] * d.nb + o];
+                const float2 g = __ldg(dgam + o);
+                y = make_float2((g.x * v.x + g.y * v.y) * inv_sqrt_l, (g.x * v.y - g.y * v.x) * inv_sqrt_l);
+            }
+            sy[i] = y;
+        }
+        __syncthreads();
+        // coefficients of column (line, r): U[d] = sum_k y'[k,d] e^{-2 pi i (kP+d) r / L};
+        // c_0 = Re U[0], c_d = Re U[d] + Re U[-d], c_{w+d} = Im U[d] - Im U[-d]
+        for (int n = tid; n < ncols; n += kAdjThreads) {
+            const int sl = n / S, rr = n % S;
+            float *cf = scoef + n * 16;
+            for (int cc = 0; cc < 16; ++cc) cf[cc] = 0.f;
+            const float2 *yl = sy + sl * d.nb;
+            for (int a = 0; a <= d.hw; ++a) {
+                float ur_p = 0.f, ui_p = 0.f, ur_m = 0.f, ui_m = 0.f;
+                const float2 bp = stw[S + (d.hw + a) * S + rr], bm = stw[S + (d.hw - a) * S + rr];
+                for (int k = 0; k < d.K; ++k) {
+                    const float2 e = stw[((d.kmin + k) % S) * rr % S];
+                    const float wpr = e.x * bp.x - e.y * bp.y, wpi = e.x * bp.y + e.y * bp.x;
+                    const float wmr = e.x * bm.x - e.y * bm.y, wmi = e.x * bm.y + e.y * bm.x;
+                    const float2 yp = yl[k * d.W + d.hw + a], ym = yl[k * d.W + d.hw - a];
+                    ur_p = fmaf(yp.x, wpr, fmaf(yp.y, wpi, ur_p));
+                    ui_p = fmaf(yp.y, wpr, fmaf(-yp.x, wpi, ui_p));
+                    ur_m = fmaf(ym.x, wmr, fmaf(ym.y, wmi, ur_m));
+                    ui_m = fmaf(ym.y, wmr, fmaf(-ym.x, wmi, ui_m));
+                }
+                if (a == 0) {
+                    cf[0] = ur_p;
+                } else {
+                    cf[a] = ur_p + ur_m;
+                    cf[d.hw + a] = ui_p - ui_m;
                 }
             }
+            for (int h = 0; h < 2; ++h) {
+                float v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) v[u] = cf[h * 8 + u];
+                uint4 hi4, lo4;
+                split8x2(v, hi4, lo4);
+                const uint32_t off = canon_off(n, h * 8, 256);
+                *reinterpret_cast<uint4 *>(sC + off) = hi4;
+                *reinterpret_cast<uint4 *>(sC + halfC + off) = lo4;
+            }
         }
+        ptx::fence_proxy_async_smem();
         ptx::tc_fence_before();
         __syncthreads();
-    }
-    if (good) {
+        if (tid == 0) {
+            issue(0, it & 1);
+            if (nchunks > 1) issue(1, (it + 1) & 1);
+        }
+        const int2 *tr = tnf + (size_t)job.parity * d.L;
+        const int *wb = wbase + job.parity * (d.P / 32);
+        for (int i = tid; i < S; i += kAdjThreads) svr[i] = __ldg(vr + job.parity * S + i);
+        for (int q = 0; q < nchunks; ++q) {
+            const uint32_t b = (it + q) & 1;
+            for (int i = lane; i < wstride; i += 32) win[i] = 0.f;
+            if (tid < 4) sbase[tid] = __ldg(wb + q * 4 + tid);
+            const int p = q * kAdjChunk + quad * 32 + lane;  // this lane's period
+            const int base = __ldg(wb + q * 4 + quad);
+            const bool w = ptx::mbar_wait_bounded(&bars[b], ((it + q) >> 1) & 1, kWaitLimit);
+            good = __syncthreads_and(w);
+            if (!good) break;
+            ptx::tc_fence_after();
+            for (int cb = 0; cb < 64; cb += 16) {
+                const int rr0 = (col0 + cb) % S;
+                const int4 *te = reinterpret_cast<const int4 *>(tr + (size_t)p * S + rr0);
+                int n16[16];
+                float f16[16];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int4 e = __ldg(te + u);
+                    n16[2 * u] = e.x - base;
+                    f16[2 * u] = __int_as_float(e.y);
+                    n16[2 * u + 1] = e.z - base;
+                    f16[2 * u + 1] = __int_as_float(e.w);
+                }
+                float v[16];
+                ptx::tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * ncols + col0 + cb), v);
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    const float vs = svr[rr0 + u] * v[u];
+                    const float hv = f16[u] * vs;  // f v s -> cell n + 1
+                    const int i0 = n16[u] + (n16[u] >> 5), i1 = (n16[u] + 1) + ((n16[u] + 1) >> 5);
+                    win[i0] += vs - hv;            // (1 - f) v s -> cell n
+                    if (!c.wide_step) __syncwarp();
+                    win[i1] += hv;
+                    __syncwarp();
+                }
+            }
+            ptx::tc_fence_before();
+            __syncthreads();
+            if (tid == 0 && q + 2 < nchunks) issue(q + 2, b);
+            // add the windows into the line accumulators, cell by cell, warps in order
+            for (int i = tid; i < nsegc * d.Ne; i += kAdjThreads) {
+                const int sl = i / d.Ne, e = i % d.Ne;
+                float add = 0.f;
+                for (int k = 0; k < nwin_per_line; ++k) {
+                    // warps of line sl: column groups cg with cg*64/S == sl, all 4 quadrants
+                    const int cg = sl * (S / 64) + k / 4, qd = k % 4;
+                    const int off = e - sbase[qd];
+                    if (off >= 0 && off < c.win_len) add += swin[(cg * 4 + qd) * wstride + off + (off >> 5)];
+                }
+                sacc[i] += add;
+            }
+            __syncthreads();
+        }
+        if (!good) break;
+        it += nchunks;
         for (int sl = 0; sl < job.nseg; ++sl) {
             const float g = __ldg(gain + job.seg[sl] / d.Nz);
             float *dst = fine + (size_t)job.seg[sl] * d.Ne;
-            const float *acc = sacc + sl * c.ne_adj;
-            for (int e = tid; e < d.Ne; e += kAdjThreads) dst[e] = g * acc[padx(e)];
+            const float *acc = sacc + sl * d.Ne;
+            for (int e = tid; e < d.Ne; e += kAdjThreads) dst[e] = g * acc[e];
         }
-    } else if (tid == 0) {
-        atomicExch(err, 1);
+        __syncthreads();
     }
+    if (!good && tid == 0) atomicExch(err, 1);
     ptx::tc_fence_before();
     __syncthreads();
     if (warp == 0) ptx::tmem_dealloc(tmem, c.tmem_adj);
@@ -437,36 +581,38 @@ uint32_t pow2_cols(int n) {
     return c;
 }
 
-bool plan(const Dims &d, TcCfg &c) {
-    if (d.S > 128 || 128 % d.S != 0 || d.S % 16 != 0) return false;  // lines tile 128 MMA rows
+bool plan(const Dims &d, TcCfg &c, int win_len) {
+    if (d.S > 128 || 128 % d.S != 0 || d.S % 64 != 0) return false;  // S in {64, 128}
     if (d.W > 16) return false;                                      // twiddle columns fit N = 16
     if (d.P % kAdjChunk != 0) return false;                          // adjoint period chunks
     c.spt = 128 / d.S;
-    c.Kc = (d.P % 64 == 0) ? 64 : 32;
-    c.G = c.spt >= 2 ? 1 : 2;  // two lines per forward job either way
+    c.Kc = 64;
+    c.G = 2;  // 128-row tiles per forward job
     if (c.spt * c.G > kTcMaxSeg) return false;
     c.ne_pad = (d.Ne + 3) / 4 * 4;
     c.tmem_fwd = pow2_cols(c.G * 16);
     uint32_t o = 0;
     c.f_fine = o;
-    o = align_up(o + 4u * c.ne_pad * c.G * c.spt, 128);
+    o = align_up(o + 8u * c.ne_pad * c.G * c.spt, 128);  // c[n] and c[n+1]-c[n] arrays
     c.f_B = o;
     o = align_up(o + 64u * d.P, 128);
     c.f_A = o;
     o = align_up(o + 2u * 2u * c.G * 128u * c.Kc * 2u, 128);
     c.f_tw = o;
     o = align_up(o + 8u * (d.S + d.W * d.S), 128);
+    c.f_T = o;
+    o = align_up(o + 4u * c.G * 128u * d.W, 128);
     c.f_bar = o;
     c.f_total = o + 64;
-    // adjoint: 256 MMA columns of (line, r)
+    // adjoint: 256 MMA columns (line, r), two D buffers
     c.nseg_adj = 256 / d.S;
-    if (c.nseg_adj > kTcMaxSeg || c.nseg_adj < 2) return false;
     c.ncols_adj = c.nseg_adj * d.S;
-    c.tmem_adj = pow2_cols(c.ncols_adj);
-    c.ne_adj = d.Ne + (d.Ne >> 5) + 2;
+    c.tmem_adj = pow2_cols(2 * c.ncols_adj);
+    if (c.tmem_adj > 512) return false;
+    c.win_len = win_len;
     o = 0;
     c.a_fine = o;
-    o = align_up(o + 4u * c.ne_adj * c.nseg_adj, 128);
+    o = align_up(o + 4u * d.Ne * c.nseg_adj, 128);
     c.a_A = o;
     o = align_up(o + 64u * d.P, 128);
     c.a_B = o;
@@ -475,9 +621,14 @@ bool plan(const Dims &d, TcCfg &c) {
     o = align_up(o + 8u * (d.S + d.W * d.S), 128);
     c.a_y = o;
     o = align_up(o + 8u * c.nseg_adj * d.nb, 128);
+    c.a_coef = o;
+    o = align_up(o + 4u * 16u * c.ncols_adj, 128);
+    c.a_win = o;
+    o = align_up(o + 4u * (uint32_t)(win_len + (win_len >> 5)) * (kAdjThreads / 32), 128);
+    c.a_vr = o;
+    o = align_up(o + 4u * d.S, 128);
     c.a_bar = o;
-    // at least 80 KiB so that at most two blocks (2 x 256 TMEM columns) share an SM
-    c.a_total = std::max<uint32_t>(o + 64, 80u * 1024u);
+    c.a_total = o + 64;
     return c.f_total <= 227 * 1024 && c.a_total <= 227 * 1024;
 }
 
@@ -515,8 +666,44 @@ void tc_init(mpi_ffl_handle *h) {
     TcState *s = new TcState();
     h->tc_state = s;
     const Dims &d = h->d;
-    if (!plan(d, s->cfg)) return;
+    // adjoint windows: per trajectory and block of 32 periods, the smallest fine cell
+    // touched (any r); the window must hold every cell of the block, and the cell of
+    // a fixed r must move strictly monotonically with the period (distinct lanes)
+    const std::vector<int> &tn = h->traj_n;
+    if ((int64_t)tn.size() != (int64_t)d.n_par * d.L || d.P % 32 != 0) return;
+    std::vector<int> wb((size_t)d.n_par * (d.P / 32));
+    int span = 0, min_step = 1 << 30;
+    bool monotone = true;
+    for (int par = 0; par < d.n_par; ++par) {
+        const int *n = tn.data() + (size_t)par * d.L;
+        for (int b = 0; b < d.P / 32; ++b) {
+            int lo = 1 << 30, hi = -1;
+            for (int p = 32 * b; p < 32 * b + 32; ++p)
+                for (int r = 0; r < d.S; ++r) {
+                    lo = std::min(lo, n[(size_t)p * d.S + r]);
+                    hi = std::max(hi, n[(size_t)p * d.S + r]);
+                }
+            wb[(size_t)par * (d.P / 32) + b] = lo;
+            span = std::max(span, hi + 2 - lo);
+        }
+        for (int r = 0; r < d.S && monotone; ++r) {
+            const int dir = n[(size_t)d.S + r] - n[r];
+            for (int p = 0; p + 1 < d.P; ++p) {
+                const int st = n[(size_t)(p + 1) * d.S + r] - n[(size_t)p * d.S + r];
+                min_step = std::min(min_step, st < 0 ? -st : st);
+                if (st == 0 || (st > 0) != (dir > 0)) {
+                    monotone = false;
+                    break;
+                }
+            }
+        }
+    }
+    const int win_len = (span + 31) / 32 * 32;
+    if (!monotone || win_len > 2048) return;
+    if (!plan(d, s->cfg, win_len)) return;
     TcCfg &c = s->cfg;
+    c.wide_step = min_step >= 2 ? 1 : 0;
+    upload_vec(&s->wbase, wb);
     const double kPi = 3.14159265358979323846;
     // twiddle columns: c = d (cos, d = 0..w) and c = w + d (sin, d = 1..w)
     auto tw = [&](int p, int col) -> double {
@@ -586,7 +773,10 @@ void tc_init(mpi_ffl_handle *h) {
     upload_vec(&s->jobs_adj, ja);
     cudaMalloc((void **)&s->err, sizeof(int));
     if (s->err) cudaMemset(s->err, 0, sizeof(int));
-    if (!s->twB || !s->twA || !s->tw2 || !s->jobs_fwd || !s->jobs_adj || !s->err) return;
+    if (!s->twB || !s->twA || !s->tw2 || !s->jobs_fwd || !s->jobs_adj || !s->err || !s->wbase) return;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&s->n_sm, cudaDevAttrMultiProcessorCount, dev);
     cudaFuncSetAttribute(k_tc_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.f_total);
     cudaFuncSetAttribute(k_tc_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.a_total);
     cudaGetLastError();
@@ -596,7 +786,7 @@ void tc_init(mpi_ffl_handle *h) {
 void tc_release(mpi_ffl_handle *h) {
     TcState *s = state(h);
     if (!s) return;
-    void *ptrs[] = {s->jobs_fwd, s->jobs_adj, s->twB, s->twA, s->tw2, s->err};
+    void *ptrs[] = {s->jobs_fwd, s->jobs_adj, s->twB, s->twA, s->tw2, s->err, s->wbase};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete s;
@@ -608,15 +798,17 @@ void tc_tables_changed(mpi_ffl_handle *) {}
 void tc_forward_line(mpi_ffl_handle *h, const float *fine, const float *gain, float *data, cudaStream_t st) {
     TcState *s = state(h);
     s->cfg.prec = h->precision;
-    k_tc_fwd<<<s->n_fwd, kFwdThreads, s->cfg.f_total, st>>>(fine, h->t_traj, gain, s->jobs_fwd, s->twB, s->tw2,
-                                                           h->t_dgam, data, h->d, s->cfg, s->err);
+    const int grid = std::min(s->n_fwd, s->n_sm);
+    k_tc_fwd<<<grid, kFwdThreads + 32, s->cfg.f_total, st>>>(fine, h->t_tnf, h->t_vr, gain, s->jobs_fwd, s->n_fwd, s->twB,
+                                                        s->tw2, h->t_dgam, data, h->d, s->cfg, s->err);
 }
 
 void tc_adjoint_line(mpi_ffl_handle *h, const float *data, const float *gain, float *fine, cudaStream_t st) {
     TcState *s = state(h);
     s->cfg.prec = h->precision;
-    k_tc_adj<<<s->n_adj, kAdjThreads, s->cfg.a_total, st>>>(data, h->t_traj, gain, s->jobs_adj, s->twA, s->tw2,
-                                                           h->t_dgam, fine, h->d, s->cfg, s->err);
+    const int grid = std::min(s->n_adj, s->n_sm);
+    k_tc_adj<<<grid, kAdjThreads, s->cfg.a_total, st>>>(data, h->t_tnf, h->t_vr, gain, s->jobs_adj, s->n_adj, s->twA,
+                                                        s->tw2, h->t_dgam, s->wbase, fine, h->d, s->cfg, s->err);
 }
 
 int tc_take_error(mpi_ffl_handle *h) {

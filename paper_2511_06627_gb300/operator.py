@@ -35,7 +35,7 @@ class FFLOperator:
 
     def __init__(self, nx, nz, n_angles, S, P, A=6.0, phi0=0.0, zigzag=1, Q=8, fwhm=2.0,
                  k_min=1, k_max=8, half_width=2, angles=None, gains=None, d_gamma=None,
-                 precision=_lib.PREC_FP32):
+                 precision=_lib.PREC_FP32, path=None):
         lib = _lib.load()
         if not torch.cuda.is_available():
             raise RuntimeError("FFLOperator needs a CUDA device")
@@ -73,6 +73,8 @@ class FFLOperator:
                            Q=Q, fwhm=fwhm, k_min=k_min, k_max=k_max, half_width=half_width)
         if precision != _lib.PREC_FP32:
             self.set_precision(precision)
+        if path is not None:
+            self.set_path(path)
 
     @classmethod
     def from_config(cls, cfg, **kw):
@@ -201,6 +203,16 @@ class FFLOperator:
     # ---------------------------------------------------------------- settings
     def set_precision(self, precision):
         check(self._lib.mpi_ffl_set_precision(self._h, int(precision)), self._h)
+
+    def set_path(self, path):
+        """Evaluation path: PATH_* constant or one of 'staged', 'fused', 'line_gemm', 'full_gemm'."""
+        if isinstance(path, str):
+            path = _lib.PATHS[path]
+        check(self._lib.mpi_ffl_set_path(self._h, int(path)), self._h)
+
+    @property
+    def path(self):
+        return int(self._lib.mpi_ffl_get_path(self._h))
 
     def set_gain(self, gains):
         arr = (C.c_float * self.n_angles)(*[float(g) for g in gains])
