@@ -235,9 +235,9 @@ void angle_table(mpi_ffl_handle *h) {
         const double th = h->angles[m];
         const double c = std::cos(th), s = std::sin(th);
         if (std::fabs(c) >= std::fabs(s) - 1e-9) {
-            a[m] = AngleParam{(float)(1.0 / c), (float)(s / c), (float)(1.0 / std::fabs(c)), 1};
+            a[m] = AngleParam{(float)(1.0 / c), (float)(s / c), (float)(1.0 / std::fabs(c)), 1, (float)c};
         } else {
-            a[m] = AngleParam{(float)(-1.0 / s), (float)(c / s), (float)(1.0 / std::fabs(s)), 0};
+            a[m] = AngleParam{(float)(-1.0 / s), (float)(c / s), (float)(1.0 / std::fabs(s)), 0, (float)(-s)};
         }
     }
     upload(h, &h->t_ang, a);
@@ -354,7 +354,7 @@ void release(mpi_ffl_handle *h) {
                     h->t_csr, h->t_tw1, h->t_tw2_ro, h->t_tw2_qr, h->t_dgam, h->t_groups, h->w_volT,
                     h->w_proj, h->w_fine, h->w_sig, h->w_data, h->w_vol2, h->w_red, h->w_scal,
                     h->s_xp, h->s_y, h->s_g, h->s_r, h->s_hist, h->s_flags, h->tc_twb, h->t_agroups,
-                    h->t_tnf, h->t_vr};
+                    h->t_tnf, h->t_vr, h->w_err};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (auto &r : h->prof_rec) {
@@ -381,7 +381,7 @@ void ensure_sig(mpi_ffl_handle *h) {
 // ------------------------------------------------------------ stages
 void stage_p(mpi_ffl_handle *h, const float *x, float *proj, cudaStream_t st) {
     if (any_column_angle(h)) TIMED(MPI_FFL_K_TRANSPOSE, launch_transpose_xy(x, h->w_volT, h->d.N, h->d.Nz, st));
-    TIMED(MPI_FFL_K_PROJECT, launch_project(x, h->w_volT, h->t_ang, h->t_agroups, h->n_agroups, proj, h->d.N, h->d.Nz, st));
+    TIMED(MPI_FFL_K_PROJECT, launch_project(x, h->w_volT, h->t_ang, h->t_agroups, h->n_agroups, proj, h->d.N, h->d.Nz, st, h->w_err));
     check_launch(h, "project");
 }
 
@@ -589,6 +589,8 @@ extern "C" int mpi_ffl_create(const mpi_ffl_geometry *geom, const mpi_ffl_trajec
         dev_alloc(h, &h->s_g, d.nvox);
         dev_alloc(h, &h->s_r, d.ndata);
         dev_alloc(h, &h->s_flags, 4);
+        dev_alloc(h, &h->w_err, 1);
+        CK(cudaMemset(h->w_err, 0, sizeof(int)));
         tc_init(h);
         col_init(h);
         CK(cudaDeviceSynchronize());
@@ -715,7 +717,10 @@ extern "C" int mpi_ffl_set_psf_fwhm(mpi_ffl_handle *h, double fwhm) {
 extern "C" int mpi_ffl_sync_check(mpi_ffl_handle *h, void *stream) {
     return guarded(h, [&]() {
         CK(cudaStreamSynchronize(S(stream)));
-        if (tc_take_error(h) | col_take_error(h)) {
+        int werr = 0;
+        CK(cudaMemcpy(&werr, h->w_err, sizeof(int), cudaMemcpyDeviceToHost));
+        if (werr) CK(cudaMemset(h->w_err, 0, sizeof(int)));
+        if (tc_take_error(h) | col_take_error(h) | werr) {
             h->err = "a tensor-core kernel gave up on a bounded wait";
             return MPI_FFL_ERR_TIMEOUT;
         }

@@ -21,6 +21,7 @@ struct AngleParam {
     float slope;   // tan (rows) or cot (columns)
     float scale;   // 1/|cos| or 1/|sin|
     int row_major; // 1: march rows of x[z][y][:], 0: columns
+    float inv_c_rcp;  // 1 / inv_c (cos, or -sin)
 };
 
 // One time sample of a raster line: fine-grid cell n and the velocity-weighted
@@ -109,6 +110,7 @@ struct mpi_ffl_handle {
     double *s_hist = nullptr;
     int s_hist_len = 0;
     int *s_flags = nullptr;
+    int *w_err = nullptr;      // set by kernels that gave up on a bounded wait
     // measurement hooks
     int prof_on = 0;
     int64_t launches = 0;
@@ -135,7 +137,7 @@ void set_thread_error(const std::string &msg);
 // Projector (k_projector.cu)
 void launch_transpose_xy(const float *vol, float *volT, int N, int Nz, cudaStream_t st);
 void launch_project(const float *vol, const float *volT, const AngleParam *ang, const int *agroups,
-                    int n_agroups, float *proj, int N, int Nz, cudaStream_t st);
+                    int n_agroups, float *proj, int N, int Nz, cudaStream_t st, int *err);
 constexpr int kProjAnglesPerBlock = 2;  // angle slots per projector block (k_projector.cu)
 void launch_backproject(const float *proj, const AngleParam *ang, float *vol, int N, int Nz,
                         int M, cudaStream_t st);

@@ -6,6 +6,7 @@
 // Column-marched angles read a transposed copy of the volume, so that every
 // staged voxel line is contiguous.
 #include "internal.h"
+#include "tc_ptx.cuh"
 
 namespace mpiffl {
 
@@ -38,7 +39,7 @@ void launch_transpose_xy(const float *vol, float *volT, int N, int Nz, cudaStrea
 // thread is one ray (angle, bin i) and adds its interpolated sample for all kZc
 // slices at once, so the interpolation weights are computed once per kZc samples.
 constexpr int kZc = 8;
-constexpr int kMaxLd = 4;  // staged floats per thread and step
+constexpr int kMaxLd = 8;  // staged floats per thread and step
 
 __global__ void __launch_bounds__(1024) k_project(const float *__restrict__ vol, const float *__restrict__ volT,
                                                   const AngleParam *__restrict__ ang,
@@ -103,9 +104,111 @@ __global__ void __launch_bounds__(1024) k_project(const float *__restrict__ vol,
     }
 }
 
+// Pipelined variant (N % 4 == 0): an extra producer warp streams voxel line s of the
+// block's kZc slices into a ring of kPStages shared-memory stages with bulk copies
+// that complete on full[stage]; every consumer warp signals empty[stage] when it has
+// used a stage, so no block-wide barrier sits in the march loop.
+constexpr int kPStages = 8;
+
+__global__ void __launch_bounds__(1024 + 32) k_project_pipe(const float *__restrict__ vol,
+                                                            const float *__restrict__ volT,
+                                                            const AngleParam *__restrict__ ang,
+                                                            const int *__restrict__ agroups,
+                                                            float *__restrict__ proj, int N, int Nz,
+                                                            int rays_per_angle, int *err) {
+    extern __shared__ __align__(128) float psm[];  // kPStages x kZc x N
+    uint64_t *bars = reinterpret_cast<uint64_t *>(psm + kPStages * kZc * N);  // full[K], empty[K]
+    const int nthreads_c = rays_per_angle * kProjAnglesPerBlock;  // consumers
+    const int ncw = nthreads_c / 32;
+    const int z0 = blockIdx.y * kZc;
+    const int nz = min(kZc, Nz - z0);
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        for (int k = 0; k < kPStages; ++k) {
+            ptx::mbar_init(&bars[k], 1);
+            ptx::mbar_init(&bars[kPStages + k], ncw);
+        }
+        ptx::fence_mbar_init();
+    }
+    __syncthreads();
+    const AngleParam a0 = ang[agroups[blockIdx.x * kProjAnglesPerBlock]];
+    const float *src = a0.row_major ? vol : volT;  // one orientation per block
+    const uint32_t row_bytes = (uint32_t)N * 4u;
+    if (tid >= nthreads_c) {
+        // ---------------------------------------------------------------- producer warp
+        if (tid == nthreads_c) {
+            for (int s = 0; s < N; ++s) {
+                const int k = s % kPStages;
+                if (s >= kPStages && !ptx::mbar_wait_bounded(&bars[kPStages + k], ((s / kPStages) - 1) & 1, 1u << 24)) {
+                    atomicExch(err, 1);
+                    break;
+                }
+                float *dst = psm + k * kZc * N;
+                ptx::mbar_arrive_expect_tx(&bars[k], row_bytes * nz);
+                for (int zz = 0; zz < nz; ++zz)
+                    ptx::bulk_g2s(dst + zz * N, src + ((size_t)(z0 + zz) * N + s) * N, row_bytes, &bars[k]);
+            }
+        }
+        return;
+    }
+    // -------------------------------------------------------------------- consumers
+    const int slot = tid / rays_per_angle;
+    const int i = tid % rays_per_angle;
+    const int m = agroups[blockIdx.x * kProjAnglesPerBlock + slot];
+    const bool active = (m >= 0) && (i < N);
+    const AngleParam ap = ang[m >= 0 ? m : agroups[blockIdx.x * kProjAnglesPerBlock]];
+    const float c = 0.5f * (float)(N - 1);
+    const float fi = fmaf(ap.inv_c, (float)i - c, c);
+    float acc[kZc];
+#pragma unroll
+    for (int zz = 0; zz < kZc; ++zz) acc[zz] = 0.f;
+    bool good = true;
+    for (int s = 0; s < N; ++s) {
+        const int k = s % kPStages;
+        if (!ptx::mbar_wait_bounded(&bars[k], (s / kPStages) & 1, 1u << 24)) {
+            good = false;
+            break;
+        }
+        const float *cur = psm + k * kZc * N;
+        if (active) {
+            const float f = fmaf(ap.slope, (float)s - c, fi);
+            const float fl = floorf(f);
+            const int kk = (int)fl;
+            const float t = f - fl;
+            const float w0 = (kk >= 0 && kk < N) ? 1.f - t : 0.f;
+            const float w1 = (kk + 1 >= 0 && kk + 1 < N) ? t : 0.f;
+            const int k0 = min(max(kk, 0), N - 1);
+            const int k1 = min(max(kk + 1, 0), N - 1);
+#pragma unroll
+            for (int zz = 0; zz < kZc; ++zz)
+                if (zz < nz) acc[zz] = fmaf(w0, cur[zz * N + k0], fmaf(w1, cur[zz * N + k1], acc[zz]));
+        }
+        __syncwarp();
+        if ((tid & 31) == 0) ptx::mbar_arrive(&bars[kPStages + k]);
+    }
+    if (!good) {
+        if ((tid & 31) == 0) atomicExch(err, 1);
+        return;
+    }
+    if (active) {
+#pragma unroll
+        for (int zz = 0; zz < kZc; ++zz)
+            if (zz < nz) proj[((size_t)m * Nz + z0 + zz) * N + i] = acc[zz] * ap.scale;
+    }
+}
+
 void launch_project(const float *vol, const float *volT, const AngleParam *ang, const int *agroups,
-                    int n_agroups, float *proj, int N, int Nz, cudaStream_t st) {
+                    int n_agroups, float *proj, int N, int Nz, cudaStream_t st, int *err) {
     const int rays = (N + 31) / 32 * 32;
+    if (N % 4 == 0 && err) {
+        const size_t smem = sizeof(float) * kPStages * kZc * N + 16 * kPStages;
+        if (smem > 48 * 1024)
+            cudaFuncSetAttribute(k_project_pipe, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        dim3 grid(n_agroups, (Nz + kZc - 1) / kZc);
+        k_project_pipe<<<grid, rays * kProjAnglesPerBlock + 32, smem, st>>>(vol, volT, ang, agroups, proj, N, Nz,
+                                                                            rays, err);
+        return;
+    }
     const int threads = rays * kProjAnglesPerBlock;
     const size_t smem = sizeof(float) * 2 * kZc * N;
     if (smem > 48 * 1024)
@@ -115,8 +218,10 @@ void launch_project(const float *vol, const float *volT, const AngleParam *ang, 
 }
 
 // Transpose: a thread owns one voxel column (x, y) and kZc slices. For every angle
-// it finds the (at most two) rays whose interpolation touches the voxel, with the
-// forward's exact weights, and gathers their kZc projection values. No atomics.
+// the rays whose interpolation touches the voxel are among i1-1, i1, i1+1 (i1 the
+// nearest ray); ray i's sample position f_i is recomputed with the forward's exact
+// arithmetic and its weight max(0, 1 - |f_i - q|) equals the forward's (1-t or t)
+// bit for bit. The kZc projection values of each ray are gathered. No atomics.
 __global__ void __launch_bounds__(256) k_backproject(const float *__restrict__ proj,
                                                      const AngleParam *__restrict__ ang,
                                                      float *__restrict__ vol, int N, int Nz, int M) {
@@ -132,30 +237,24 @@ __global__ void __launch_bounds__(256) k_backproject(const float *__restrict__ p
     for (int m = 0; m < M; ++m) {
         const AngleParam a = ang[m];
         const int s = a.row_major ? y : x;             // march step holding this voxel
-        const int qi = a.row_major ? x : y;            // its index along the step's line
-        const float q = (float)qi;
-        const float off = fmaf(a.slope, (float)s - c, c);
-        const float ir = (q - off) / a.inv_c + c;      // ray whose sample lands on q (approx.)
-        const int i1 = __float2int_rn(ir);
-        int iA = 0, iB = 0;
-        float wA = 0.f, wB = 0.f;
+        const float q = (float)(a.row_major ? x : y);  // its index along the step's line
+        const float sm = (float)s - c;
+        // nearest ray: inv_c (i - c) + slope (s - c) + c = q
+        const int i1 = __float2int_rn(fmaf(q - fmaf(a.slope, sm, c), a.inv_c_rcp, c));
+        float w[3];
+        int ii[3];
 #pragma unroll
-        for (int di = -1; di <= 1; ++di) {
-            const int i = i1 + di;
-            if (i < 0 || i >= N) continue;
-            // the forward's sample position of ray i at step s, bit for bit
-            const float f = fmaf(a.slope, (float)s - c, fmaf(a.inv_c, (float)i - c, c));
-            const float fl = floorf(f);
-            const int k = (int)fl;
-            const float t = f - fl;
-            const float w = (k == qi) ? 1.f - t : ((k + 1 == qi) ? t : 0.f);
-            if (w != 0.f) {
-                if (wA == 0.f) { iA = i; wA = w; }
-                else { iB = i; wB = w; }
-            }
+        for (int u = 0; u < 3; ++u) {
+            const int i = i1 - 1 + u;
+            const float f = fmaf(a.slope, sm, fmaf(a.inv_c, (float)i - c, c));  // the forward's f
+            const bool in = (i >= 0) && (i < N);
+            w[u] = in ? fmaxf(0.f, 1.f - fabsf(f - q)) * a.scale : 0.f;
+            ii[u] = in ? i : 0;
         }
-        wA *= a.scale;
-        wB *= a.scale;
+        // at most two consecutive rays carry weight: (i1-1, i1) or (i1, i1+1)
+        const bool lo = w[0] != 0.f;
+        const float wA = lo ? w[0] : w[1], wB = lo ? w[1] : w[2];
+        const int iA = lo ? ii[0] : ii[1], iB = lo ? ii[1] : ii[2];
         const float *pm = proj + ((size_t)m * Nz + z0) * N;
 #pragma unroll
         for (int zz = 0; zz < kZc; ++zz)
