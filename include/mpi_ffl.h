@@ -175,7 +175,8 @@ int mpi_ffl_get_path(const mpi_ffl_handle *h);
 
 /* Replace the per-angle gains (host array of n_angles) or the PSF width. Both take
  * effect for work enqueued after the call returns; the call synchronises the device
- * before touching tables that queued work may still read. */
+ * before touching tables that queued work may still read. A new PSF width also
+ * rebuilds the collapsed line operator (W H), which takes a moment on the host. */
 int mpi_ffl_set_gain(mpi_ffl_handle *h, const float *gain);
 int mpi_ffl_set_psf_fwhm(mpi_ffl_handle *h, double fwhm_vox);
 
@@ -215,6 +216,17 @@ int mpi_ffl_param_grad(mpi_ffl_handle *h, const float *d_x, const float *d_gb_ri
  * on one handle must not overlap on the GPU. n >= 0. */
 int mpi_ffl_dot_f64(mpi_ffl_handle *h, const float *d_a, const float *d_b, int64_t n, double *d_out,
                     void *stream);
+
+/* As mpi_ffl_param_grad, from the projections P x (n_proj floats, e.g. kept from the
+ * forward as a checkpoint) instead of x, so P is not applied again. */
+int mpi_ffl_param_grad_proj(mpi_ffl_handle *h, const float *d_proj, const float *d_gb_ri, float *d_g_gain,
+                            float *d_g_fwhm, void *stream);
+
+/* The per-angle line operators alone (Sec. 2.2, Eq. (23) without P):
+ * b = blockdiag_m(A_DC) proj and proj = blockdiag_m(A_DC)^T b, on the current path.
+ * d_proj: n_proj floats [m][z][i]; d_b: n_data floats. */
+int mpi_ffl_line_forward(mpi_ffl_handle *h, const float *d_proj, float *d_b_ri, void *stream);
+int mpi_ffl_line_adjoint(mpi_ffl_handle *h, const float *d_b_ri, float *d_proj, void *stream);
 
 /* T^T T x (Sec. 3.3, Eq. (25)) on a volume. */
 int mpi_ffl_apply_ttt(mpi_ffl_handle *h, const float *d_x, float *d_out, void *stream);

@@ -89,6 +89,9 @@ PROTOTYPES = {
     "mpi_ffl_adjoint": (C.c_int, [H, FP, FP, ST]),
     "mpi_ffl_apply_stage": (C.c_int, [H, C.c_int32, C.c_int32, FP, FP, ST]),
     "mpi_ffl_param_grad": (C.c_int, [H, FP, FP, FP, FP, ST]),
+    "mpi_ffl_param_grad_proj": (C.c_int, [H, FP, FP, FP, FP, ST]),
+    "mpi_ffl_line_forward": (C.c_int, [H, FP, FP, ST]),
+    "mpi_ffl_line_adjoint": (C.c_int, [H, FP, FP, ST]),
     "mpi_ffl_apply_ttt": (C.c_int, [H, FP, FP, ST]),
     "mpi_ffl_dot_f64": (C.c_int, [H, FP, FP, C.c_int64, FP, ST]),
     "mpi_ffl_dot_f64_noalloc": (C.c_int, [FP, FP, C.c_int64, FP, ST]),

@@ -390,18 +390,18 @@ void stage_pt(mpi_ffl_handle *h, const float *proj, float *x, cudaStream_t st) {
     check_launch(h, "backproject");
 }
 
-void forward_impl(mpi_ffl_handle *h, const float *x, float *b, const float *htab, const float *gain,
-                  cudaStream_t st) {
+// blockdiag(A_DC) on projections: proj -> data
+void line_forward_impl(mpi_ffl_handle *h, const float *proj, float *b, const float *htab, const float *gain,
+                       cudaStream_t st) {
     const Dims &d = h->d;
     int path = h->path;
     if (path == MPI_FFL_PATH_FULL_GEMM && htab != h->t_htab) path = MPI_FFL_PATH_LINE_GEMM;  // other taps
-    stage_p(h, x, h->w_proj, st);
     if (path == MPI_FFL_PATH_FULL_GEMM) {
-        TIMED(MPI_FFL_K_GEMM_FWD, col_forward(h, h->w_proj, true, gain, b, st));
+        TIMED(MPI_FFL_K_GEMM_FWD, col_forward(h, proj, true, gain, b, st));
         check_launch(h, "gemm_fwd");
         return;
     }
-    TIMED(MPI_FFL_K_PSF_FWD, launch_psf_fwd(h->w_proj, htab, h->w_fine, d, st));
+    TIMED(MPI_FFL_K_PSF_FWD, launch_psf_fwd(proj, htab, h->w_fine, d, st));
     check_launch(h, "psf_fwd");
     if (path == MPI_FFL_PATH_LINE_GEMM) {
         TIMED(MPI_FFL_K_GEMM_FWD, col_forward(h, h->w_fine, false, gain, b, st));
@@ -420,12 +420,18 @@ void forward_impl(mpi_ffl_handle *h, const float *x, float *b, const float *htab
     check_launch(h, "dft_fwd");
 }
 
-void adjoint_impl(mpi_ffl_handle *h, const float *b, float *x, cudaStream_t st) {
+void forward_impl(mpi_ffl_handle *h, const float *x, float *b, const float *htab, const float *gain,
+                  cudaStream_t st) {
+    stage_p(h, x, h->w_proj, st);
+    line_forward_impl(h, h->w_proj, b, htab, gain, st);
+}
+
+// blockdiag(A_DC)^T: data -> projections
+void line_adjoint_impl(mpi_ffl_handle *h, const float *b, float *proj, cudaStream_t st) {
     const Dims &d = h->d;
     if (h->path == MPI_FFL_PATH_FULL_GEMM) {
-        TIMED(MPI_FFL_K_GEMM_ADJ, col_adjoint(h, b, true, h->t_gain, h->w_proj, st));
+        TIMED(MPI_FFL_K_GEMM_ADJ, col_adjoint(h, b, true, h->t_gain, proj, st));
         check_launch(h, "gemm_adj");
-        stage_pt(h, h->w_proj, x, st);
         return;
     }
     if (h->path == MPI_FFL_PATH_LINE_GEMM) {
@@ -441,9 +447,35 @@ void adjoint_impl(mpi_ffl_handle *h, const float *b, float *x, cudaStream_t st) 
         TIMED(MPI_FFL_K_RESAMPLE_ADJ, launch_resample_adj(h->w_sig, h->t_csr_ptr, h->t_csr, h->t_gain, h->t_groups, h->n_groups, h->w_fine, d, st));
         check_launch(h, "resample_adj");
     }
-    TIMED(MPI_FFL_K_PSF_ADJ, launch_psf_adj(h->w_fine, h->t_htab, h->w_proj, d, st));
+    TIMED(MPI_FFL_K_PSF_ADJ, launch_psf_adj(h->w_fine, h->t_htab, proj, d, st));
     check_launch(h, "psf_adj");
+}
+
+void adjoint_impl(mpi_ffl_handle *h, const float *b, float *x, cudaStream_t st) {
+    line_adjoint_impl(h, b, h->w_proj, st);
     stage_pt(h, h->w_proj, x, st);
+}
+
+// d loss / d gain_m = <g_b[m], A_m x |_{g_m = 1}> and d loss / d fwhm = <g_b, (dA/dfwhm) x>,
+// from the projections P x
+void param_grad_impl(mpi_ffl_handle *h, const float *proj, const float *d_gb, float *d_g_gain, float *d_g_fwhm,
+                     cudaStream_t st) {
+    const Dims &d = h->d;
+    if (d_g_gain) {
+        line_forward_impl(h, proj, h->s_r, h->t_htab, h->t_unit_gain, st);
+        const int64_t per = (int64_t)2 * d.Nz * d.nb;
+        const int nbk = std::min(1024, std::max(1, (int)((per + 1023) / 1024)));
+        TIMED(MPI_FFL_K_SOLVER, launch_angle_dots(h->s_r, d_gb, d.M, per, h->w_red, nbk, st));
+        TIMED(MPI_FFL_K_SOLVER, launch_angle_finalize(h->w_red, d.M, nbk, d_g_gain, st));
+        check_launch(h, "gain grad");
+    }
+    if (d_g_fwhm) {
+        line_forward_impl(h, proj, h->s_r, h->t_dhtab, h->t_gain, st);
+        const int nbk = reduce_blocks(d.ndata);
+        TIMED(MPI_FFL_K_SOLVER, launch_dot(h->s_r, d_gb, d.ndata, h->w_red, nbk, st));
+        TIMED(MPI_FFL_K_SOLVER, launch_finalize_to_float(h->w_red, nbk, d_g_fwhm, st));
+        check_launch(h, "fwhm grad");
+    }
 }
 
 double dot_sync(mpi_ffl_handle *h, const float *a, const float *b, int64_t n, cudaStream_t st) {
@@ -710,6 +742,16 @@ extern "C" int mpi_ffl_set_psf_fwhm(mpi_ffl_handle *h, double fwhm) {
         CK(cudaMemcpy(h->t_htab, ht.data(), sizeof(float) * ht.size(), cudaMemcpyHostToDevice));
         CK(cudaMemcpy(h->t_dhtab, dht.data(), sizeof(float) * dht.size(), cudaMemcpyHostToDevice));
         tc_tables_changed(h);
+        // W H holds the PSF: rebuild the collapsed operator
+        const bool had = col_supported(h);
+        col_release(h);
+        col_init(h);
+        if (had && !col_supported(h) && (h->path == MPI_FFL_PATH_LINE_GEMM || h->path == MPI_FFL_PATH_FULL_GEMM)) {
+            h->path = MPI_FFL_PATH_STAGED;
+            h->precision = MPI_FFL_PREC_FP32;
+            h->err = "collapsed operator could not be rebuilt; fell back to the staged path";
+            return MPI_FFL_ERR_OOM;
+        }
         return MPI_FFL_OK;
     });
 }
@@ -781,24 +823,43 @@ extern "C" int mpi_ffl_param_grad(mpi_ffl_handle *h, const float *d_x, const flo
             h->err = "NULL buffer";
             return MPI_FFL_ERR_INVALID_ARG;
         }
-        const Dims &d = h->d;
         cudaStream_t st = S(stream);
-        if (d_g_gain) {
-            // d loss / d g_m = <g_b[m], A_m x |_{g_m = 1}>
-            forward_impl(h, d_x, h->s_r, h->t_htab, h->t_unit_gain, st);
-            const int64_t per = (int64_t)2 * d.Nz * d.nb;
-            const int nbk = std::min(1024, std::max(1, (int)((per + 1023) / 1024)));
-            TIMED(MPI_FFL_K_SOLVER, launch_angle_dots(h->s_r, d_gb, d.M, per, h->w_red, nbk, st));
-            TIMED(MPI_FFL_K_SOLVER, launch_angle_finalize(h->w_red, d.M, nbk, d_g_gain, st));
-            check_launch(h, "gain grad");
+        stage_p(h, d_x, h->w_proj, st);
+        param_grad_impl(h, h->w_proj, d_gb, d_g_gain, d_g_fwhm, st);
+        return MPI_FFL_OK;
+    });
+}
+
+extern "C" int mpi_ffl_param_grad_proj(mpi_ffl_handle *h, const float *d_proj, const float *d_gb, float *d_g_gain,
+                                       float *d_g_fwhm, void *stream) {
+    return guarded(h, [&]() {
+        if (!d_proj || !d_gb) {
+            h->err = "NULL buffer";
+            return MPI_FFL_ERR_INVALID_ARG;
         }
-        if (d_g_fwhm) {
-            forward_impl(h, d_x, h->s_r, h->t_dhtab, h->t_gain, st);
-            const int nbk = reduce_blocks(d.ndata);
-            TIMED(MPI_FFL_K_SOLVER, launch_dot(h->s_r, d_gb, d.ndata, h->w_red, nbk, st));
-            TIMED(MPI_FFL_K_SOLVER, launch_finalize_to_float(h->w_red, nbk, d_g_fwhm, st));
-            check_launch(h, "fwhm grad");
+        param_grad_impl(h, d_proj, d_gb, d_g_gain, d_g_fwhm, S(stream));
+        return MPI_FFL_OK;
+    });
+}
+
+extern "C" int mpi_ffl_line_forward(mpi_ffl_handle *h, const float *d_proj, float *d_b, void *stream) {
+    return guarded(h, [&]() {
+        if (!d_proj || !d_b) {
+            h->err = "NULL buffer";
+            return MPI_FFL_ERR_INVALID_ARG;
         }
+        line_forward_impl(h, d_proj, d_b, h->t_htab, h->t_gain, S(stream));
+        return MPI_FFL_OK;
+    });
+}
+
+extern "C" int mpi_ffl_line_adjoint(mpi_ffl_handle *h, const float *d_b, float *d_proj, void *stream) {
+    return guarded(h, [&]() {
+        if (!d_proj || !d_b) {
+            h->err = "NULL buffer";
+            return MPI_FFL_ERR_INVALID_ARG;
+        }
+        line_adjoint_impl(h, d_b, d_proj, S(stream));
         return MPI_FFL_OK;
     });
 }

@@ -160,6 +160,39 @@ class FFLOperator:
                                            _ptr(gf) if gf is not None else None, _stream()), self._h)
         return gg, gf
 
+    def project(self, x):
+        """P x: projections [M, N_z, N]."""
+        return self.apply_stage(0, x)
+
+    def backproject(self, proj):
+        """P^T proj: a volume."""
+        return self.apply_stage(0, proj, transpose=True)
+
+    def line_forward(self, proj, out=None):
+        """blockdiag(A_DC) on projections [M, N_z, N] -> data."""
+        self._check(proj, (self.n_angles, self.nz, self.nx), "proj")
+        out = self.new_data() if out is None else out
+        check(self._lib.mpi_ffl_line_forward(self._h, _ptr(proj), _ptr(out), _stream()), self._h)
+        return out
+
+    def line_adjoint(self, b):
+        """blockdiag(A_DC)^T: data -> projections."""
+        self._check(b, self.data_shape, "b")
+        out = torch.empty((self.n_angles, self.nz, self.nx), device=self.device, dtype=torch.float32)
+        check(self._lib.mpi_ffl_line_adjoint(self._h, _ptr(b), _ptr(out), _stream()), self._h)
+        return out
+
+    def param_grad_proj(self, proj, grad_b, want_gain=True, want_fwhm=True):
+        """As param_grad, from the projections P x."""
+        self._check(proj, (self.n_angles, self.nz, self.nx), "proj")
+        self._check(grad_b, self.data_shape, "grad_b")
+        gg = torch.empty(self.n_angles, device=self.device, dtype=torch.float32) if want_gain else None
+        gf = torch.empty(1, device=self.device, dtype=torch.float32) if want_fwhm else None
+        check(self._lib.mpi_ffl_param_grad_proj(self._h, _ptr(proj), _ptr(grad_b),
+                                                _ptr(gg) if gg is not None else None,
+                                                _ptr(gf) if gf is not None else None, _stream()), self._h)
+        return gg, gf
+
     def power_norm(self, n_iter=50, seed=1234):
         out = C.c_double()
         check(self._lib.mpi_ffl_power_norm(self._h, int(n_iter), C.c_uint64(seed), C.byref(out), _stream()), self._h)
@@ -217,6 +250,7 @@ class FFLOperator:
     def set_gain(self, gains):
         arr = (C.c_float * self.n_angles)(*[float(g) for g in gains])
         check(self._lib.mpi_ffl_set_gain(self._h, arr), self._h)
+        self.gains = [float(g) for g in gains]
 
     def set_fwhm(self, fwhm):
         check(self._lib.mpi_ffl_set_psf_fwhm(self._h, float(fwhm)), self._h)
