@@ -244,6 +244,47 @@ int mpi_ffl_solve(mpi_ffl_handle *h, const float *d_b_ri, float *d_x_inout,
                   const mpi_ffl_solve_params *params, mpi_ffl_solve_report *report,
                   void *stream);
 
+/* ---- Continuous batching (serving) -------------------------------------------------
+ * A job is one reconstruction of Eq. (26) on its own handle (the handle must not be
+ * used for anything else while the job lives): it owns a device copy of the data and
+ * the solver state (x, x_prev, y, gradient, residual, residual history), so nothing
+ * crosses PCIe between iterations. mpi_ffl_job_step advances any set of jobs by one
+ * iteration each; jobs whose handles are on the FULL_GEMM path share one launch per
+ * kernel kind (momentum, projector, line GEMM, residual, norm and stop test, adjoint
+ * line GEMM, backprojector, update), jobs on other paths run their A and A^T alone
+ * between those launches. A job that meets its stop test does no further work on the
+ * device; a job that has used its iteration budget is skipped by the host. */
+typedef struct mpi_ffl_job mpi_ffl_job;
+
+typedef struct {
+    int32_t iters_done;      /* iterations completed                               */
+    int32_t stopped;         /* 1: stop test met, 2: non-finite residual            */
+    int32_t finished;        /* stopped or iteration budget used                    */
+    double residual_first;   /* ||A y - b|| of the first iteration (FP64)          */
+    double residual_last;    /* ||A y - b|| of the last iteration (FP64)           */
+    double tau, lambda;
+    int64_t device_bytes;    /* device memory the job owns (besides its handle)    */
+} mpi_ffl_job_status_t;
+
+/* Allocates the job's state, copies d_b (n_data floats) and x0 (n_vox floats or NULL
+ * for zero), and fixes tau and lambda as mpi_ffl_solve does (running the power
+ * iteration on the handle if needed, which synchronises the stream). */
+int mpi_ffl_job_create(mpi_ffl_handle *h, const float *d_b, const float *d_x0, const mpi_ffl_solve_params *p,
+                       mpi_ffl_job **out, void *stream);
+int mpi_ffl_job_step(mpi_ffl_job *const *jobs, int32_t n, void *stream);
+/* Synchronises the stream and reads the job's progress. */
+int mpi_ffl_job_status(const mpi_ffl_job *j, mpi_ffl_job_status_t *out, void *stream);
+/* Device pointer to the job's three int flags: [0] stop verdict, [1] iterations done,
+ * [2] frozen. A server can copy them asynchronously to poll many jobs at once. */
+int mpi_ffl_job_flags(const mpi_ffl_job *j, const int32_t **d_flags);
+/* Enqueues copies of the flags of jobs[0..n) into host_flags (3 per job; pinned host
+ * memory for asynchrony); the values are valid once the stream has reached them. */
+int mpi_ffl_job_poll(mpi_ffl_job *const *jobs, int32_t n, int32_t *host_flags, void *stream);
+/* Copies the current iterate to d_x (n_vox floats). */
+int mpi_ffl_job_result(const mpi_ffl_job *j, float *d_x, void *stream);
+/* Waits for the device and frees the job's state (not its handle). NULL is a no-op. */
+int mpi_ffl_job_destroy(mpi_ffl_job *j);
+
 /* ---- Handle-free entry point that allocates nothing -----------------------------
  * The paper has no counterpart to this call; it serves callers that cannot call
  * cudaMalloc (or mpi_ffl_create, which allocates): for example code running while a

@@ -547,6 +547,15 @@ int guarded(mpi_ffl_handle *h, F &&f) {
 
 namespace mpiffl {
 void set_thread_error(const std::string &msg) { g_create_error = msg; }
+double power_norm_for_job(mpi_ffl_handle *h, int n_iter, uint64_t seed, cudaStream_t st) {
+    return power_norm_impl(h, n_iter, seed, st);
+}
+double ttt_norm_for_job(const Dims &d) { return ttt_norm(d); }
+bool handle_has_column_angles(const mpi_ffl_handle *h) { return any_column_angle(h); }
+void forward_for_job(mpi_ffl_handle *h, const float *x, float *b, cudaStream_t st) {
+    forward_impl(h, x, b, h->t_htab, h->t_gain, st);
+}
+void adjoint_for_job(mpi_ffl_handle *h, const float *b, float *x, cudaStream_t st) { adjoint_impl(h, b, x, st); }
 }  // namespace mpiffl
 
 // ============================================================ C ABI

@@ -53,6 +53,7 @@ struct GemmArgs {
     int stages;
     uint32_t tmem_cols;
     int *err;
+    const int *done;     // nonzero: the problem is finished, its blocks do nothing
 };
 
 __device__ __forceinline__ void split8(const float (&v)[8], uint4 &hi, uint4 &lo) {
@@ -70,8 +71,7 @@ __device__ __forceinline__ void split8(const float (&v)[8], uint4 &hi, uint4 &lo
     lo = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
-__global__ void __launch_bounds__(192, 1) k_gemm_split(GemmArgs g) {
-    extern __shared__ __align__(128) uint8_t sm[];
+__device__ __forceinline__ void gemm_body(const GemmArgs &g, int mt, int nt, uint8_t *sm) {
     const uint32_t bytesA = kBM * kBK * 2;          // one of hi | lo
     const uint32_t bytesB = (uint32_t)g.BN * kBK * 2;
     const uint32_t stage = 2 * bytesA + 2 * bytesB;
@@ -79,7 +79,6 @@ __global__ void __launch_bounds__(192, 1) k_gemm_split(GemmArgs g) {
     uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 2 * g.stages + 1);
     int *flag = reinterpret_cast<int *>(tslot + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int mt = blockIdx.x, nt = blockIdx.y;
 
     if (tid == 0) {
         for (int s = 0; s < g.stages; ++s) {
@@ -205,6 +204,21 @@ __global__ void __launch_bounds__(192, 1) k_gemm_split(GemmArgs g) {
     if (warp == 0) ptx::tmem_dealloc(tmem, g.tmem_cols);
 }
 
+__global__ void __launch_bounds__(192, 1) k_gemm_split(GemmArgs g) {
+    extern __shared__ __align__(128) uint8_t sm[];
+    gemm_body(g, blockIdx.x, blockIdx.y, sm);
+}
+
+// One launch for several GEMM problems: items[b] = (problem, m tile, n tile).
+__global__ void __launch_bounds__(192, 1) k_gemm_batch(const GemmArgs *__restrict__ args,
+                                                       const int4 *__restrict__ items) {
+    extern __shared__ __align__(128) uint8_t sm[];
+    const int4 it = items[blockIdx.x];
+    const GemmArgs g = args[it.x];
+    if (g.done && *g.done) return;
+    gemm_body(g, it.y, it.z, sm);
+}
+
 uint16_t bf16_bits(double x) {
     const float f = (float)x;
     uint32_t u;
@@ -298,11 +312,51 @@ void launch(const mpi_ffl_handle *h, const float *A, int64_t lda, int Ka, const 
     const size_t smem = smem_for(B.BN, g.stages);
     g.tmem_cols = B.BN <= 32 ? 32 : B.BN <= 64 ? 64 : B.BN <= 128 ? 128 : 256;
     g.err = cs(h)->err;
+    g.done = nullptr;
     dim3 grid((M + kBM - 1) / kBM, B.ntile);
     k_gemm_split<<<grid, 192, smem, st>>>(g);
 }
 
 }  // namespace
+
+// Arguments of the GEMM problems of one line stage of handle h (one per trajectory).
+int gemm_problems(const mpi_ffl_handle *h, bool adjoint, const float *in, float *out, const int *done,
+                  GemmArgs *args, int4 *items, int item_cap, int &n_items) {
+    ColState *s = cs(h);
+    const Dims &d = h->d;
+    int np = 0;
+    for (int par = 0; par < s->n_par; ++par) {
+        const Packed &B = adjoint ? s->full_a[par] : s->full_f[par];
+        GemmArgs &g = args[np];
+        g = GemmArgs{};
+        g.A = in;
+        g.lda = adjoint ? 2 * d.nb : d.N;
+        g.Ka = (int)g.lda;
+        g.arow = s->rows[par];
+        g.M = s->nrows[par];
+        g.B = B.dev;
+        g.BN = B.BN;
+        g.nkc = B.nkc;
+        g.C = out;
+        g.ldc = adjoint ? d.N : 2 * d.nb;
+        g.crow = s->rows[par];
+        g.Nc = (int)g.ldc;
+        g.rscale = h->t_gain;
+        g.rdiv = d.Nz;
+        g.prec = h->precision;
+        smem_for(B.BN, g.stages);
+        g.tmem_cols = B.BN <= 32 ? 32 : B.BN <= 64 ? 64 : B.BN <= 128 ? 128 : 256;
+        g.err = s->err;
+        g.done = done;
+        for (int mt = 0; mt < (g.M + kBM - 1) / kBM; ++mt)
+            for (int nt = 0; nt < B.ntile; ++nt) {
+                if (n_items >= item_cap) return -1;
+                items[n_items++] = make_int4(np, mt, nt, 0);
+            }
+        ++np;
+    }
+    return np;
+}
 
 bool col_supported(const mpi_ffl_handle *h) {
     const ColState *s = cs(h);
@@ -444,6 +498,36 @@ void col_adjoint(mpi_ffl_handle *h, const float *data, bool full, const float *g
         launch(h, data, 2 * d.nb, 2 * d.nb, s->rows[par], s->nrows[par], B, out, nout, s->rows[par], nout, gain,
                d.Nz, st);
     }
+}
+
+size_t gemm_args_size() { return sizeof(GemmArgs); }
+
+// Full-GEMM line stage (W H or its transpose) of several handles in one launch.
+// args/items are host staging arrays; dargs/ditems their device copies (same
+// layout), already uploaded by the caller before this launch runs.
+int col_batch_prepare(mpi_ffl_handle *const *hs, const float *const *in, float *const *out, const int *const *done,
+                      int n, bool adjoint, void *args, int4 *items, int arg_cap, int item_cap, int &n_items) {
+    GemmArgs *a = reinterpret_cast<GemmArgs *>(args);
+    int np = 0;
+    n_items = 0;
+    for (int j = 0; j < n; ++j) {
+        if (np + 2 > arg_cap) return -1;
+        const int base_items = n_items;
+        const int k = gemm_problems(hs[j], adjoint, in[j], out[j], done[j], a + np, items, item_cap, n_items);
+        if (k < 0) return -1;
+        for (int i = base_items; i < n_items; ++i) items[i].x += np;
+        np += k;
+    }
+    return np;
+}
+
+void col_batch_launch(const void *dargs, const int4 *ditems, int n_items, cudaStream_t st) {
+    if (n_items <= 0) return;
+    k_gemm_batch<<<n_items, 192, 227 * 1024, st>>>(reinterpret_cast<const GemmArgs *>(dargs), ditems);
+}
+
+void col_batch_init() {
+    cudaFuncSetAttribute(k_gemm_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
 }
 
 }  // namespace mpiffl

@@ -14,6 +14,15 @@ int col_take_error(mpi_ffl_handle *h);   // 1 if a GEMM gave up on a bounded wai
 void col_forward(mpi_ffl_handle *h, const float *in, bool full, const float *gain, float *data, cudaStream_t st);
 void col_adjoint(mpi_ffl_handle *h, const float *data, bool full, const float *gain, float *out, cudaStream_t st);
 
+// Batched full-GEMM line stages (continuous batching): fill host staging arrays of
+// GEMM problems and (problem, m tile, n tile) items for handles hs[0..n); returns the
+// number of problems or -1 when the capacities are too small.
+size_t gemm_args_size();
+int col_batch_prepare(mpi_ffl_handle *const *hs, const float *const *in, float *const *out, const int *const *done,
+                      int n, bool adjoint, void *args, int4 *items, int arg_cap, int item_cap, int &n_items);
+void col_batch_launch(const void *dargs, const int4 *ditems, int n_items, cudaStream_t st);
+void col_batch_init();
+
 // host-side model pieces shared with the table builders (api.cu)
 double langevin_d1_host(double x);
 double langevin_half_point_host();

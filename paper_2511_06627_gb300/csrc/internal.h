@@ -130,6 +130,77 @@ struct mpi_ffl_handle {
 
 namespace mpiffl {
 
+// ---------------------------------------------------------------- batched launches
+// One problem of a batched launch (continuous batching, batch.cu). `done` (device
+// int, may be NULL) turns the problem's blocks into no-ops once it is nonzero.
+struct TransposeJob {
+    const float *vol;
+    float *volT;
+    int N, Nz;
+    const int *done;
+};
+struct ProjectJob {
+    const float *vol, *volT;
+    const AngleParam *ang;
+    const int *agroups;
+    float *proj;
+    int N, Nz, n_agroups;
+    const int *done;
+};
+struct BackprojectJob {
+    const float *proj;
+    const AngleParam *ang;
+    float *vol;
+    int N, Nz, M;
+    const int *done;
+};
+struct MomentumJob {   // y = x + beta (x - xp)
+    const float *x, *xp;
+    float *y;
+    float beta;
+    int64_t n;
+    const int *done;
+};
+struct ResidualJob {   // r <- r - b; partial sums of r^2 into partials[0..nblk)
+    float *r;
+    const float *b;
+    int64_t n;
+    double *partials;
+    int nblk;
+    const int *done;
+};
+struct StopJob {       // hist[k] = sqrt(sum partials); stop test; status out
+    const double *partials;
+    int nblk;
+    double *hist;
+    int k;
+    double stop_rel;
+    int *flags;        // [0] stop (1 converged, 2 non-finite), [1] iterations done
+    int *done;         // set when the job must not run further
+};
+struct UpdateJob {     // x_out = P(y - tau (g + lam T^T T y)); a frozen job copies x_cur
+    const float *y, *g;
+    float *xo;
+    const float *xcur;
+    float tau, lam;
+    int nonneg, N, Nz;
+    const int *done;
+};
+
+int transpose_blocks(int N, int Nz);
+int project_blocks(int n_agroups, int Nz);
+int backproject_blocks(int N, int Nz);
+int update_blocks(int N, int Nz);
+void launch_transpose_batch(const TransposeJob *jobs, const int *offs, int n, int total, cudaStream_t st);
+void launch_project_batch(const ProjectJob *jobs, const int *offs, int n, int total, int maxN, int *err,
+                          cudaStream_t st);
+void launch_backproject_batch(const BackprojectJob *jobs, const int *offs, int n, int total, cudaStream_t st);
+void launch_momentum_batch(const MomentumJob *jobs, const int *offs, int n, int total, cudaStream_t st);
+void launch_residual_batch(const ResidualJob *jobs, const int *offs, int n, int total, cudaStream_t st);
+void launch_stop_batch(const StopJob *jobs, int n, cudaStream_t st);
+void launch_update_batch(const UpdateJob *jobs, const int *offs, int n, int total, cudaStream_t st);
+void launch_freeze_batch(const StopJob *jobs, int n, cudaStream_t st);  // done = stop verdict
+
 // Message returned by mpi_ffl_last_error(NULL) on this thread.
 void set_thread_error(const std::string &msg);
 

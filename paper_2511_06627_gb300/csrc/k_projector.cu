@@ -10,22 +10,27 @@
 
 namespace mpiffl {
 
-__global__ void k_transpose_xy(const float *__restrict__ vol, float *__restrict__ volT, int N) {
+__device__ __forceinline__ void transpose_body(const float *__restrict__ vol, float *__restrict__ volT, int N,
+                                               int bx, int by, int bz) {
     __shared__ float tile[32][33];
-    const size_t zoff = (size_t)blockIdx.z * N * N;
-    int x = blockIdx.x * 32 + threadIdx.x;
-    int y0 = blockIdx.y * 32;
+    const size_t zoff = (size_t)bz * N * N;
+    int x = bx * 32 + threadIdx.x;
+    int y0 = by * 32;
     for (int k = threadIdx.y; k < 32; k += blockDim.y) {
         int y = y0 + k;
         if (x < N && y < N) tile[k][threadIdx.x] = vol[zoff + (size_t)y * N + x];
     }
     __syncthreads();
-    int yo = blockIdx.y * 32 + threadIdx.x;
-    int x0 = blockIdx.x * 32;
+    int yo = by * 32 + threadIdx.x;
+    int x0 = bx * 32;
     for (int k = threadIdx.y; k < 32; k += blockDim.y) {
         int xo = x0 + k;
         if (xo < N && yo < N) volT[zoff + (size_t)xo * N + yo] = tile[threadIdx.x][k];
     }
+}
+
+__global__ void k_transpose_xy(const float *__restrict__ vol, float *__restrict__ volT, int N) {
+    transpose_body(vol, volT, N, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 void launch_transpose_xy(const float *vol, float *volT, int N, int Nz, cudaStream_t st) {
@@ -110,17 +115,15 @@ __global__ void __launch_bounds__(1024) k_project(const float *__restrict__ vol,
 // used a stage, so no block-wide barrier sits in the march loop.
 constexpr int kPStages = 8;
 
-__global__ void __launch_bounds__(1024 + 32) k_project_pipe(const float *__restrict__ vol,
-                                                            const float *__restrict__ volT,
-                                                            const AngleParam *__restrict__ ang,
-                                                            const int *__restrict__ agroups,
-                                                            float *__restrict__ proj, int N, int Nz,
-                                                            int rays_per_angle, int *err) {
-    extern __shared__ __align__(128) float psm[];  // kPStages x kZc x N
+__device__ __forceinline__ void project_pipe_body(const float *__restrict__ vol, const float *__restrict__ volT,
+                                                  const AngleParam *__restrict__ ang,
+                                                  const int *__restrict__ agroups, float *__restrict__ proj,
+                                                  int N, int Nz, int rays_per_angle, int *err, int bx, int by,
+                                                  float *psm) {
     uint64_t *bars = reinterpret_cast<uint64_t *>(psm + kPStages * kZc * N);  // full[K], empty[K]
     const int nthreads_c = rays_per_angle * kProjAnglesPerBlock;  // consumers
     const int ncw = nthreads_c / 32;
-    const int z0 = blockIdx.y * kZc;
+    const int z0 = by * kZc;
     const int nz = min(kZc, Nz - z0);
     const int tid = threadIdx.x;
     if (tid == 0) {
@@ -131,7 +134,7 @@ __global__ void __launch_bounds__(1024 + 32) k_project_pipe(const float *__restr
         ptx::fence_mbar_init();
     }
     __syncthreads();
-    const AngleParam a0 = ang[agroups[blockIdx.x * kProjAnglesPerBlock]];
+    const AngleParam a0 = ang[agroups[bx * kProjAnglesPerBlock]];
     const float *src = a0.row_major ? vol : volT;  // one orientation per block
     const uint32_t row_bytes = (uint32_t)N * 4u;
     if (tid >= nthreads_c) {
@@ -154,9 +157,9 @@ __global__ void __launch_bounds__(1024 + 32) k_project_pipe(const float *__restr
     // -------------------------------------------------------------------- consumers
     const int slot = tid / rays_per_angle;
     const int i = tid % rays_per_angle;
-    const int m = agroups[blockIdx.x * kProjAnglesPerBlock + slot];
+    const int m = agroups[bx * kProjAnglesPerBlock + slot];
     const bool active = (m >= 0) && (i < N);
-    const AngleParam ap = ang[m >= 0 ? m : agroups[blockIdx.x * kProjAnglesPerBlock]];
+    const AngleParam ap = ang[m >= 0 ? m : agroups[bx * kProjAnglesPerBlock]];
     const float c = 0.5f * (float)(N - 1);
     const float fi = fmaf(ap.inv_c, (float)i - c, c);
     float acc[kZc];
@@ -197,6 +200,16 @@ __global__ void __launch_bounds__(1024 + 32) k_project_pipe(const float *__restr
     }
 }
 
+__global__ void __launch_bounds__(1024 + 32) k_project_pipe(const float *__restrict__ vol,
+                                                            const float *__restrict__ volT,
+                                                            const AngleParam *__restrict__ ang,
+                                                            const int *__restrict__ agroups,
+                                                            float *__restrict__ proj, int N, int Nz,
+                                                            int rays_per_angle, int *err) {
+    extern __shared__ __align__(128) float psm[];  // kPStages x kZc x N
+    project_pipe_body(vol, volT, ang, agroups, proj, N, Nz, rays_per_angle, err, blockIdx.x, blockIdx.y, psm);
+}
+
 void launch_project(const float *vol, const float *volT, const AngleParam *ang, const int *agroups,
                     int n_agroups, float *proj, int N, int Nz, cudaStream_t st, int *err) {
     const int rays = (N + 31) / 32 * 32;
@@ -222,12 +235,12 @@ void launch_project(const float *vol, const float *volT, const AngleParam *ang, 
 // nearest ray); ray i's sample position f_i is recomputed with the forward's exact
 // arithmetic and its weight max(0, 1 - |f_i - q|) equals the forward's (1-t or t)
 // bit for bit. The kZc projection values of each ray are gathered. No atomics.
-__global__ void __launch_bounds__(256) k_backproject(const float *__restrict__ proj,
-                                                     const AngleParam *__restrict__ ang,
-                                                     float *__restrict__ vol, int N, int Nz, int M) {
-    const int x = blockIdx.x * 32 + threadIdx.x;
-    const int y = blockIdx.y * 8 + threadIdx.y;
-    const int z0 = blockIdx.z * kZc;
+__device__ __forceinline__ void backproject_body(const float *__restrict__ proj, const AngleParam *__restrict__ ang,
+                                                 float *__restrict__ vol, int N, int Nz, int M, int bx, int by,
+                                                 int bz) {
+    const int x = bx * 32 + threadIdx.x;
+    const int y = by * 8 + threadIdx.y;
+    const int z0 = bz * kZc;
     const int nz = min(kZc, Nz - z0);
     if (x >= N || y >= N) return;
     const float c = 0.5f * (float)(N - 1);
@@ -265,10 +278,86 @@ __global__ void __launch_bounds__(256) k_backproject(const float *__restrict__ p
         if (zz < nz) vol[((size_t)(z0 + zz) * N + y) * N + x] = acc[zz];
 }
 
+__global__ void __launch_bounds__(256) k_backproject(const float *__restrict__ proj,
+                                                     const AngleParam *__restrict__ ang,
+                                                     float *__restrict__ vol, int N, int Nz, int M) {
+    backproject_body(proj, ang, vol, N, Nz, M, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
 void launch_backproject(const float *proj, const AngleParam *ang, float *vol, int N, int Nz,
                         int M, cudaStream_t st) {
     dim3 grid((N + 31) / 32, (N + 7) / 8, (Nz + kZc - 1) / kZc), block(32, 8);
     k_backproject<<<grid, block, 0, st>>>(proj, ang, vol, N, Nz, M);
+}
+
+// ---------------------------------------------------------------------- batches
+// One launch serves several problems: block b belongs to the problem j with
+// offs[j] <= b < offs[j + 1]; its local block index is b - offs[j].
+__device__ __forceinline__ int batch_find(const int *__restrict__ offs, int n, int b) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(offs + mid) <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void k_transpose_batch(const TransposeJob *__restrict__ jobs, const int *__restrict__ offs, int n) {
+    const int j = batch_find(offs, n, blockIdx.x);
+    const TransposeJob J = jobs[j];
+    if (J.done && *J.done) return;
+    int b = blockIdx.x - offs[j];
+    const int gx = (J.N + 31) / 32;
+    const int bx = b % gx, by = (b / gx) % gx, bz = b / (gx * gx);
+    transpose_body(J.vol, J.volT, J.N, bx, by, bz);
+}
+
+__global__ void __launch_bounds__(1024 + 32) k_project_batch(const ProjectJob *__restrict__ jobs,
+                                                             const int *__restrict__ offs, int n, int *err) {
+    extern __shared__ __align__(128) float psm[];
+    const int j = batch_find(offs, n, blockIdx.x);
+    const ProjectJob J = jobs[j];
+    if (J.done && *J.done) return;
+    const int b = blockIdx.x - offs[j];
+    const int rays = (J.N + 31) / 32 * 32;
+    if ((int)threadIdx.x >= rays * kProjAnglesPerBlock + 32) {
+        // threads beyond this problem's block shape take no part (barrier counts use its shape)
+        __syncthreads();
+        return;
+    }
+    project_pipe_body(J.vol, J.volT, J.ang, J.agroups, J.proj, J.N, J.Nz, rays, err, b % J.n_agroups,
+                      b / J.n_agroups, psm);
+}
+
+__global__ void __launch_bounds__(256) k_backproject_batch(const BackprojectJob *__restrict__ jobs,
+                                                           const int *__restrict__ offs, int n) {
+    const int j = batch_find(offs, n, blockIdx.x);
+    const BackprojectJob J = jobs[j];
+    if (J.done && *J.done) return;
+    const int b = blockIdx.x - offs[j];
+    const int gx = (J.N + 31) / 32, gy = (J.N + 7) / 8;
+    backproject_body(J.proj, J.ang, J.vol, J.N, J.Nz, J.M, b % gx, (b / gx) % gy, b / (gx * gy));
+}
+
+int transpose_blocks(int N, int Nz) { return ((N + 31) / 32) * ((N + 31) / 32) * Nz; }
+int project_blocks(int n_agroups, int Nz) { return n_agroups * ((Nz + kZc - 1) / kZc); }
+int backproject_blocks(int N, int Nz) { return ((N + 31) / 32) * ((N + 7) / 8) * ((Nz + kZc - 1) / kZc); }
+
+void launch_transpose_batch(const TransposeJob *jobs, const int *offs, int n, int total, cudaStream_t st) {
+    k_transpose_batch<<<total, dim3(32, 8), 0, st>>>(jobs, offs, n);
+}
+
+void launch_project_batch(const ProjectJob *jobs, const int *offs, int n, int total, int maxN, int *err,
+                          cudaStream_t st) {
+    const int rays = (maxN + 31) / 32 * 32;
+    const size_t smem = sizeof(float) * kPStages * kZc * maxN + 16 * kPStages;
+    cudaFuncSetAttribute(k_project_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_project_batch<<<total, rays * kProjAnglesPerBlock + 32, smem, st>>>(jobs, offs, n, err);
+}
+
+void launch_backproject_batch(const BackprojectJob *jobs, const int *offs, int n, int total, cudaStream_t st) {
+    k_backproject_batch<<<total, dim3(32, 8), 0, st>>>(jobs, offs, n);
 }
 
 }  // namespace mpiffl
