@@ -7,7 +7,14 @@ samples), harmonics 1..16 kept at +-4 bins. Inputs are synthetic (a seeded
 mouse-like phantom). Prints one JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--precision fp32|bf16x3|tf32] [--workload invivo|phantom|tiny]
+                  [--path staged|fused|line_gemm|full_gemm] [--workload invivo|phantom|tiny]
+                  [--serving-requests 64] [--recon-iters 100] [--no-cpu-baseline] [--quick]
+
+The headline `value` is the full-GEMM path (the operator with S D F V E H
+precomputed per trajectory, on tensor cores in split bf16 with FP32 accuracy);
+`paths` reports every evaluation path of the same operator, `recon` seconds per
+reconstruction, `serving` the continuous-batching run of the serving workload
+against one-at-a-time plain FP32.
 
 --impl reference times the FP64 CPU oracle on the host cores on a bounded
 sample of the same workload (a subset of angles), scaled to pairs/s.
@@ -179,10 +186,101 @@ ALGO_BYTES = {
 }
 
 
+def _timed_pairs(op, x, b, xa, steps, flush, stream):
+    """Time `steps` A+A^T pairs (CUDA events per step, L2 flushed between steps); returns ms."""
+    import torch
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    for k in range(steps):
+        flush.zero_()
+        starts[k].record(stream)
+        op.forward(x, out=b)
+        op.adjoint(b, out=xa)
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    return sum(s_.elapsed_time(e) for s_, e in zip(starts, ends))
+
+
+def serving_bench(n_requests, iters, seed=0):
+    """The serving workload: a Poisson stream of mixed reconstruction requests.
+
+    Requests follow the serving recipe (64^3 .. 256^2x128 volumes, 8-36 angles,
+    harmonics 1..K, K in 8..16); data are b = A x + complex Gaussian noise (0.5 % of
+    max |b|) from seeded phantoms, computed on the GPU before the run. The sequential
+    plain-FP32 baseline solves one request at a time with the staged FP32 path; the
+    arrival rate is 1.5x its measured throughput and its latencies follow from its
+    measured per-request service times (single FIFO server). The batched server then
+    replays the same arrivals live.
+    """
+    import torch
+
+    from paper_2511_06627_gb300 import FFLOperator
+    from paper_2511_06627_gb300.serving import ReconServer, Request, percentile
+    from phantoms.configs import serving_mix
+
+    mix = serving_mix(seed=seed, n_requests=n_requests)
+    keys = ("nx", "nz", "n_angles", "S", "P", "A", "phi0", "zigzag", "Q", "fwhm", "k_min", "k_max", "half_width")
+    phantoms = {}
+    reqs = []
+    gen = torch.Generator(device="cuda").manual_seed(seed)
+    for i, c in enumerate(mix):
+        g = {k: c[k] for k in keys}
+        key = (c["nx"], c["nz"])
+        if key not in phantoms:
+            phantoms[key] = torch.from_numpy(phantom_for(c, seed=seed)).cuda()
+        op = FFLOperator(**g)
+        op.set_path("line_gemm")
+        b = op.forward(phantoms[key])
+        sig = 0.005 * float(b.abs().max())
+        b += sig * torch.randn(b.shape, device="cuda", generator=gen)
+        torch.cuda.synchronize()
+        op.close()
+        reqs.append(Request(geometry=g, data=b, iters=iters, n_power=20, name=f"req{i}"))
+    # sequential plain FP32: measured service time per request (handle set-up + solve)
+    service = []
+    for r in reqs:
+        t0 = time.perf_counter()
+        op = FFLOperator(**r.geometry)
+        op.solve(r.data, iters=r.iters, n_power=r.n_power, report=False)
+        torch.cuda.synchronize()
+        service.append(time.perf_counter() - t0)
+        op.close()
+    rate = 1.5 / (sum(service) / len(service))
+    rng = np.random.default_rng(seed + 1)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=len(reqs)))
+    arrivals -= arrivals[0]
+    t_free, seq_lat = 0.0, []
+    for a, s_ in zip(arrivals, service):
+        start = max(a, t_free)
+        t_free = start + s_
+        seq_lat.append(t_free - a)
+    seq_makespan = t_free
+    for r, a in zip(reqs, arrivals):
+        r.arrival = float(a)
+    server = ReconServer(hbm_budget_bytes=150 * 2**30, path="full_gemm", max_active=64, poll_every=4,
+                         keep_results=False)
+    t0 = time.perf_counter()
+    done = server.run(reqs)
+    makespan = time.perf_counter() - t0
+    lat = [r.latency for r in done]
+    return {
+        "requests": len(reqs), "iters_per_request": iters, "arrival_rate_per_s": rate,
+        "batched": {"recons_per_s": len(done) / makespan, "p50_s": percentile(lat, 50), "p99_s": percentile(lat, 99),
+                    "path": "full_gemm (bf16x3 tensor cores), continuous batching", "peak_hbm_bytes": server.peak_bytes,
+                    "batched_steps": server.steps},
+        "sequential_plain_fp32": {"recons_per_s": len(reqs) / seq_makespan, "p50_s": percentile(seq_lat, 50),
+                                  "p99_s": percentile(seq_lat, 99),
+                                  "note": "staged FP32 path, one request at a time; latencies from measured service "
+                                          "times under the same arrivals"},
+        "hbm_budget_bytes": 150 * 2**30,
+    }
+
+
 def run_ours(args, cfg, rank, world, local_rank):
     import torch
 
-    from paper_2511_06627_gb300 import PREC_BF16X3, PREC_FP32, PREC_TF32, FFLOperator
+    from paper_2511_06627_gb300 import FFLOperator
 
     torch.cuda.set_device(local_rank)
     dist = None
@@ -190,13 +288,13 @@ def run_ours(args, cfg, rank, world, local_rank):
         import torch.distributed as dist
 
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
-    prec = {"fp32": PREC_FP32, "bf16x3": PREC_BF16X3, "tf32": PREC_TF32}[args.precision]
-    op = FFLOperator.from_config(cfg, precision=prec)
-    if args.path:
-        op.set_path(args.path)
+    path = args.path or ("staged" if args.plain else "full_gemm")
+    op = FFLOperator.from_config(cfg)
+    op.set_path(path)
     sz = op.sizes
     dims = dict(nvox=sz.n_vox, nproj=sz.n_proj, nfine=sz.n_fine, nsig=sz.n_sig, ndata=sz.n_data)
-    x_host = torch.from_numpy(phantom_for(cfg)).pin_memory()
+    x_np = phantom_for(cfg)
+    x_host = torch.from_numpy(x_np).pin_memory()
     x = x_host.cuda()
     b = op.new_data()
     xa = op.new_volume()
@@ -230,7 +328,7 @@ def run_ours(args, cfg, rank, world, local_rank):
     launches = op.launch_count() - launches0
     prof = op.profile_read()
     op.profile(False)
-    ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    ms = sum(s_.elapsed_time(e) for s_, e in zip(starts, ends))
     if dist:
         t = torch.tensor([ms], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -268,18 +366,43 @@ def run_ours(args, cfg, rank, world, local_rank):
     algo = ALGO_BYTES[top](dims)
     achieved = algo / (per_launch_ms / 1e3) / 1e9
     kernel_share = {k: round(v[0] / max(ms, 1e-9), 4) for k, v in prof.items() if v[1] > 0}
+    kernel_ms = {k: round(v[0] / v[1], 4) for k, v in prof.items() if v[1] > 0}
+
+    # ---- the other evaluation paths of the same operator (same inputs, same timing rules)
+    paths = {path: {"pairs_per_s": value, "ms_per_pair": ms / args.steps}}
+    if not args.quick:
+        for p in ("staged", "fused", "line_gemm", "full_gemm"):
+            if p in paths:
+                continue
+            try:
+                op.set_path(p)
+            except Exception as exc:  # shape not taken by that path
+                paths[p] = {"unsupported": str(exc)}
+                continue
+            for _ in range(2):
+                step()
+            pm = _timed_pairs(op, x, b, xa, max(3, args.steps // 2), flush, stream)
+            n = max(3, args.steps // 2)
+            paths[p] = {"pairs_per_s": n / (pm / 1e3), "ms_per_pair": pm / n}
+        op.set_path(path)
+    plain = paths.get("staged", {}).get("pairs_per_s")
 
     result = {
         "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else args.precision, "data": "synthetic",
-        "config": {"workload": workload_desc(cfg), "precision": args.precision,
-                   "l2": "flushed (256 MB write) between timed steps; time signal 1.2 GB > L2",
+        "vs_baseline": None,
+        "dtype": "f32" if path == "staged" else "f32 (line stage on tensor cores as bf16 hi+lo, 3 products, f32 acc)",
+        "data": "synthetic",
+        "config": {"workload": workload_desc(cfg), "path": path,
+                   "l2": "flushed (256 MB write) between timed steps",
                    "step": "b = A x then x' = A^T b, inputs resident in HBM"},
         "roofline": {"kernel": top, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": None, "peak_source": src,
                      "algorithmic_bytes_per_launch": algo, "avg_launch_ms": per_launch_ms},
         "kernel_time_share": kernel_share,
+        "kernel_ms_per_launch": kernel_ms,
+        "paths": paths,
+        "speedup_vs_plain_fp32": (value / plain) if plain else None,
         "e2e": {"value": pairs / (e2e_ms / 1e3), "unit": "pairs/s", "h2d_bytes_per_step": 4 * sz.n_vox,
                 "d2h_bytes_per_step": 4 * sz.n_vox},
         "clocks": clk.summary(),
@@ -287,28 +410,75 @@ def run_ours(args, cfg, rank, world, local_rank):
         "wall_s_timed_region": t_wall,
     }
     if args.recon_iters > 0:
-        # seconds per reconstruction: the solve of Eq. (26) on data b = A x (noise-free)
-        bd = op.forward(x)
-        ata = op.power_norm(20, 1234)
-        torch.cuda.synchronize()
-        r0 = torch.cuda.Event(enable_timing=True)
-        r1 = torch.cuda.Event(enable_timing=True)
-        r0.record(stream)
-        _, rep = op.solve(bd, iters=args.recon_iters, ata_norm=ata, report=False)
-        r1.record(stream)
-        torch.cuda.synchronize()
-        result["recon"] = {"s_per_recon": r0.elapsed_time(r1) / 1e3, "iters": args.recon_iters,
-                           "note": "tau, lambda from a 20-step power iteration done beforehand"}
+        # seconds per reconstruction (Eq. (26), 100 iterations, lambda by default rule) on b = A x
+        bd = op.forward(x).clone()
+        rec = {}
+        xs = {}
+        for p in ([path, "staged"] if path != "staged" else ["staged"]):
+            op.set_path(p)
+            ata = op.power_norm(20, 1234)
+            torch.cuda.synchronize()
+            r0 = torch.cuda.Event(enable_timing=True)
+            r1 = torch.cuda.Event(enable_timing=True)
+            r0.record(stream)
+            xr, _ = op.solve(bd, iters=args.recon_iters, ata_norm=ata, report=False)
+            r1.record(stream)
+            torch.cuda.synchronize()
+            xs[p] = xr
+            rec[p] = {"s_per_recon": r0.elapsed_time(r1) / 1e3, "iters": args.recon_iters}
+        if len(xs) == 2:
+            a_, b_ = xs[path].double(), xs["staged"].double()
+            rec["rel_l2_between_paths"] = float((a_ - b_).norm() / b_.norm())
+        rec["note"] = "tau from a 20-step power iteration done before the timed solve"
+        result["recon"] = rec
+        op.set_path(path)
+    if args.serving_requests > 0 and world == 1:
+        result["serving"] = serving_bench(args.serving_requests, args.serving_iters)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        xo = phantom_for(cfg).astype(np.float64)
-        per, text = oracle_pair_seconds(cfg, xo, max(1, min(cfg["n_angles"], args.oracle_angles)))
-        result["cpu_baseline"] = {"value": 1.0 / per, "unit": "pairs/s", "cores": cores(), "kind": "oracle",
-                                  "sample": text}
+        result["cpu_baseline"] = cpu_baseline_leg(cfg, x_np, op, args)
     if rank == 0:
         print(json.dumps(result), flush=True)
     op.close()
     if dist:
         dist.destroy_process_group()
+
+
+def cpu_baseline_leg(cfg, x_np, op, args):
+    """The FP64 oracle timed on the host cores on a bounded sample (a subset of the
+    angles), plus the error of every GPU evaluation path against the oracle on that
+    same sample (one angle of A x and the matching one-angle A^T y)."""
+    import torch
+
+    from oracle import Setup, operator
+
+    xo = x_np.astype(np.float64)
+    nang = max(1, min(cfg["n_angles"], args.oracle_angles))
+    per, text = oracle_pair_seconds(cfg, xo, nang)
+    st = Setup.from_config(cfg)
+    m = 0
+    fs = operator.forward_stages(xo, st, angles=np.array([m]))
+    ref_b = fs["data"][0]
+    rng = np.random.default_rng(9)
+    y = rng.standard_normal(ref_b.shape) + 1j * rng.standard_normal(ref_b.shape)
+    ref_x = operator.adjoint_stages(y[None], st, angles=np.array([m]))["vol"]
+    y_full = np.zeros(st.data_shape, dtype=np.complex128)
+    y_full[m] = y
+    y_dev = torch.from_numpy(np.stack([y_full.real, y_full.imag], -1).astype(np.float32)).cuda()
+    x_dev = torch.from_numpy(x_np).cuda()
+    errs = {}
+    for p in ("staged", "fused", "line_gemm", "full_gemm"):
+        try:
+            op.set_path(p)
+        except Exception:
+            continue
+        bb = op.forward(x_dev)[m].cpu().numpy().astype(np.float64)
+        xx = op.adjoint(y_dev).cpu().numpy().astype(np.float64)
+        got_b = bb[..., 0] + 1j * bb[..., 1]
+        errs[p] = {"forward_rel_l2": float(np.linalg.norm(got_b - ref_b) / np.linalg.norm(ref_b)),
+                   "adjoint_rel_l2": float(np.linalg.norm(xx - ref_x) / np.linalg.norm(ref_x))}
+    return {"value": 1.0 / per, "unit": "pairs/s", "cores": cores(), "kind": "oracle", "sample": text,
+            "gpu_error_vs_oracle": errs,
+            "error_sample": f"angle {m}: A x on the phantom, A^T y for random y on that angle"}
 
 
 def main():
@@ -317,12 +487,15 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16x3", "tf32"])
     ap.add_argument("--path", default=None, choices=["staged", "fused", "line_gemm", "full_gemm"])
     ap.add_argument("--workload", default="invivo", choices=["invivo", "phantom", "tiny"])
     ap.add_argument("--oracle-angles", type=int, default=1)
     ap.add_argument("--recon-iters", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serving-requests", type=int, default=64)
+    ap.add_argument("--serving-iters", type=int, default=100)
+    ap.add_argument("--plain", action="store_true", help="time the staged FP32 path as the headline")
+    ap.add_argument("--quick", action="store_true", help="skip the other evaluation paths")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -633,7 +633,6 @@ extern "C" int mpi_ffl_create(const mpi_ffl_geometry *geom, const mpi_ffl_trajec
         dev_alloc(h, &h->w_err, 1);
         CK(cudaMemset(h->w_err, 0, sizeof(int)));
         tc_init(h);
-        col_init(h);
         CK(cudaDeviceSynchronize());
     } catch (const Fail &e) {
         if (g_create_error.empty()) g_create_error = h->err.empty() ? "create failed" : h->err;
@@ -713,6 +712,14 @@ extern "C" int mpi_ffl_set_path(mpi_ffl_handle *h, int32_t path) {
         h->err = "unknown path";
         return MPI_FFL_ERR_INVALID_ARG;
     }
+    if ((path == MPI_FFL_PATH_LINE_GEMM || path == MPI_FFL_PATH_FULL_GEMM) && !h->col_state) {
+        try {
+            col_init(h);  // W and W H are built on first use
+        } catch (...) {
+            h->err = "building the collapsed line operator failed";
+            return MPI_FFL_ERR_OOM;
+        }
+    }
     if ((path == MPI_FFL_PATH_FUSED && !tc_supported(h)) ||
         ((path == MPI_FFL_PATH_LINE_GEMM || path == MPI_FFL_PATH_FULL_GEMM) && !col_supported(h))) {
         h->err = "this path does not support the problem shape";
@@ -751,10 +758,12 @@ extern "C" int mpi_ffl_set_psf_fwhm(mpi_ffl_handle *h, double fwhm) {
         CK(cudaMemcpy(h->t_htab, ht.data(), sizeof(float) * ht.size(), cudaMemcpyHostToDevice));
         CK(cudaMemcpy(h->t_dhtab, dht.data(), sizeof(float) * dht.size(), cudaMemcpyHostToDevice));
         tc_tables_changed(h);
-        // W H holds the PSF: rebuild the collapsed operator
+        // W H holds the PSF: rebuild the collapsed operator if it was built
         const bool had = col_supported(h);
-        col_release(h);
-        col_init(h);
+        if (h->col_state) {
+            col_release(h);
+            col_init(h);
+        }
         if (had && !col_supported(h) && (h->path == MPI_FFL_PATH_LINE_GEMM || h->path == MPI_FFL_PATH_FULL_GEMM)) {
             h->path = MPI_FFL_PATH_STAGED;
             h->precision = MPI_FFL_PREC_FP32;

@@ -22,6 +22,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <thread>
 #include <vector>
 
 #include "collapsed.h"
@@ -419,15 +420,24 @@ void col_init(mpi_ffl_handle *h) {
         std::vector<double> Wt((size_t)d.Ne * R), WH((size_t)R * d.N, 0.0), WHt((size_t)d.N * R);
         for (int o = 0; o < R; ++o)
             for (int e = 0; e < d.Ne; ++e) Wt[(size_t)e * R + o] = Wr[(size_t)o * d.Ne + e];
-        for (int o = 0; o < R; ++o) {
-            double *out = WH.data() + (size_t)o * d.N;
-            const double *wrow = Wr.data() + (size_t)o * d.Ne;
-            for (int e = 0; e < d.Ne; ++e) {
-                const double w = wrow[e];
-                if (w == 0.0) continue;
-                const double *hrow = Hm.data() + (size_t)e * d.N;
-                for (int i = 0; i < d.N; ++i) out[i] += w * hrow[i];
-            }
+        {
+            // rows of W H on the host's cores (each row is independent)
+            const int nt = std::max(1, std::min<int>(R, (int)std::thread::hardware_concurrency()));
+            std::vector<std::thread> pool;
+            for (int t = 0; t < nt; ++t)
+                pool.emplace_back([&, t]() {
+                    for (int o = t; o < R; o += nt) {
+                        double *out = WH.data() + (size_t)o * d.N;
+                        const double *wrow = Wr.data() + (size_t)o * d.Ne;
+                        for (int e = 0; e < d.Ne; ++e) {
+                            const double w = wrow[e];
+                            if (w == 0.0) continue;
+                            const double *hrow = Hm.data() + (size_t)e * d.N;
+                            for (int i = 0; i < d.N; ++i) out[i] += w * hrow[i];
+                        }
+                    }
+                });
+            for (auto &th : pool) th.join();
         }
         for (int o = 0; o < R; ++o)
             for (int i = 0; i < d.N; ++i) WHt[(size_t)i * R + o] = WH[(size_t)o * d.N + i];

@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(256) k_psf_fwd(const float *__restrict__ proj,
 void launch_psf_fwd(const float *proj, const float *htab, float *fine, const Dims &d, cudaStream_t st) {
     const size_t smem = sizeof(float) * (d.N + d.htab_len);
     if (smem > 48 * 1024)
-        cudaFuncSetAttribute(k_psf_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_psf_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     k_psf_fwd<<<d.nseg, 256, smem, st>>>(proj, htab, fine, d);
 }
 
@@ -132,7 +132,7 @@ void launch_psf_adj(const float *fine, const float *htab, float *proj, const Dim
     const int stride = d.Ne + (((d.Q - d.Ne) % 32) + 32) % 32;  // stride = Q (mod 32)
     const size_t smem = sizeof(float) * (d.htab_len + (size_t)segs * stride);
     if (smem > 48 * 1024)
-        cudaFuncSetAttribute(k_psf_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_psf_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     k_psf_adj<<<(d.nseg + segs - 1) / segs, kPsfAdjThreads, smem, st>>>(fine, htab, proj, d, stride, segs);
 }
 
@@ -314,7 +314,7 @@ static void dft_fwd_hw(const float *sig, const float *tw1, const float2 *tw2_ro,
     const int W = 2 * HW + 1;
     const size_t smem = sizeof(float) * d.P * W + sizeof(float2) * d.S * W;
     if (smem > 48 * 1024)
-        cudaFuncSetAttribute(k_dft_fwd<HW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_dft_fwd<HW>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     k_dft_fwd<HW><<<d.nseg, 128, smem, st>>>(sig, tw1, tw2_ro, dgam, data, d, (float)(1.0 / sqrt((double)d.L)));
 }
 
@@ -324,7 +324,7 @@ static void dft_adj_hw(const float *data, const float *tw1, const float2 *tw2_qr
     const int W = 2 * HW + 1;
     const size_t smem = sizeof(float) * d.P * W + sizeof(float2) * d.nb;
     if (smem > 48 * 1024)
-        cudaFuncSetAttribute(k_dft_adj<HW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_dft_adj<HW>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     k_dft_adj<HW><<<d.nseg, 128, smem, st>>>(data, tw1, tw2_qr, dgam, sig, d, (float)(1.0 / sqrt((double)d.L)));
 }
 

@@ -216,7 +216,7 @@ void launch_project(const float *vol, const float *volT, const AngleParam *ang, 
     if (N % 4 == 0 && err) {
         const size_t smem = sizeof(float) * kPStages * kZc * N + 16 * kPStages;
         if (smem > 48 * 1024)
-            cudaFuncSetAttribute(k_project_pipe, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaFuncSetAttribute(k_project_pipe, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
         dim3 grid(n_agroups, (Nz + kZc - 1) / kZc);
         k_project_pipe<<<grid, rays * kProjAnglesPerBlock + 32, smem, st>>>(vol, volT, ang, agroups, proj, N, Nz,
                                                                             rays, err);
@@ -225,7 +225,7 @@ void launch_project(const float *vol, const float *volT, const AngleParam *ang, 
     const int threads = rays * kProjAnglesPerBlock;
     const size_t smem = sizeof(float) * 2 * kZc * N;
     if (smem > 48 * 1024)
-        cudaFuncSetAttribute(k_project, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_project, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     dim3 grid(n_agroups, (Nz + kZc - 1) / kZc);
     k_project<<<grid, threads, smem, st>>>(vol, volT, ang, agroups, proj, N, Nz, rays);
 }
@@ -352,7 +352,7 @@ void launch_project_batch(const ProjectJob *jobs, const int *offs, int n, int to
                           cudaStream_t st) {
     const int rays = (maxN + 31) / 32 * 32;
     const size_t smem = sizeof(float) * kPStages * kZc * maxN + 16 * kPStages;
-    cudaFuncSetAttribute(k_project_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_project_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     k_project_batch<<<total, rays * kProjAnglesPerBlock + 32, smem, st>>>(jobs, offs, n, err);
 }
 

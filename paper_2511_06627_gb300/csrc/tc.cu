@@ -777,8 +777,9 @@ void tc_init(mpi_ffl_handle *h) {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&s->n_sm, cudaDevAttrMultiProcessorCount, dev);
-    cudaFuncSetAttribute(k_tc_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.f_total);
-    cudaFuncSetAttribute(k_tc_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.a_total);
+    // the attribute is global to the kernel: allow the largest carve-up any handle may use
+    cudaFuncSetAttribute(k_tc_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(k_tc_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     cudaGetLastError();
     s->ok = true;
 }

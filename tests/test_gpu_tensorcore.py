@@ -97,3 +97,16 @@ def test_unsupported_shape_refuses_tensor_cores():
     op = FFLOperator(nx=16, nz=3, n_angles=2, S=24, P=10, A=3.0, Q=4, fwhm=2.0, k_min=1, k_max=3, half_width=1)
     with pytest.raises(MpiFflError):
         op.set_precision(PREC_BF16X3)
+
+
+def test_handles_of_different_shapes_coexist():
+    """Kernel launch attributes are process-wide: a later handle with a smaller
+    shared-memory carve-up must not break an earlier, larger one."""
+    from paper_2511_06627_gb300 import PREC_BF16X3
+
+    st_big, op_big = _make("s64", PREC_BF16X3)
+    st_small, op_small = _make("tiny", PREC_BF16X3)
+    x = random_volume(st_big.nz, st_big.nx, seed=33).astype(np.float32)
+    b = op_big.forward(_t(x))
+    op_big.sync_check()
+    assert rel_l2(b.cpu().numpy(), to_interleaved(operator.forward(x, st_big))) < OP_TOL
