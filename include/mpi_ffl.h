@@ -59,7 +59,7 @@ extern "C" {
 /* Arithmetic of the harmonic-band DFT and its transpose (the other stages are FP32). */
 #define MPI_FFL_PREC_FP32 0   /* plain: FP32 FMA on CUDA cores, stage by stage        */
 #define MPI_FFL_PREC_BF16X3 1 /* tensor cores: bf16 hi+lo split, 3 products, FP32 acc  */
-#define MPI_FFL_PREC_TF32 2   /* tensor cores: tf32 operands, FP32 accumulate          */
+#define MPI_FFL_PREC_TF32 2   /* tensor cores: tf32 hi+lo split, 3 products, FP32 acc  */
 
 /* How A and A^T are evaluated (the operator is the same; only the order of evaluation
  * and the arithmetic differ):
@@ -165,8 +165,12 @@ int mpi_ffl_get_sizes(const mpi_ffl_handle *h, mpi_ffl_sizes *out);
 
 /* Arithmetic of the line stages for forward/adjoint/solve (MPI_FFL_PREC_*). FP32
  * selects the STAGED path; BF16X3 keeps a tensor-core path, or selects FUSED when the
- * path was STAGED. TF32 returns MPI_FFL_ERR_UNSUPPORTED in this version. */
+ * path was STAGED. TF32 (22 of 24 mantissa bits per operand, about 8x smaller error
+ * than BF16X3) applies to the two GEMM paths and returns MPI_FFL_ERR_UNSUPPORTED on
+ * the others. set_path keeps TF32 when moving between the GEMM paths. */
 int mpi_ffl_set_precision(mpi_ffl_handle *h, int32_t precision);
+/* Current precision (MPI_FFL_PREC_*), or MPI_FFL_ERR_INVALID_ARG for a NULL handle. */
+int mpi_ffl_get_precision(const mpi_ffl_handle *h);
 
 /* Evaluation path (MPI_FFL_PATH_*); returns MPI_FFL_ERR_UNSUPPORTED when the shape is
  * outside what the path's kernels accept (the handle keeps its previous path). */

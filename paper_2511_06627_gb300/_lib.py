@@ -69,6 +69,12 @@ class Sizes(C.Structure):
                 ("fine_len", C.c_int32), ("line_len", C.c_int32), ("workspace_bytes", C.c_int64)]
 
 
+class JobStatus(C.Structure):
+    _fields_ = [("iters_done", C.c_int32), ("stopped", C.c_int32), ("finished", C.c_int32),
+                ("residual_first", C.c_double), ("residual_last", C.c_double), ("tau", C.c_double),
+                ("lambda_", C.c_double), ("device_bytes", C.c_int64)]
+
+
 H = C.c_void_p
 FP = C.c_void_p  # device float* (passed as integer addresses)
 ST = C.c_void_p  # cudaStream_t
@@ -82,6 +88,7 @@ PROTOTYPES = {
     "mpi_ffl_set_precision": (C.c_int, [H, C.c_int32]),
     "mpi_ffl_set_path": (C.c_int, [H, C.c_int32]),
     "mpi_ffl_get_path": (C.c_int, [H]),
+    "mpi_ffl_get_precision": (C.c_int, [H]),
     "mpi_ffl_set_gain": (C.c_int, [H, C.POINTER(C.c_float)]),
     "mpi_ffl_set_psf_fwhm": (C.c_int, [H, C.c_double]),
     "mpi_ffl_sync_check": (C.c_int, [H, ST]),
@@ -100,6 +107,13 @@ PROTOTYPES = {
     "mpi_ffl_profile_enable": (C.c_int, [H, C.c_int32]),
     "mpi_ffl_profile_read": (C.c_int, [H, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "mpi_ffl_launch_count": (C.c_int64, [H]),
+    "mpi_ffl_job_create": (C.c_int, [H, FP, FP, C.POINTER(SolveParams), C.POINTER(C.c_void_p), ST]),
+    "mpi_ffl_job_step": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, ST]),
+    "mpi_ffl_job_status": (C.c_int, [C.c_void_p, C.POINTER(JobStatus), ST]),
+    "mpi_ffl_job_flags": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p)]),
+    "mpi_ffl_job_poll": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.c_void_p, ST]),
+    "mpi_ffl_job_result": (C.c_int, [C.c_void_p, FP, ST]),
+    "mpi_ffl_job_destroy": (C.c_int, [C.c_void_p]),
 }
 
 KERNEL_KINDS = ["transpose", "project", "backproject", "psf_fwd", "psf_adj", "resample_fwd", "resample_adj",

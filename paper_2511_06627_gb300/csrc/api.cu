@@ -687,8 +687,12 @@ extern "C" int mpi_ffl_set_precision(mpi_ffl_handle *h, int32_t precision) {
         return MPI_FFL_ERR_INVALID_ARG;
     }
     if (precision == MPI_FFL_PREC_TF32) {
-        h->err = "TF32 line kernels are not built in this version";
-        return MPI_FFL_ERR_UNSUPPORTED;
+        if (h->path != MPI_FFL_PATH_LINE_GEMM && h->path != MPI_FFL_PATH_FULL_GEMM) {
+            h->err = "TF32 splits are built for the GEMM paths only";
+            return MPI_FFL_ERR_UNSUPPORTED;
+        }
+        h->precision = precision;
+        return MPI_FFL_OK;
     }
     if (precision == MPI_FFL_PREC_FP32) {
         h->precision = precision;
@@ -725,12 +729,19 @@ extern "C" int mpi_ffl_set_path(mpi_ffl_handle *h, int32_t path) {
         h->err = "this path does not support the problem shape";
         return MPI_FFL_ERR_UNSUPPORTED;
     }
+    const bool keep_tf32 = h->precision == MPI_FFL_PREC_TF32 &&
+                           (path == MPI_FFL_PATH_LINE_GEMM || path == MPI_FFL_PATH_FULL_GEMM);
     h->path = path;
-    h->precision = path == MPI_FFL_PATH_STAGED ? MPI_FFL_PREC_FP32 : MPI_FFL_PREC_BF16X3;
+    h->precision = path == MPI_FFL_PATH_STAGED ? MPI_FFL_PREC_FP32
+                   : keep_tf32                 ? MPI_FFL_PREC_TF32
+                                               : MPI_FFL_PREC_BF16X3;
     return MPI_FFL_OK;
 }
 
 extern "C" int mpi_ffl_get_path(const mpi_ffl_handle *h) { return h ? h->path : MPI_FFL_ERR_INVALID_ARG; }
+extern "C" int mpi_ffl_get_precision(const mpi_ffl_handle *h) {
+    return h ? h->precision : MPI_FFL_ERR_INVALID_ARG;
+}
 
 extern "C" int mpi_ffl_set_gain(mpi_ffl_handle *h, const float *gain) {
     return guarded(h, [&]() {

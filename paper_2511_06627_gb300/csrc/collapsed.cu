@@ -13,7 +13,8 @@
 // alternate Re and Im, so the data stay in their interleaved complex layout.
 //
 // GEMM kernel: C[row] = scale[row] * sum_k A[row][k] B[n][k] on tcgen05 with the
-// FP32 operands split into bf16 hi + lo (hi*hi + hi*lo + lo*hi, FP32 accumulate).
+// FP32 operands split into bf16 or tf32 hi + lo (hi*hi + hi*lo + lo*hi, FP32
+// accumulate): bf16 parts keep 16 mantissa bits of each operand, tf32 parts 22.
 // Warps 0-3 convert A rows (gathered by an index list) into the canonical K-major
 // shared-memory layout and run the epilogue; warp 4 issues the MMAs; warp 5 streams
 // the pre-split B operand with bulk copies. Stages are handed over with mbarriers.
@@ -55,7 +56,38 @@ struct GemmArgs {
     uint32_t tmem_cols;
     int *err;
     const int *done;     // nonzero: the problem is finished, its blocks do nothing
+    int tf32;            // 1: tf32 hi + lo operands (32 K elements per stage), 0: bf16 (64)
+    int nacc;            // accumulators in TMEM: K chunk kc adds into accumulator kc % nacc
+    int acc_stride;      // TMEM columns between accumulators (a multiple of 32, >= BN)
 };
+
+// The tensor-core accumulation into TMEM is not round-to-nearest FP32, so its error
+// grows with the number of MMAs chained into one accumulator. K chunks are spread
+// over nacc accumulators (as many as fit two blocks per SM into the 512 TMEM
+// columns, at most 4), which the epilogue adds in FP32.
+void set_accumulators(GemmArgs &g) {
+    g.acc_stride = (g.BN + 31) / 32 * 32;
+    g.nacc = std::max(1, std::min({4, 256 / g.acc_stride, g.nkc}));
+    const int cols = g.nacc * g.acc_stride;
+    g.tmem_cols = cols <= 32 ? 32 : cols <= 64 ? 64 : cols <= 128 ? 128 : cols <= 256 ? 256 : 512;
+}
+
+// tf32 hi + lo split of 4 floats (round to nearest, ties away): hi = tf32(v), lo = tf32(v - hi)
+__device__ __forceinline__ uint32_t to_tf32(float v) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
+    return r;
+}
+__device__ __forceinline__ void split4_tf32(const float (&v)[4], uint4 &hi, uint4 &lo) {
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        h[i] = to_tf32(v[i]);
+        l[i] = to_tf32(v[i] - __uint_as_float(h[i]));
+    }
+    hi = make_uint4(h[0], h[1], h[2], h[3]);
+    lo = make_uint4(l[0], l[1], l[2], l[3]);
+}
 
 __device__ __forceinline__ void split8(const float (&v)[8], uint4 &hi, uint4 &lo) {
     uint32_t h[4], l[4];
@@ -101,10 +133,20 @@ __device__ __forceinline__ void gemm_body(const GemmArgs &g, int mt, int nt, uin
 
     if (warp < 4) {
         // ------------------------------------------------------------ A producers
-        const int row = tid;
-        const int gm = mt * kBM + row;
-        const int ar = gm < g.M ? __ldg(g.arow + gm) : -1;
-        const float *arow = ar >= 0 ? g.A + (size_t)ar * g.lda : nullptr;
+        // Warp w fills rows 32w..32w+31 of the tile. In one pass a lane takes row
+        // 32w + 8rg + (lane & 7) and 16-byte core-matrix row kg = 4kh + (lane >> 3)
+        // (8 bf16 or 4 tf32 values): 8 rows x 4 consecutive core-matrix rows per
+        // warp store, i.e. 512 contiguous shared-memory bytes, conflict-free; the
+        // global reads are 8 row segments of 128 (bf16) or 64 (tf32) bytes.
+        const int r7 = lane & 7, kq = lane >> 3;
+        const float *rp[4];
+#pragma unroll
+        for (int rg = 0; rg < 4; ++rg) {
+            const int gmr = mt * kBM + 32 * warp + 8 * rg + r7;
+            const int arr = gmr < g.M ? __ldg(g.arow + gmr) : -1;
+            rp[rg] = arr >= 0 ? g.A + (size_t)arr * g.lda : nullptr;
+        }
+        const bool vec = (g.lda % 4 == 0) && ((reinterpret_cast<uintptr_t>(g.A) & 15) == 0);
         bool ok = true;
         for (int kc = 0; kc < g.nkc; ++kc) {
             const int s = kc % g.stages;
@@ -113,39 +155,101 @@ __device__ __forceinline__ void gemm_body(const GemmArgs &g, int mt, int nt, uin
                 break;
             }
             uint8_t *sa = sm + s * stage;
-            const int k0 = kc * kBK;
-#pragma unroll 2
-            for (int kb = 0; kb < kBK / 8; ++kb) {
-                float v[8];
+            if (g.tf32) {
+                float4 v[8];
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
-                    const int k = k0 + kb * 8 + u;
-                    v[u] = (arow && k < g.Ka) ? __ldg(arow + k) : 0.f;
+                    const int rg = u >> 1, kg = 4 * (u & 1) + kq;
+                    const int k = kc * (kBK / 2) + kg * 4;
+                    const float *p = rp[rg];
+                    if (p && vec && k + 4 <= g.Ka) {
+                        v[u] = __ldg(reinterpret_cast<const float4 *>(p + k));
+                    } else {
+                        v[u].x = (p && k + 0 < g.Ka) ? __ldg(p + k + 0) : 0.f;
+                        v[u].y = (p && k + 1 < g.Ka) ? __ldg(p + k + 1) : 0.f;
+                        v[u].z = (p && k + 2 < g.Ka) ? __ldg(p + k + 2) : 0.f;
+                        v[u].w = (p && k + 3 < g.Ka) ? __ldg(p + k + 3) : 0.f;
+                    }
                 }
-                uint4 hi, lo;
-                split8(v, hi, lo);
-                const uint32_t off = (row / 8) * 1024u + kb * 128u + (row % 8) * 16u;
-                *reinterpret_cast<uint4 *>(sa + off) = hi;
-                *reinterpret_cast<uint4 *>(sa + bytesA + off) = lo;
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int rg = u >> 1, kg = 4 * (u & 1) + kq;
+                    const float f[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+                    uint4 hi, lo;
+                    split4_tf32(f, hi, lo);
+                    const uint32_t off = (4 * warp + rg) * 1024u + kg * 128u + r7 * 16u;
+                    *reinterpret_cast<uint4 *>(sa + off) = hi;
+                    *reinterpret_cast<uint4 *>(sa + bytesA + off) = lo;
+                }
+            } else {
+#pragma unroll 2
+                for (int h = 0; h < 2; ++h) {
+                    float4 v[8];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int rg = 2 * h + (u >> 1), kg = 4 * (u & 1) + kq;
+                        const int k = kc * kBK + kg * 8;
+                        const float *p = rp[rg];
+                        if (p && vec && k + 8 <= g.Ka) {
+                            v[2 * u] = __ldg(reinterpret_cast<const float4 *>(p + k));
+                            v[2 * u + 1] = __ldg(reinterpret_cast<const float4 *>(p + k + 4));
+                        } else {
+                            float t[8];
+#pragma unroll
+                            for (int e = 0; e < 8; ++e) t[e] = (p && k + e < g.Ka) ? __ldg(p + k + e) : 0.f;
+                            v[2 * u] = make_float4(t[0], t[1], t[2], t[3]);
+                            v[2 * u + 1] = make_float4(t[4], t[5], t[6], t[7]);
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int rg = 2 * h + (u >> 1), kg = 4 * (u & 1) + kq;
+                        const float f[8] = {v[2 * u].x,     v[2 * u].y,     v[2 * u].z,     v[2 * u].w,
+                                            v[2 * u + 1].x, v[2 * u + 1].y, v[2 * u + 1].z, v[2 * u + 1].w};
+                        uint4 hi, lo;
+                        split8(f, hi, lo);
+                        const uint32_t off = (4 * warp + rg) * 1024u + kg * 128u + r7 * 16u;
+                        *reinterpret_cast<uint4 *>(sa + off) = hi;
+                        *reinterpret_cast<uint4 *>(sa + bytesA + off) = lo;
+                    }
+                }
             }
             ptx::fence_proxy_async_smem();
             __syncwarp();
             if (lane == 0) ptx::mbar_arrive(&bars[s]);
         }
         // ------------------------------------------------------------ epilogue
+        // TMEM lane = tile row = tid (tcgen05.ld 32x32b: warp w reads lanes 32w..32w+31)
+        const int gm = mt * kBM + tid;
+        const int ar = gm < g.M ? __ldg(g.arow + gm) : -1;
         if (ok && ptx::mbar_wait_bounded(&bars[2 * g.stages], 0, kWait)) {
             ptx::tc_fence_after();
             const int cr = gm < g.M ? __ldg(g.crow + gm) : -1;
             const float sc = (cr >= 0 && g.rscale) ? __ldg(g.rscale + ar / g.rdiv) : 1.f;
             float *crow = cr >= 0 ? g.C + (size_t)cr * g.ldc : nullptr;
+            const bool vecc = (g.ldc % 4 == 0) && ((reinterpret_cast<uintptr_t>(g.C) & 15) == 0);
+            const int nacc = min(g.nacc, g.nkc);
             for (int c0 = 0; c0 < g.BN; c0 += 16) {
                 float v[16];
                 ptx::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + c0, v);
+                for (int a = 1; a < nacc; ++a) {
+                    float w[16];
+                    ptx::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(a * g.acc_stride + c0), w);
+#pragma unroll
+                    for (int u = 0; u < 16; ++u) v[u] += w[u];
+                }
                 const int n0 = nt * g.BN + c0;
                 if (crow) {
+                    if (vecc && n0 + 16 <= g.Nc) {
 #pragma unroll
-                    for (int u = 0; u < 16; ++u)
-                        if (n0 + u < g.Nc) crow[n0 + u] = sc * v[u];
+                        for (int u = 0; u < 4; ++u)
+                            *reinterpret_cast<float4 *>(crow + n0 + 4 * u) =
+                                make_float4(sc * v[4 * u], sc * v[4 * u + 1], sc * v[4 * u + 2], sc * v[4 * u + 3]);
+                    } else {
+#pragma unroll
+                        for (int u = 0; u < 16; ++u)
+                            if (n0 + u < g.Nc) crow[n0 + u] = sc * v[u];
+                    }
                 }
             }
         } else {
@@ -154,7 +258,7 @@ __device__ __forceinline__ void gemm_body(const GemmArgs &g, int mt, int nt, uin
     } else if (warp == 4) {
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
-            const uint32_t idesc = ptx::instr_desc(1, kBM, (uint32_t)g.BN);
+            const uint32_t idesc = ptx::instr_desc(g.tf32 ? 2 : 1, kBM, (uint32_t)g.BN);
             bool ok = true;
             for (int kc = 0; kc < g.nkc && ok; ++kc) {
                 const int s = kc % g.stages;
@@ -165,15 +269,23 @@ __device__ __forceinline__ void gemm_body(const GemmArgs &g, int mt, int nt, uin
                 ptx::tc_fence_after();
                 const uint32_t a0 = ptx::smem_u32(sm + s * stage);
                 const uint32_t b0 = a0 + 2 * bytesA;
+                const uint32_t tacc = tmem + (uint32_t)((kc % g.nacc) * g.acc_stride);
+                const bool first = kc < g.nacc;  // the first chunk of its accumulator
                 for (int ks = 0; ks < kBK / 16; ++ks) {
                     const uint64_t dAh = ptx::smem_desc(a0 + ks * 256, 128, 1024);
                     const uint64_t dAl = ptx::smem_desc(a0 + bytesA + ks * 256, 128, 1024);
                     const uint64_t dBh = ptx::smem_desc(b0 + ks * 256, 128, 1024);
                     const uint64_t dBl = ptx::smem_desc(b0 + bytesB + ks * 256, 128, 1024);
-                    ptx::mma_bf16(tmem, dAh, dBh, idesc, (kc > 0 || ks > 0) ? 1u : 0u);
-                    if (g.prec == MPI_FFL_PREC_BF16X3) {
-                        ptx::mma_bf16(tmem, dAh, dBl, idesc, 1u);
-                        ptx::mma_bf16(tmem, dAl, dBh, idesc, 1u);
+                    // 4 MMA K-steps of 256 bytes per stage: K = 16 bf16 or K = 8 tf32 elements
+                    const uint32_t acc = (!first || ks > 0) ? 1u : 0u;
+                    if (g.tf32) {
+                        ptx::mma_tf32(tacc, dAh, dBh, idesc, acc);
+                        ptx::mma_tf32(tacc, dAh, dBl, idesc, 1u);
+                        ptx::mma_tf32(tacc, dAl, dBh, idesc, 1u);
+                    } else {
+                        ptx::mma_bf16(tacc, dAh, dBh, idesc, acc);
+                        ptx::mma_bf16(tacc, dAh, dBl, idesc, 1u);
+                        ptx::mma_bf16(tacc, dAl, dBh, idesc, 1u);
                     }
                 }
                 ptx::mma_commit(&bars[g.stages + s]);
@@ -234,11 +346,25 @@ double bf16_value(uint16_t b) {
     return f;
 }
 
+uint32_t tf32_bits(double x) {
+    const float f = (float)x;
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    return (u + 0x1000u) & 0xFFFFE000u;  // round to nearest (ties away), 10-bit mantissa
+}
+double tf32_value(uint32_t b) {
+    float f;
+    std::memcpy(&f, &b, 4);
+    return f;
+}
+
 // Pre-split B operand for k_gemm_split: Bm is Nv x Kv (row-major, double); padded to
-// ntile*BN x nkc*kBK; blocks [tile][chunk][hi, lo] of BN x kBK in the canonical layout.
-std::vector<uint8_t> pack_b(const std::vector<double> &Bm, int Nv, int Kv, int BN, int &ntile, int &nkc) {
+// ntile*BN x nkc*(K per chunk); blocks [tile][chunk][hi, lo] of BN rows x 128 bytes per
+// row in the canonical layout (64 bf16 or 32 tf32 elements per row and chunk).
+std::vector<uint8_t> pack_b(const std::vector<double> &Bm, int Nv, int Kv, int BN, int &ntile, int &nkc, bool tf32) {
     ntile = (Nv + BN - 1) / BN;
-    nkc = (Kv + kBK - 1) / kBK;
+    const int kpc = tf32 ? kBK / 2 : kBK;
+    nkc = (Kv + kpc - 1) / kpc;
     const size_t blk = (size_t)BN * kBK * 2;
     std::vector<uint8_t> out((size_t)ntile * nkc * 2 * blk, 0);
     for (int t = 0; t < ntile; ++t)
@@ -247,14 +373,22 @@ std::vector<uint8_t> pack_b(const std::vector<double> &Bm, int Nv, int Kv, int B
             uint8_t *lo = hi + blk;
             for (int nl = 0; nl < BN; ++nl) {
                 const int n = t * BN + nl;
-                for (int kl = 0; kl < kBK; ++kl) {
-                    const int k = kc * kBK + kl;
+                for (int kl = 0; kl < kpc; ++kl) {
+                    const int k = kc * kpc + kl;
                     const double v = (n < Nv && k < Kv) ? Bm[(size_t)n * Kv + k] : 0.0;
-                    const uint16_t hb = bf16_bits(v);
-                    const uint16_t lb = bf16_bits(v - bf16_value(hb));
-                    const size_t off = (size_t)(nl / 8) * 1024 + (kl / 8) * 128 + (nl % 8) * 16 + (kl % 8) * 2;
-                    std::memcpy(hi + off, &hb, 2);
-                    std::memcpy(lo + off, &lb, 2);
+                    if (tf32) {
+                        const uint32_t hb = tf32_bits(v);
+                        const uint32_t lb = tf32_bits(v - tf32_value(hb));
+                        const size_t off = (size_t)(nl / 8) * 1024 + (kl / 4) * 128 + (nl % 8) * 16 + (kl % 4) * 4;
+                        std::memcpy(hi + off, &hb, 4);
+                        std::memcpy(lo + off, &lb, 4);
+                    } else {
+                        const uint16_t hb = bf16_bits(v);
+                        const uint16_t lb = bf16_bits(v - bf16_value(hb));
+                        const size_t off = (size_t)(nl / 8) * 1024 + (kl / 8) * 128 + (nl % 8) * 16 + (kl % 8) * 2;
+                        std::memcpy(hi + off, &hb, 2);
+                        std::memcpy(lo + off, &lb, 2);
+                    }
                 }
             }
         }
@@ -268,8 +402,9 @@ struct Packed {
 
 struct ColState {
     bool ok = false;
-    // per trajectory: forward / adjoint operands of W (EVF) and W H (full)
-    Packed evf_f[2], evf_a[2], full_f[2], full_a[2];
+    // per operand format (0 bf16, 1 tf32) and trajectory: forward / adjoint operands of
+    // W (line) and W H (full)
+    Packed evf_f[2][2], evf_a[2][2], full_f[2][2], full_a[2][2];
     int *rows[2] = {nullptr, nullptr};  // line indices of each trajectory
     int nrows[2] = {0, 0};
     int *err = nullptr;
@@ -286,9 +421,13 @@ bool upload_packed(Packed &p, const std::vector<uint8_t> &v) {
     return cudaMemcpy(p.dev, v.data(), v.size(), cudaMemcpyHostToDevice) == cudaSuccess;
 }
 
+// Pipeline depth: as many stages (2..4) as leave room for two blocks per SM, so that
+// a grid of up to two blocks per SM runs in one wave.
 size_t smem_for(int BN, int &stages) {
     const size_t stage = 2u * kBM * kBK * 2 + 2u * BN * kBK * 2;
-    stages = (int)std::min<size_t>(4, (220u * 1024u - 256u) / stage);
+    const size_t two_per_sm = (113u * 1024u - 256u) / stage;
+    const size_t cap = (220u * 1024u - 256u) / stage;
+    stages = (int)std::min<size_t>(cap, std::max<size_t>(2, std::min<size_t>(4, two_per_sm)));
     return stages * stage + 256;
 }
 
@@ -310,8 +449,9 @@ void launch(const mpi_ffl_handle *h, const float *A, int64_t lda, int Ka, const 
     g.rscale = rscale;
     g.rdiv = rdiv;
     g.prec = h->precision;
+    g.tf32 = h->precision == MPI_FFL_PREC_TF32 ? 1 : 0;
     const size_t smem = smem_for(B.BN, g.stages);
-    g.tmem_cols = B.BN <= 32 ? 32 : B.BN <= 64 ? 64 : B.BN <= 128 ? 128 : 256;
+    set_accumulators(g);
     g.err = cs(h)->err;
     g.done = nullptr;
     dim3 grid((M + kBM - 1) / kBM, B.ntile);
@@ -327,7 +467,8 @@ int gemm_problems(const mpi_ffl_handle *h, bool adjoint, const float *in, float 
     const Dims &d = h->d;
     int np = 0;
     for (int par = 0; par < s->n_par; ++par) {
-        const Packed &B = adjoint ? s->full_a[par] : s->full_f[par];
+        const int f = h->precision == MPI_FFL_PREC_TF32 ? 1 : 0;
+        const Packed &B = adjoint ? s->full_a[f][par] : s->full_f[f][par];
         GemmArgs &g = args[np];
         g = GemmArgs{};
         g.A = in;
@@ -345,8 +486,9 @@ int gemm_problems(const mpi_ffl_handle *h, bool adjoint, const float *in, float 
         g.rscale = h->t_gain;
         g.rdiv = d.Nz;
         g.prec = h->precision;
+        g.tf32 = f;
         smem_for(B.BN, g.stages);
-        g.tmem_cols = B.BN <= 32 ? 32 : B.BN <= 64 ? 64 : B.BN <= 128 ? 128 : 256;
+        set_accumulators(g);
         g.err = s->err;
         g.done = done;
         for (int mt = 0; mt < (g.M + kBM - 1) / kBM; ++mt)
@@ -441,13 +583,26 @@ void col_init(mpi_ffl_handle *h) {
         }
         for (int o = 0; o < R; ++o)
             for (int i = 0; i < d.N; ++i) WHt[(size_t)i * R + o] = WH[(size_t)o * d.N + i];
-        auto mk = [&](Packed &p, const std::vector<double> &m, int Nv, int Kv, int BN) {
+        auto mk1 = [&](Packed &p, const std::vector<double> &m, int Nv, int Kv, int BN, bool tf) {
             p.BN = BN;
-            return upload_packed(p, pack_b(m, Nv, Kv, BN, p.ntile, p.nkc));
+            return upload_packed(p, pack_b(m, Nv, Kv, BN, p.ntile, p.nkc, tf));
         };
-        const int bnf = R <= 256 ? (R + 15) / 16 * 16 : 144;
-        if (!mk(s->evf_f[par], Wr, R, d.Ne, bnf) || !mk(s->evf_a[par], Wt, d.Ne, R, 256) ||
-            !mk(s->full_f[par], WH, R, d.N, bnf) || !mk(s->full_a[par], WHt, d.N, R, d.N <= 256 ? (d.N + 15) / 16 * 16 : 256))
+        auto mk = [&](Packed (&p)[2][2], const std::vector<double> &m, int Nv, int Kv, int BN) {
+            return mk1(p[0][par], m, Nv, Kv, BN, false) && mk1(p[1][par], m, Nv, Kv, BN, true);
+        };
+        // N tile: about two blocks per SM over both trajectories' M tiles
+        int n_sm = 152, dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+        const int mtiles = std::max(1, d.n_par * ((d.nseg / d.n_par + kBM - 1) / kBM));
+        auto pick_bn = [&](int Nv) {
+            const int want_tiles = std::max(1, (2 * n_sm + mtiles - 1) / mtiles);
+            int bn = (Nv + want_tiles - 1) / want_tiles;
+            bn = std::max(32, std::min(256, (bn + 15) / 16 * 16));
+            return bn;
+        };
+        if (!mk(s->evf_f, Wr, R, d.Ne, pick_bn(R)) || !mk(s->evf_a, Wt, d.Ne, R, pick_bn(d.Ne)) ||
+            !mk(s->full_f, WH, R, d.N, pick_bn(R)) || !mk(s->full_a, WHt, d.N, R, pick_bn(d.N)))
             return;
         // lines of this trajectory
         std::vector<int> rows;
@@ -469,8 +624,9 @@ void col_release(mpi_ffl_handle *h) {
     ColState *s = cs(h);
     if (!s) return;
     for (int p = 0; p < 2; ++p) {
-        for (Packed *pk : {&s->evf_f[p], &s->evf_a[p], &s->full_f[p], &s->full_a[p]})
-            if (pk->dev) cudaFree(pk->dev);
+        for (int f = 0; f < 2; ++f)
+            for (Packed *pk : {&s->evf_f[f][p], &s->evf_a[f][p], &s->full_f[f][p], &s->full_a[f][p]})
+                if (pk->dev) cudaFree(pk->dev);
         if (s->rows[p]) cudaFree(s->rows[p]);
     }
     if (s->err) cudaFree(s->err);
@@ -492,7 +648,8 @@ void col_forward(mpi_ffl_handle *h, const float *in, bool full, const float *gai
     ColState *s = cs(h);
     const Dims &d = h->d;
     for (int par = 0; par < s->n_par; ++par) {
-        const Packed &B = full ? s->full_f[par] : s->evf_f[par];
+        const int f = h->precision == MPI_FFL_PREC_TF32 ? 1 : 0;
+        const Packed &B = full ? s->full_f[f][par] : s->evf_f[f][par];
         launch(h, in, full ? d.N : d.Ne, full ? d.N : d.Ne, s->rows[par], s->nrows[par], B, data, 2 * d.nb,
                s->rows[par], 2 * d.nb, gain, d.Nz, st);
     }
@@ -503,7 +660,8 @@ void col_adjoint(mpi_ffl_handle *h, const float *data, bool full, const float *g
     ColState *s = cs(h);
     const Dims &d = h->d;
     for (int par = 0; par < s->n_par; ++par) {
-        const Packed &B = full ? s->full_a[par] : s->evf_a[par];
+        const int f = h->precision == MPI_FFL_PREC_TF32 ? 1 : 0;
+        const Packed &B = full ? s->full_a[f][par] : s->evf_a[f][par];
         const int nout = full ? d.N : d.Ne;
         launch(h, data, 2 * d.nb, 2 * d.nb, s->rows[par], s->nrows[par], B, out, nout, s->rows[par], nout, gain,
                d.Nz, st);

@@ -189,6 +189,7 @@ struct UpdateJob {     // x_out = P(y - tau (g + lam T^T T y)); a frozen job cop
 
 int transpose_blocks(int N, int Nz);
 int project_blocks(int n_agroups, int Nz);
+bool project_batch_ok(int N);  // problem size the batched projector takes
 int backproject_blocks(int N, int Nz);
 int update_blocks(int N, int Nz);
 void launch_transpose_batch(const TransposeJob *jobs, const int *offs, int n, int total, cudaStream_t st);

@@ -109,23 +109,36 @@ __global__ void __launch_bounds__(1024) k_project(const float *__restrict__ vol,
     }
 }
 
-// Pipelined variant (N % 4 == 0): an extra producer warp streams voxel line s of the
-// block's kZc slices into a ring of kPStages shared-memory stages with bulk copies
-// that complete on full[stage]; every consumer warp signals empty[stage] when it has
-// used a stage, so no block-wide barrier sits in the march loop.
+// Pipelined variant (N % 4 == 0, N <= 512): an extra producer warp streams voxel line
+// s of the block's kZc slices into a ring of kPStages shared-memory stages with bulk
+// copies that complete on full[stage]; every consumer warp signals empty[stage] when
+// it has used a stage, so no block-wide barrier sits in the march loop. Each staged
+// line sits between kPad zeros on the left and at least 4 on the right (row stride
+// LD >= N + 8, a compile-time constant), so a tap index clamped to [-2, N] reads a
+// zero outside the grid: the taps need no range checks, the slice offsets are
+// immediates, and the sums equal those of the checked form (a zero tap adds nothing).
 constexpr int kPStages = 8;
+constexpr int kPad = 4;
 
+template <int LD>
 __device__ __forceinline__ void project_pipe_body(const float *__restrict__ vol, const float *__restrict__ volT,
                                                   const AngleParam *__restrict__ ang,
                                                   const int *__restrict__ agroups, float *__restrict__ proj,
                                                   int N, int Nz, int rays_per_angle, int *err, int bx, int by,
                                                   float *psm) {
-    uint64_t *bars = reinterpret_cast<uint64_t *>(psm + kPStages * kZc * N);  // full[K], empty[K]
+    uint64_t *bars = reinterpret_cast<uint64_t *>(psm + kPStages * kZc * LD);  // full[K], empty[K]
     const int nthreads_c = rays_per_angle * kProjAnglesPerBlock;  // consumers
     const int ncw = nthreads_c / 32;
     const int z0 = by * kZc;
     const int nz = min(kZc, Nz - z0);
     const int tid = threadIdx.x;
+    // zero the pads of every staged line: [0, kPad) and [kPad + N, LD). The stride is
+    // this problem's thread count: in a batch launch, threads past it have left.
+    const int padw = LD - N;
+    for (int t = tid; t < kPStages * kZc * padw; t += nthreads_c + 32) {
+        const int row = t / padw, cpos = t - row * padw;
+        psm[row * LD + (cpos < kPad ? cpos : N + cpos)] = 0.f;
+    }
     if (tid == 0) {
         for (int k = 0; k < kPStages; ++k) {
             ptx::mbar_init(&bars[k], 1);
@@ -139,22 +152,29 @@ __device__ __forceinline__ void project_pipe_body(const float *__restrict__ vol,
     const uint32_t row_bytes = (uint32_t)N * 4u;
     if (tid >= nthreads_c) {
         // ---------------------------------------------------------------- producer warp
-        if (tid == nthreads_c) {
-            for (int s = 0; s < N; ++s) {
-                const int k = s % kPStages;
-                if (s >= kPStages && !ptx::mbar_wait_bounded(&bars[kPStages + k], ((s / kPStages) - 1) & 1, 1u << 24)) {
-                    atomicExch(err, 1);
-                    break;
-                }
-                float *dst = psm + k * kZc * N;
-                ptx::mbar_arrive_expect_tx(&bars[k], row_bytes * nz);
-                for (int zz = 0; zz < nz; ++zz)
-                    ptx::bulk_g2s(dst + zz * N, src + ((size_t)(z0 + zz) * N + s) * N, row_bytes, &bars[k]);
+        // lane 0 announces the stage's bytes, then lane zz copies slice zz: the nz
+        // copies of a step are issued side by side, not one after another
+        const int lane = tid - nthreads_c;
+        for (int s = 0; s < N; ++s) {
+            const int k = s % kPStages;
+            int ok = 1;  // lane 0 waits for the stage to be free; the warp leaves together
+            if (s >= kPStages && lane == 0)
+                ok = ptx::mbar_wait_bounded(&bars[kPStages + k], ((s / kPStages) - 1) & 1, 1u << 24);
+            if (!__shfl_sync(0xffffffffu, ok, 0)) {
+                if (lane == 0) atomicExch(err, 1);
+                break;
             }
+            float *dst = psm + k * kZc * LD + kPad;
+            if (lane == 0) ptx::mbar_arrive_expect_tx(&bars[k], row_bytes * nz);
+            __syncwarp();
+            if (lane < nz)
+                ptx::bulk_g2s(dst + lane * LD, src + ((size_t)(z0 + lane) * N + s) * N, row_bytes, &bars[k]);
         }
         return;
     }
     // -------------------------------------------------------------------- consumers
+    // Threads of an inactive slot or beyond the last ray run the loop on clamped,
+    // in-bounds taps and store nothing; slices past nz hold stale data, never stored.
     const int slot = tid / rays_per_angle;
     const int i = tid % rays_per_angle;
     const int m = agroups[bx * kProjAnglesPerBlock + slot];
@@ -172,20 +192,13 @@ __device__ __forceinline__ void project_pipe_body(const float *__restrict__ vol,
             good = false;
             break;
         }
-        const float *cur = psm + k * kZc * N;
-        if (active) {
-            const float f = fmaf(ap.slope, (float)s - c, fi);
-            const float fl = floorf(f);
-            const int kk = (int)fl;
-            const float t = f - fl;
-            const float w0 = (kk >= 0 && kk < N) ? 1.f - t : 0.f;
-            const float w1 = (kk + 1 >= 0 && kk + 1 < N) ? t : 0.f;
-            const int k0 = min(max(kk, 0), N - 1);
-            const int k1 = min(max(kk + 1, 0), N - 1);
+        const float f = fmaf(ap.slope, (float)s - c, fi);
+        const float fl = floorf(f);
+        const float t = f - fl;
+        const int kk = min(max((int)fl, -2), N);
+        const float *p = psm + k * kZc * LD + kPad + kk;
 #pragma unroll
-            for (int zz = 0; zz < kZc; ++zz)
-                if (zz < nz) acc[zz] = fmaf(w0, cur[zz * N + k0], fmaf(w1, cur[zz * N + k1], acc[zz]));
-        }
+        for (int zz = 0; zz < kZc; ++zz) acc[zz] = fmaf(1.f - t, p[zz * LD], fmaf(t, p[zz * LD + 1], acc[zz]));
         __syncwarp();
         if ((tid & 31) == 0) ptx::mbar_arrive(&bars[kPStages + k]);
     }
@@ -200,26 +213,53 @@ __device__ __forceinline__ void project_pipe_body(const float *__restrict__ vol,
     }
 }
 
+template <int LD>
 __global__ void __launch_bounds__(1024 + 32) k_project_pipe(const float *__restrict__ vol,
                                                             const float *__restrict__ volT,
                                                             const AngleParam *__restrict__ ang,
                                                             const int *__restrict__ agroups,
                                                             float *__restrict__ proj, int N, int Nz,
                                                             int rays_per_angle, int *err) {
-    extern __shared__ __align__(128) float psm[];  // kPStages x kZc x N
-    project_pipe_body(vol, volT, ang, agroups, proj, N, Nz, rays_per_angle, err, blockIdx.x, blockIdx.y, psm);
+    extern __shared__ __align__(128) float psm[];  // kPStages x kZc x LD
+    project_pipe_body<LD>(vol, volT, ang, agroups, proj, N, Nz, rays_per_angle, err, blockIdx.x, blockIdx.y, psm);
+}
+
+// Smallest compiled row stride that holds N + 8 floats; 0 if N is above 512.
+int pipe_ld(int N) {
+    for (int ld : {40, 72, 136, 200, 264, 392, 520})
+        if (N + 8 <= ld) return ld;
+    return 0;
+}
+
+size_t pipe_smem(int ld) { return sizeof(float) * kPStages * kZc * ld + 16 * kPStages; }
+
+bool pipe_ok(const float *vol, const float *volT, int N) {
+    return N % 4 == 0 && pipe_ld(N) > 0 && (reinterpret_cast<uintptr_t>(vol) & 15) == 0 &&
+           (reinterpret_cast<uintptr_t>(volT) & 15) == 0;
+}
+
+template <int LD>
+void launch_pipe(dim3 grid, int threads, cudaStream_t st, const float *vol, const float *volT, const AngleParam *ang,
+                 const int *agroups, float *proj, int N, int Nz, int rays, int *err) {
+    cudaFuncSetAttribute(k_project_pipe<LD>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    k_project_pipe<LD><<<grid, threads, pipe_smem(LD), st>>>(vol, volT, ang, agroups, proj, N, Nz, rays, err);
 }
 
 void launch_project(const float *vol, const float *volT, const AngleParam *ang, const int *agroups,
                     int n_agroups, float *proj, int N, int Nz, cudaStream_t st, int *err) {
     const int rays = (N + 31) / 32 * 32;
-    if (N % 4 == 0 && err) {
-        const size_t smem = sizeof(float) * kPStages * kZc * N + 16 * kPStages;
-        if (smem > 48 * 1024)
-            cudaFuncSetAttribute(k_project_pipe, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    if (err && pipe_ok(vol, volT, N)) {
         dim3 grid(n_agroups, (Nz + kZc - 1) / kZc);
-        k_project_pipe<<<grid, rays * kProjAnglesPerBlock + 32, smem, st>>>(vol, volT, ang, agroups, proj, N, Nz,
-                                                                            rays, err);
+        const int threads = rays * kProjAnglesPerBlock + 32;
+        switch (pipe_ld(N)) {
+        case 40: launch_pipe<40>(grid, threads, st, vol, volT, ang, agroups, proj, N, Nz, rays, err); break;
+        case 72: launch_pipe<72>(grid, threads, st, vol, volT, ang, agroups, proj, N, Nz, rays, err); break;
+        case 136: launch_pipe<136>(grid, threads, st, vol, volT, ang, agroups, proj, N, Nz, rays, err); break;
+        case 200: launch_pipe<200>(grid, threads, st, vol, volT, ang, agroups, proj, N, Nz, rays, err); break;
+        case 264: launch_pipe<264>(grid, threads, st, vol, volT, ang, agroups, proj, N, Nz, rays, err); break;
+        case 392: launch_pipe<392>(grid, threads, st, vol, volT, ang, agroups, proj, N, Nz, rays, err); break;
+        default: launch_pipe<520>(grid, threads, st, vol, volT, ang, agroups, proj, N, Nz, rays, err); break;
+        }
         return;
     }
     const int threads = rays * kProjAnglesPerBlock;
@@ -230,63 +270,110 @@ void launch_project(const float *vol, const float *volT, const AngleParam *ang, 
     k_project<<<grid, threads, smem, st>>>(vol, volT, ang, agroups, proj, N, Nz, rays);
 }
 
-// Transpose: a thread owns one voxel column (x, y) and kZc slices. For every angle
-// the rays whose interpolation touches the voxel are among i1-1, i1, i1+1 (i1 the
-// nearest ray); ray i's sample position f_i is recomputed with the forward's exact
-// arithmetic and its weight max(0, 1 - |f_i - q|) equals the forward's (1-t or t)
-// bit for bit. The kZc projection values of each ray are gathered. No atomics.
-__device__ __forceinline__ void backproject_body(const float *__restrict__ proj, const AngleParam *__restrict__ ang,
-                                                 float *__restrict__ vol, int N, int Nz, int M, int bx, int by,
-                                                 int bz) {
-    const int x = bx * 32 + threadIdx.x;
-    const int y = by * 8 + threadIdx.y;
-    const int z0 = bz * kZc;
-    const int nz = min(kZc, Nz - z0);
-    if (x >= N || y >= N) return;
-    const float c = 0.5f * (float)(N - 1);
-    float acc[kZc];
-#pragma unroll
-    for (int zz = 0; zz < kZc; ++zz) acc[zz] = 0.f;
-    for (int m = 0; m < M; ++m) {
-        const AngleParam a = ang[m];
-        const int s = a.row_major ? y : x;             // march step holding this voxel
-        const float q = (float)(a.row_major ? x : y);  // its index along the step's line
-        const float sm = (float)s - c;
-        // nearest ray: inv_c (i - c) + slope (s - c) + c = q
-        const int i1 = __float2int_rn(fmaf(q - fmaf(a.slope, sm, c), a.inv_c_rcp, c));
-        float w[3];
-        int ii[3];
-#pragma unroll
-        for (int u = 0; u < 3; ++u) {
-            const int i = i1 - 1 + u;
-            const float f = fmaf(a.slope, sm, fmaf(a.inv_c, (float)i - c, c));  // the forward's f
-            const bool in = (i >= 0) && (i < N);
-            w[u] = in ? fmaxf(0.f, 1.f - fabsf(f - q)) * a.scale : 0.f;
-            ii[u] = in ? i : 0;
-        }
-        // at most two consecutive rays carry weight: (i1-1, i1) or (i1, i1+1)
-        const bool lo = w[0] != 0.f;
-        const float wA = lo ? w[0] : w[1], wB = lo ? w[1] : w[2];
-        const int iA = lo ? ii[0] : ii[1], iB = lo ? ii[1] : ii[2];
-        const float *pm = proj + ((size_t)m * Nz + z0) * N;
-#pragma unroll
-        for (int zz = 0; zz < kZc; ++zz)
-            if (zz < nz) acc[zz] = fmaf(wA, __ldg(pm + zz * N + iA), fmaf(wB, __ldg(pm + zz * N + iB), acc[zz]));
-    }
-#pragma unroll
-    for (int zz = 0; zz < kZc; ++zz)
-        if (zz < nz) vol[((size_t)(z0 + zz) * N + y) * N + x] = acc[zz];
+// Transpose: a block owns a tile of kBpTX x kBpTY voxel columns and kBpZ slices; a
+// thread owns one column (x, y) and its kBpZ slices. For every angle the rays whose
+// interpolation touches the voxel are among i1-1, i1, i1+1 (i1 the nearest ray); ray
+// i's sample position f_i is recomputed with the forward's exact arithmetic and its
+// weight max(0, 1 - |f_i - q|) equals the forward's (1-t or t), so at most two
+// consecutive rays carry weight. No atomics. The rays a tile can touch for one angle
+// form a window of at most kBpSeg consecutive rays that starts one before the
+// smallest nearest ray of the tile's corners (the nearest-ray map is monotone in
+// both coordinates, so the corners bound it). Angles are taken kBpChunk at a time:
+// the chunk's windows of proj x scale (zero outside the detector) are staged in
+// shared memory, then every thread gathers its two rays per slice from there.
+constexpr int kBpTX = 32, kBpTY = 16, kBpZ = 16, kBpSeg = 40, kBpChunk = 12;
+
+struct BpShared {
+    float seg[kBpChunk][kBpZ][kBpSeg];
+    AngleParam ang[kBpChunk];
+    int ilo[kBpChunk];
+};
+
+__device__ __forceinline__ int nearest_ray(const AngleParam &a, int s, int q, float c) {
+    const float sm = (float)s - c;
+    return __float2int_rn(fmaf((float)q - fmaf(a.slope, sm, c), a.inv_c_rcp, c));
 }
 
-__global__ void __launch_bounds__(256) k_backproject(const float *__restrict__ proj,
-                                                     const AngleParam *__restrict__ ang,
-                                                     float *__restrict__ vol, int N, int Nz, int M) {
-    backproject_body(proj, ang, vol, N, Nz, M, blockIdx.x, blockIdx.y, blockIdx.z);
+__device__ __forceinline__ void backproject_body(const float *__restrict__ proj, const AngleParam *__restrict__ ang,
+                                                 float *__restrict__ vol, int N, int Nz, int M, int bx, int by,
+                                                 int bz, BpShared &S) {
+    const int tid = threadIdx.y * kBpTX + threadIdx.x;
+    const int nthr = kBpTX * kBpTY;
+    const int x = bx * kBpTX + threadIdx.x;
+    const int y = by * kBpTY + threadIdx.y;
+    const int z0 = bz * kBpZ;
+    const int nz = min(kBpZ, Nz - z0);
+    const float c = 0.5f * (float)(N - 1);
+    const int xlo = bx * kBpTX, xhi = min(xlo + kBpTX, N) - 1;
+    const int ylo = by * kBpTY, yhi = min(ylo + kBpTY, N) - 1;
+    // threads past the grid edge follow the loop on the edge voxel and store nothing
+    const float fx = (float)min(x, N - 1), fy = (float)min(y, N - 1);
+    float acc[kBpZ];
+#pragma unroll
+    for (int zz = 0; zz < kBpZ; ++zz) acc[zz] = 0.f;
+    for (int m0 = 0; m0 < M; m0 += kBpChunk) {
+        const int na = min(kBpChunk, M - m0);
+        __syncthreads();  // the previous chunk has been used
+        if (tid < na) {
+            const AngleParam a = ang[m0 + tid];
+            S.ang[tid] = a;
+            const int s0 = a.row_major ? ylo : xlo, s1 = a.row_major ? yhi : xhi;
+            const int q0 = a.row_major ? xlo : ylo, q1 = a.row_major ? xhi : yhi;
+            const int lo = min(min(nearest_ray(a, s0, q0, c), nearest_ray(a, s0, q1, c)),
+                               min(nearest_ray(a, s1, q0, c), nearest_ray(a, s1, q1, c)));
+            S.ilo[tid] = lo - 1;
+        }
+        __syncthreads();
+        for (int t = tid; t < na * kBpZ * kBpSeg; t += nthr) {
+            const int a = t / (kBpZ * kBpSeg);
+            const int r = t - a * (kBpZ * kBpSeg);
+            const int zz = r / kBpSeg, j = r - zz * kBpSeg;
+            const int i = S.ilo[a] + j, z = z0 + zz;
+            float v = 0.f;
+            if (i >= 0 && i < N && z < Nz) v = __ldg(proj + ((size_t)(m0 + a) * Nz + z) * N + i) * S.ang[a].scale;
+            S.seg[a][zz][j] = v;
+        }
+        __syncthreads();
+        for (int a = 0; a < na; ++a) {
+            const AngleParam A = S.ang[a];
+            const float sm = (A.row_major ? fy : fx) - c;  // march step holding this voxel, centred
+            const float q = A.row_major ? fx : fy;          // its index along the step's line
+            // nearest ray: inv_c (i - c) + slope (s - c) + c = q
+            const int i1 = __float2int_rn(fmaf(q - fmaf(A.slope, sm, c), A.inv_c_rcp, c));
+            const float d1 = (float)i1 - c;  // exact, as are d1 - 1 and d1 + 1
+            const float f0 = fmaf(A.slope, sm, fmaf(A.inv_c, d1 - 1.f, c));  // the forward's f
+            const float f1 = fmaf(A.slope, sm, fmaf(A.inv_c, d1, c));
+            const float f2 = fmaf(A.slope, sm, fmaf(A.inv_c, d1 + 1.f, c));
+            const float w0 = fmaxf(0.f, 1.f - fabsf(f0 - q));
+            const float w1 = fmaxf(0.f, 1.f - fabsf(f1 - q));
+            const float w2 = fmaxf(0.f, 1.f - fabsf(f2 - q));
+            // two consecutive rays carry the weight: (i1-1, i1) or (i1, i1+1)
+            const bool lo = w0 != 0.f;
+            const float wA = lo ? w0 : w1, wB = lo ? w1 : w2;
+            const int j = min(max(i1 - (lo ? 1 : 0) - S.ilo[a], 0), kBpSeg - 2);
+            const float *p = &S.seg[a][0][j];
+#pragma unroll
+            for (int zz = 0; zz < kBpZ; ++zz)
+                acc[zz] = fmaf(wA, p[zz * kBpSeg], fmaf(wB, p[zz * kBpSeg + 1], acc[zz]));
+        }
+    }
+    if (x < N && y < N) {
+#pragma unroll
+        for (int zz = 0; zz < kBpZ; ++zz)
+            if (zz < nz) vol[((size_t)(z0 + zz) * N + y) * N + x] = acc[zz];
+    }
+}
+
+__global__ void __launch_bounds__(kBpTX * kBpTY) k_backproject(const float *__restrict__ proj,
+                                                              const AngleParam *__restrict__ ang,
+                                                              float *__restrict__ vol, int N, int Nz, int M) {
+    __shared__ BpShared S;
+    backproject_body(proj, ang, vol, N, Nz, M, blockIdx.x, blockIdx.y, blockIdx.z, S);
 }
 
 void launch_backproject(const float *proj, const AngleParam *ang, float *vol, int N, int Nz,
                         int M, cudaStream_t st) {
-    dim3 grid((N + 31) / 32, (N + 7) / 8, (Nz + kZc - 1) / kZc), block(32, 8);
+    dim3 grid((N + kBpTX - 1) / kBpTX, (N + kBpTY - 1) / kBpTY, (Nz + kBpZ - 1) / kBpZ), block(kBpTX, kBpTY);
     k_backproject<<<grid, block, 0, st>>>(proj, ang, vol, N, Nz, M);
 }
 
@@ -313,6 +400,7 @@ __global__ void k_transpose_batch(const TransposeJob *__restrict__ jobs, const i
     transpose_body(J.vol, J.volT, J.N, bx, by, bz);
 }
 
+template <int LD>
 __global__ void __launch_bounds__(1024 + 32) k_project_batch(const ProjectJob *__restrict__ jobs,
                                                              const int *__restrict__ offs, int n, int *err) {
     extern __shared__ __align__(128) float psm[];
@@ -326,38 +414,58 @@ __global__ void __launch_bounds__(1024 + 32) k_project_batch(const ProjectJob *_
         __syncthreads();
         return;
     }
-    project_pipe_body(J.vol, J.volT, J.ang, J.agroups, J.proj, J.N, J.Nz, rays, err, b % J.n_agroups,
-                      b / J.n_agroups, psm);
+    project_pipe_body<LD>(J.vol, J.volT, J.ang, J.agroups, J.proj, J.N, J.Nz, rays, err, b % J.n_agroups,
+                          b / J.n_agroups, psm);
 }
 
-__global__ void __launch_bounds__(256) k_backproject_batch(const BackprojectJob *__restrict__ jobs,
-                                                           const int *__restrict__ offs, int n) {
+__global__ void __launch_bounds__(kBpTX * kBpTY) k_backproject_batch(const BackprojectJob *__restrict__ jobs,
+                                                                    const int *__restrict__ offs, int n) {
+    __shared__ BpShared S;
     const int j = batch_find(offs, n, blockIdx.x);
     const BackprojectJob J = jobs[j];
     if (J.done && *J.done) return;
     const int b = blockIdx.x - offs[j];
-    const int gx = (J.N + 31) / 32, gy = (J.N + 7) / 8;
-    backproject_body(J.proj, J.ang, J.vol, J.N, J.Nz, J.M, b % gx, (b / gx) % gy, b / (gx * gy));
+    const int gx = (J.N + kBpTX - 1) / kBpTX, gy = (J.N + kBpTY - 1) / kBpTY;
+    backproject_body(J.proj, J.ang, J.vol, J.N, J.Nz, J.M, b % gx, (b / gx) % gy, b / (gx * gy), S);
 }
 
 int transpose_blocks(int N, int Nz) { return ((N + 31) / 32) * ((N + 31) / 32) * Nz; }
 int project_blocks(int n_agroups, int Nz) { return n_agroups * ((Nz + kZc - 1) / kZc); }
-int backproject_blocks(int N, int Nz) { return ((N + 31) / 32) * ((N + 7) / 8) * ((Nz + kZc - 1) / kZc); }
+int backproject_blocks(int N, int Nz) {
+    return ((N + kBpTX - 1) / kBpTX) * ((N + kBpTY - 1) / kBpTY) * ((Nz + kBpZ - 1) / kBpZ);
+}
 
 void launch_transpose_batch(const TransposeJob *jobs, const int *offs, int n, int total, cudaStream_t st) {
     k_transpose_batch<<<total, dim3(32, 8), 0, st>>>(jobs, offs, n);
 }
 
+bool project_batch_ok(int N) { return N % 4 == 0 && pipe_ld(N) > 0; }
+
+template <int LD>
+void launch_pbatch(const ProjectJob *jobs, const int *offs, int n, int total, int threads, int *err,
+                   cudaStream_t st) {
+    cudaFuncSetAttribute(k_project_batch<LD>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    k_project_batch<LD><<<total, threads, pipe_smem(LD), st>>>(jobs, offs, n, err);
+}
+
+// Every problem in the batch has N % 4 == 0 and N <= 512 (project_batch_ok); the ring
+// stride is the one of the largest N.
 void launch_project_batch(const ProjectJob *jobs, const int *offs, int n, int total, int maxN, int *err,
                           cudaStream_t st) {
-    const int rays = (maxN + 31) / 32 * 32;
-    const size_t smem = sizeof(float) * kPStages * kZc * maxN + 16 * kPStages;
-    cudaFuncSetAttribute(k_project_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    k_project_batch<<<total, rays * kProjAnglesPerBlock + 32, smem, st>>>(jobs, offs, n, err);
+    const int threads = (maxN + 31) / 32 * 32 * kProjAnglesPerBlock + 32;
+    switch (pipe_ld(maxN)) {
+    case 40: launch_pbatch<40>(jobs, offs, n, total, threads, err, st); break;
+    case 72: launch_pbatch<72>(jobs, offs, n, total, threads, err, st); break;
+    case 136: launch_pbatch<136>(jobs, offs, n, total, threads, err, st); break;
+    case 200: launch_pbatch<200>(jobs, offs, n, total, threads, err, st); break;
+    case 264: launch_pbatch<264>(jobs, offs, n, total, threads, err, st); break;
+    case 392: launch_pbatch<392>(jobs, offs, n, total, threads, err, st); break;
+    default: launch_pbatch<520>(jobs, offs, n, total, threads, err, st); break;
+    }
 }
 
 void launch_backproject_batch(const BackprojectJob *jobs, const int *offs, int n, int total, cudaStream_t st) {
-    k_backproject_batch<<<total, dim3(32, 8), 0, st>>>(jobs, offs, n);
+    k_backproject_batch<<<total, dim3(kBpTX, kBpTY), 0, st>>>(jobs, offs, n);
 }
 
 }  // namespace mpiffl

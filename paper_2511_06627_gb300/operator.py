@@ -237,6 +237,10 @@ class FFLOperator:
     def set_precision(self, precision):
         check(self._lib.mpi_ffl_set_precision(self._h, int(precision)), self._h)
 
+    @property
+    def precision(self):
+        return int(self._lib.mpi_ffl_get_precision(self._h))
+
     def set_path(self, path):
         """Evaluation path: PATH_* constant or one of 'staged', 'fused', 'line_gemm', 'full_gemm'."""
         if isinstance(path, str):

@@ -23,29 +23,12 @@ from ._lib import check
 from .operator import FFLOperator
 
 
-class JobStatus(C.Structure):
-    _fields_ = [("iters_done", C.c_int32), ("stopped", C.c_int32), ("finished", C.c_int32),
-                ("residual_first", C.c_double), ("residual_last", C.c_double), ("tau", C.c_double),
-                ("lambda_", C.c_double), ("device_bytes", C.c_int64)]
+JobStatus = _lib.JobStatus
 
 
 def _declare(lib):
-    if getattr(lib, "_jobs_declared", False):
-        return
-    P = C.c_void_p
-    for name, res, args in (
-        ("mpi_ffl_job_create", C.c_int, [P, P, P, C.POINTER(_lib.SolveParams), C.POINTER(P), P]),
-        ("mpi_ffl_job_step", C.c_int, [C.POINTER(P), C.c_int32, P]),
-        ("mpi_ffl_job_status", C.c_int, [P, C.POINTER(JobStatus), P]),
-        ("mpi_ffl_job_flags", C.c_int, [P, C.POINTER(P)]),
-        ("mpi_ffl_job_poll", C.c_int, [C.POINTER(P), C.c_int32, P, P]),
-        ("mpi_ffl_job_result", C.c_int, [P, P, P]),
-        ("mpi_ffl_job_destroy", C.c_int, [P]),
-    ):
-        fn = getattr(lib, name)
-        fn.restype = res
-        fn.argtypes = args
-    lib._jobs_declared = True
+    """The job prototypes are declared by _lib.load(); kept for callers that import it."""
+    return lib
 
 
 @dataclasses.dataclass

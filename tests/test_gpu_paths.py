@@ -83,3 +83,43 @@ def test_gemm_paths_take_every_shape():
         op.set_path("line_gemm")
         op.set_path("full_gemm")
         assert op.path == 3
+
+
+@pytest.mark.parametrize("path", ["line_gemm", "full_gemm"])
+@pytest.mark.parametrize("name", ["s128", "wide_band"])
+def test_tf32_split_is_closer_to_the_oracle_than_bf16_split(name, path):
+    """The tf32 hi + lo operands keep 22 mantissa bits against the bf16 split's 16,
+    so the GEMM term of the error shrinks; both stay inside the operator tolerance."""
+    from paper_2511_06627_gb300 import PREC_BF16X3, PREC_TF32
+
+    st, op = _make(name)
+    op.set_path(path)
+    x = random_volume(st.nz, st.nx, seed=43).astype(np.float32)
+    rng = np.random.default_rng(44)
+    y = (rng.standard_normal(st.data_shape) + 1j * rng.standard_normal(st.data_shape)).astype(np.complex64)
+    ref_f = to_interleaved(operator.forward(x, st))
+    ref_a = operator.adjoint(y, st)
+    err = {}
+    for prec in (PREC_BF16X3, PREC_TF32):
+        op.set_precision(prec)
+        assert op.path == PATHS.index(path)
+        b = op.forward(_t(x))
+        xa = op.adjoint(_t(to_interleaved(y)))
+        op.sync_check()
+        err[prec] = (rel_l2(b.cpu().numpy(), ref_f), rel_l2(xa.cpu().numpy(), ref_a))
+    for i in range(2):
+        assert err[PREC_TF32][i] < OP_TOL
+        assert err[PREC_TF32][i] <= err[PREC_BF16X3][i] * 1.01
+    # switching between the GEMM paths keeps tf32
+    op.set_path("line_gemm" if path == "full_gemm" else "full_gemm")
+    assert op.precision == PREC_TF32
+
+
+def test_tf32_is_refused_off_the_gemm_paths():
+    from paper_2511_06627_gb300 import PREC_TF32, MpiFflError
+
+    st, op = _make("tiny")
+    for path in ("staged", "fused"):
+        op.set_path(path)
+        with pytest.raises(MpiFflError):
+            op.set_precision(PREC_TF32)
