@@ -104,6 +104,15 @@ __device__ __forceinline__ void split8(const float (&v)[8], uint4 &hi, uint4 &lo
     lo = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
+constexpr int kProdWarps = 8;                     // A producers (and epilogue)
+constexpr int kGemmThreads = (kProdWarps + 2) * 32;  // + MMA issuer + B loader
+
+// One K chunk of the A tile for one producer thread: 4 units of (row, core-matrix
+// row kg), 8 bf16 or 4 tf32 values each, as float4s (bf16: 2 per unit).
+struct AChunk {
+    float4 v[8];
+};
+
 __device__ __forceinline__ void gemm_body(const GemmArgs &g, int mt, int nt, uint8_t *sm) {
     const uint32_t bytesA = kBM * kBK * 2;          // one of hi | lo
     const uint32_t bytesB = (uint32_t)g.BN * kBK * 2;
@@ -115,7 +124,7 @@ __device__ __forceinline__ void gemm_body(const GemmArgs &g, int mt, int nt, uin
 
     if (tid == 0) {
         for (int s = 0; s < g.stages; ++s) {
-            ptx::mbar_init(&bars[s], 4 + 1);       // 4 producer warps + the B copy
+            ptx::mbar_init(&bars[s], kProdWarps + 1);  // producer warps + the B copy
             ptx::mbar_init(&bars[g.stages + s], 1);
         }
         ptx::mbar_init(&bars[2 * g.stages], 1);
@@ -131,96 +140,95 @@ __device__ __forceinline__ void gemm_body(const GemmArgs &g, int mt, int nt, uin
     ptx::tc_fence_after();
     const uint32_t tmem = *tslot;
 
-    if (warp < 4) {
+    if (warp < kProdWarps) {
         // ------------------------------------------------------------ A producers
-        // Warp w fills rows 32w..32w+31 of the tile. In one pass a lane takes row
-        // 32w + 8rg + (lane & 7) and 16-byte core-matrix row kg = 4kh + (lane >> 3)
-        // (8 bf16 or 4 tf32 values): 8 rows x 4 consecutive core-matrix rows per
-        // warp store, i.e. 512 contiguous shared-memory bytes, conflict-free; the
-        // global reads are 8 row segments of 128 (bf16) or 64 (tf32) bytes.
+        // Warp w fills row groups 2w and 2w+1 (rows 16w..16w+15). In one pass a lane
+        // takes row 8rg + (lane & 7) and 16-byte core-matrix row kg = 4kh + (lane >> 3)
+        // (8 bf16 or 4 tf32 values): 8 rows x 4 consecutive core-matrix rows per warp
+        // store, 512 contiguous shared-memory bytes, conflict-free; the global reads
+        // are 8 row segments of 128 (bf16) or 64 (tf32) bytes. The loads of chunk
+        // kc + 1 are issued before chunk kc is split and stored.
         const int r7 = lane & 7, kq = lane >> 3;
-        const float *rp[4];
+        const float *rp[2];
 #pragma unroll
-        for (int rg = 0; rg < 4; ++rg) {
-            const int gmr = mt * kBM + 32 * warp + 8 * rg + r7;
+        for (int q = 0; q < 2; ++q) {
+            const int gmr = mt * kBM + 8 * (2 * warp + q) + r7;
             const int arr = gmr < g.M ? __ldg(g.arow + gmr) : -1;
-            rp[rg] = arr >= 0 ? g.A + (size_t)arr * g.lda : nullptr;
+            rp[q] = arr >= 0 ? g.A + (size_t)arr * g.lda : nullptr;
         }
         const bool vec = (g.lda % 4 == 0) && ((reinterpret_cast<uintptr_t>(g.A) & 15) == 0);
-        bool ok = true;
-        for (int kc = 0; kc < g.nkc; ++kc) {
-            const int s = kc % g.stages;
-            if (kc >= g.stages && !ptx::mbar_wait_bounded(&bars[g.stages + s], ((kc / g.stages) - 1) & 1, kWait)) {
-                ok = false;
-                break;
-            }
-            uint8_t *sa = sm + s * stage;
-            if (g.tf32) {
-                float4 v[8];
+        auto load = [&](int kc, AChunk &c) {
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int rg = u >> 1, kg = 4 * (u & 1) + kq;
+            for (int u = 0; u < 4; ++u) {
+                const int q = u >> 1, kg = 4 * (u & 1) + kq;
+                const float *p = rp[q];
+                if (g.tf32) {
                     const int k = kc * (kBK / 2) + kg * 4;
-                    const float *p = rp[rg];
                     if (p && vec && k + 4 <= g.Ka) {
-                        v[u] = __ldg(reinterpret_cast<const float4 *>(p + k));
+                        c.v[u] = __ldg(reinterpret_cast<const float4 *>(p + k));
                     } else {
-                        v[u].x = (p && k + 0 < g.Ka) ? __ldg(p + k + 0) : 0.f;
-                        v[u].y = (p && k + 1 < g.Ka) ? __ldg(p + k + 1) : 0.f;
-                        v[u].z = (p && k + 2 < g.Ka) ? __ldg(p + k + 2) : 0.f;
-                        v[u].w = (p && k + 3 < g.Ka) ? __ldg(p + k + 3) : 0.f;
+                        c.v[u].x = (p && k + 0 < g.Ka) ? __ldg(p + k + 0) : 0.f;
+                        c.v[u].y = (p && k + 1 < g.Ka) ? __ldg(p + k + 1) : 0.f;
+                        c.v[u].z = (p && k + 2 < g.Ka) ? __ldg(p + k + 2) : 0.f;
+                        c.v[u].w = (p && k + 3 < g.Ka) ? __ldg(p + k + 3) : 0.f;
+                    }
+                } else {
+                    const int k = kc * kBK + kg * 8;
+                    if (p && vec && k + 8 <= g.Ka) {
+                        c.v[2 * u] = __ldg(reinterpret_cast<const float4 *>(p + k));
+                        c.v[2 * u + 1] = __ldg(reinterpret_cast<const float4 *>(p + k + 4));
+                    } else {
+                        float t[8];
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) t[e] = (p && k + e < g.Ka) ? __ldg(p + k + e) : 0.f;
+                        c.v[2 * u] = make_float4(t[0], t[1], t[2], t[3]);
+                        c.v[2 * u + 1] = make_float4(t[4], t[5], t[6], t[7]);
                     }
                 }
+            }
+        };
+        // split and store chunk kc into its stage; false if the stage never came free
+        auto produce = [&](int kc, const AChunk &c) -> bool {
+            const int s = kc % g.stages;
+            if (kc >= g.stages && !ptx::mbar_wait_bounded(&bars[g.stages + s], ((kc / g.stages) - 1) & 1, kWait))
+                return false;
+            uint8_t *sa = sm + s * stage;
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int rg = u >> 1, kg = 4 * (u & 1) + kq;
-                    const float f[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
-                    uint4 hi, lo;
+            for (int u = 0; u < 4; ++u) {
+                const int q = u >> 1, kg = 4 * (u & 1) + kq;
+                uint4 hi, lo;
+                if (g.tf32) {
+                    const float f[4] = {c.v[u].x, c.v[u].y, c.v[u].z, c.v[u].w};
                     split4_tf32(f, hi, lo);
-                    const uint32_t off = (4 * warp + rg) * 1024u + kg * 128u + r7 * 16u;
-                    *reinterpret_cast<uint4 *>(sa + off) = hi;
-                    *reinterpret_cast<uint4 *>(sa + bytesA + off) = lo;
+                } else {
+                    const float f[8] = {c.v[2 * u].x,     c.v[2 * u].y,     c.v[2 * u].z,     c.v[2 * u].w,
+                                        c.v[2 * u + 1].x, c.v[2 * u + 1].y, c.v[2 * u + 1].z, c.v[2 * u + 1].w};
+                    split8(f, hi, lo);
                 }
-            } else {
-#pragma unroll 2
-                for (int h = 0; h < 2; ++h) {
-                    float4 v[8];
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const int rg = 2 * h + (u >> 1), kg = 4 * (u & 1) + kq;
-                        const int k = kc * kBK + kg * 8;
-                        const float *p = rp[rg];
-                        if (p && vec && k + 8 <= g.Ka) {
-                            v[2 * u] = __ldg(reinterpret_cast<const float4 *>(p + k));
-                            v[2 * u + 1] = __ldg(reinterpret_cast<const float4 *>(p + k + 4));
-                        } else {
-                            float t[8];
-#pragma unroll
-                            for (int e = 0; e < 8; ++e) t[e] = (p && k + e < g.Ka) ? __ldg(p + k + e) : 0.f;
-                            v[2 * u] = make_float4(t[0], t[1], t[2], t[3]);
-                            v[2 * u + 1] = make_float4(t[4], t[5], t[6], t[7]);
-                        }
-                    }
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const int rg = 2 * h + (u >> 1), kg = 4 * (u & 1) + kq;
-                        const float f[8] = {v[2 * u].x,     v[2 * u].y,     v[2 * u].z,     v[2 * u].w,
-                                            v[2 * u + 1].x, v[2 * u + 1].y, v[2 * u + 1].z, v[2 * u + 1].w};
-                        uint4 hi, lo;
-                        split8(f, hi, lo);
-                        const uint32_t off = (4 * warp + rg) * 1024u + kg * 128u + r7 * 16u;
-                        *reinterpret_cast<uint4 *>(sa + off) = hi;
-                        *reinterpret_cast<uint4 *>(sa + bytesA + off) = lo;
-                    }
-                }
+                const uint32_t off = (2 * warp + q) * 1024u + kg * 128u + r7 * 16u;
+                *reinterpret_cast<uint4 *>(sa + off) = hi;
+                *reinterpret_cast<uint4 *>(sa + bytesA + off) = lo;
             }
             ptx::fence_proxy_async_smem();
             __syncwarp();
             if (lane == 0) ptx::mbar_arrive(&bars[s]);
+            return true;
+        };
+        bool ok = true;
+        AChunk ca, cb;
+        load(0, ca);
+        for (int kc = 0; kc < g.nkc && ok; kc += 2) {
+            if (kc + 1 < g.nkc) load(kc + 1, cb);
+            ok = produce(kc, ca);
+            if (!ok || kc + 1 >= g.nkc) break;
+            if (kc + 2 < g.nkc) load(kc + 2, ca);
+            ok = produce(kc + 1, cb);
         }
         // ------------------------------------------------------------ epilogue
-        // TMEM lane = tile row = tid (tcgen05.ld 32x32b: warp w reads lanes 32w..32w+31)
-        const int gm = mt * kBM + tid;
+        // TMEM lane quadrant w % 4 = tile rows 32 (w % 4) .. +31; warps w and w + 4
+        // take alternate 16-column groups.
+        const int row = 32 * (warp & 3) + lane;
+        const int gm = mt * kBM + row;
         const int ar = gm < g.M ? __ldg(g.arow + gm) : -1;
         if (ok && ptx::mbar_wait_bounded(&bars[2 * g.stages], 0, kWait)) {
             ptx::tc_fence_after();
@@ -229,12 +237,13 @@ __device__ __forceinline__ void gemm_body(const GemmArgs &g, int mt, int nt, uin
             float *crow = cr >= 0 ? g.C + (size_t)cr * g.ldc : nullptr;
             const bool vecc = (g.ldc % 4 == 0) && ((reinterpret_cast<uintptr_t>(g.C) & 15) == 0);
             const int nacc = min(g.nacc, g.nkc);
-            for (int c0 = 0; c0 < g.BN; c0 += 16) {
+            const uint32_t tl = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
+            for (int c0 = 16 * (warp >> 2); c0 < g.BN; c0 += 32) {
                 float v[16];
-                ptx::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + c0, v);
+                ptx::tmem_ld16(tl + c0, v);
                 for (int a = 1; a < nacc; ++a) {
                     float w[16];
-                    ptx::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(a * g.acc_stride + c0), w);
+                    ptx::tmem_ld16(tl + (uint32_t)(a * g.acc_stride + c0), w);
 #pragma unroll
                     for (int u = 0; u < 16; ++u) v[u] += w[u];
                 }
@@ -255,7 +264,7 @@ __device__ __forceinline__ void gemm_body(const GemmArgs &g, int mt, int nt, uin
         } else {
             atomicExch(flag, 1);
         }
-    } else if (warp == 4) {
+    } else if (warp == kProdWarps) {
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
             const uint32_t idesc = ptx::instr_desc(g.tf32 ? 2 : 1, kBM, (uint32_t)g.BN);
@@ -317,13 +326,23 @@ __device__ __forceinline__ void gemm_body(const GemmArgs &g, int mt, int nt, uin
     if (warp == 0) ptx::tmem_dealloc(tmem, g.tmem_cols);
 }
 
-__global__ void __launch_bounds__(192, 1) k_gemm_split(GemmArgs g) {
+__global__ void __launch_bounds__(kGemmThreads, 2) k_gemm_split(GemmArgs g) {
     extern __shared__ __align__(128) uint8_t sm[];
     gemm_body(g, blockIdx.x, blockIdx.y, sm);
 }
 
+// Both trajectories of a line stage in one launch: blocks [0, n0) belong to g0 (m
+// tile b / nt0, n tile b % nt0, so the n tiles of an m tile run side by side and
+// share its A rows in L2), the rest to g1.
+__global__ void __launch_bounds__(kGemmThreads, 2) k_gemm_pair(GemmArgs g0, GemmArgs g1, int nt0, int n0, int nt1) {
+    extern __shared__ __align__(128) uint8_t sm[];
+    const int b = blockIdx.x;
+    if (b < n0) gemm_body(g0, b / nt0, b % nt0, sm);
+    else gemm_body(g1, (b - n0) / nt1, (b - n0) % nt1, sm);
+}
+
 // One launch for several GEMM problems: items[b] = (problem, m tile, n tile).
-__global__ void __launch_bounds__(192, 1) k_gemm_batch(const GemmArgs *__restrict__ args,
+__global__ void __launch_bounds__(kGemmThreads, 2) k_gemm_batch(const GemmArgs *__restrict__ args,
                                                        const int4 *__restrict__ items) {
     extern __shared__ __align__(128) uint8_t sm[];
     const int4 it = items[blockIdx.x];
@@ -431,8 +450,8 @@ size_t smem_for(int BN, int &stages) {
     return stages * stage + 256;
 }
 
-void launch(const mpi_ffl_handle *h, const float *A, int64_t lda, int Ka, const int *arow, int M, const Packed &B,
-            float *C, int64_t ldc, const int *crow, int Nc, const float *rscale, int rdiv, cudaStream_t st) {
+GemmArgs make_args(const mpi_ffl_handle *h, const float *A, int64_t lda, int Ka, const int *arow, int M,
+                   const Packed &B, float *C, int64_t ldc, const int *crow, int Nc, const float *rscale, int rdiv) {
     GemmArgs g{};
     g.A = A;
     g.lda = lda;
@@ -450,12 +469,26 @@ void launch(const mpi_ffl_handle *h, const float *A, int64_t lda, int Ka, const 
     g.rdiv = rdiv;
     g.prec = h->precision;
     g.tf32 = h->precision == MPI_FFL_PREC_TF32 ? 1 : 0;
-    const size_t smem = smem_for(B.BN, g.stages);
+    smem_for(B.BN, g.stages);
     set_accumulators(g);
     g.err = cs(h)->err;
     g.done = nullptr;
-    dim3 grid((M + kBM - 1) / kBM, B.ntile);
-    k_gemm_split<<<grid, 192, smem, st>>>(g);
+    return g;
+}
+
+// One GEMM problem per trajectory, all in one launch.
+void launch_problems(const GemmArgs *g, const Packed *const *B, int n, cudaStream_t st) {
+    int stages = 0;
+    size_t smem = 0;
+    for (int i = 0; i < n; ++i) smem = std::max(smem, smem_for(B[i]->BN, stages));
+    const int mt0 = (g[0].M + kBM - 1) / kBM;
+    if (n == 1) {
+        k_gemm_split<<<dim3(mt0, B[0]->ntile), kGemmThreads, smem, st>>>(g[0]);
+        return;
+    }
+    const int n0 = mt0 * B[0]->ntile;
+    const int n1 = (g[1].M + kBM - 1) / kBM * B[1]->ntile;
+    k_gemm_pair<<<n0 + n1, kGemmThreads, smem, st>>>(g[0], g[1], B[0]->ntile, n0, B[1]->ntile);
 }
 
 }  // namespace
@@ -616,6 +649,7 @@ void col_init(mpi_ffl_handle *h) {
     if (cudaMalloc((void **)&s->err, sizeof(int)) != cudaSuccess) return;
     cudaMemset(s->err, 0, sizeof(int));
     cudaFuncSetAttribute(k_gemm_split, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(k_gemm_pair, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     cudaGetLastError();
     s->ok = true;
 }
@@ -647,25 +681,31 @@ int col_take_error(mpi_ffl_handle *h) {
 void col_forward(mpi_ffl_handle *h, const float *in, bool full, const float *gain, float *data, cudaStream_t st) {
     ColState *s = cs(h);
     const Dims &d = h->d;
+    GemmArgs g[2];
+    const Packed *B[2];
+    const int f = h->precision == MPI_FFL_PREC_TF32 ? 1 : 0;
     for (int par = 0; par < s->n_par; ++par) {
-        const int f = h->precision == MPI_FFL_PREC_TF32 ? 1 : 0;
-        const Packed &B = full ? s->full_f[f][par] : s->evf_f[f][par];
-        launch(h, in, full ? d.N : d.Ne, full ? d.N : d.Ne, s->rows[par], s->nrows[par], B, data, 2 * d.nb,
-               s->rows[par], 2 * d.nb, gain, d.Nz, st);
+        B[par] = full ? &s->full_f[f][par] : &s->evf_f[f][par];
+        g[par] = make_args(h, in, full ? d.N : d.Ne, full ? d.N : d.Ne, s->rows[par], s->nrows[par], *B[par], data,
+                           2 * d.nb, s->rows[par], 2 * d.nb, gain, d.Nz);
     }
+    launch_problems(g, B, s->n_par, st);
 }
 
 // data -> fine (W^T) or data -> proj ((W H)^T), gain per line
 void col_adjoint(mpi_ffl_handle *h, const float *data, bool full, const float *gain, float *out, cudaStream_t st) {
     ColState *s = cs(h);
     const Dims &d = h->d;
+    GemmArgs g[2];
+    const Packed *B[2];
+    const int f = h->precision == MPI_FFL_PREC_TF32 ? 1 : 0;
+    const int nout = full ? d.N : d.Ne;
     for (int par = 0; par < s->n_par; ++par) {
-        const int f = h->precision == MPI_FFL_PREC_TF32 ? 1 : 0;
-        const Packed &B = full ? s->full_a[f][par] : s->evf_a[f][par];
-        const int nout = full ? d.N : d.Ne;
-        launch(h, data, 2 * d.nb, 2 * d.nb, s->rows[par], s->nrows[par], B, out, nout, s->rows[par], nout, gain,
-               d.Nz, st);
+        B[par] = full ? &s->full_a[f][par] : &s->evf_a[f][par];
+        g[par] = make_args(h, data, 2 * d.nb, 2 * d.nb, s->rows[par], s->nrows[par], *B[par], out, nout, s->rows[par],
+                           nout, gain, d.Nz);
     }
+    launch_problems(g, B, s->n_par, st);
 }
 
 size_t gemm_args_size() { return sizeof(GemmArgs); }
@@ -674,24 +714,30 @@ size_t gemm_args_size() { return sizeof(GemmArgs); }
 // args/items are host staging arrays; dargs/ditems their device copies (same
 // layout), already uploaded by the caller before this launch runs.
 int col_batch_prepare(mpi_ffl_handle *const *hs, const float *const *in, float *const *out, const int *const *done,
-                      int n, bool adjoint, void *args, int4 *items, int arg_cap, int item_cap, int &n_items) {
+                      int n, bool adjoint, void *args, int4 *items, int arg_cap, int item_cap, int &n_items,
+                      size_t &smem) {
     GemmArgs *a = reinterpret_cast<GemmArgs *>(args);
     int np = 0;
     n_items = 0;
+    smem = 0;
     for (int j = 0; j < n; ++j) {
         if (np + 2 > arg_cap) return -1;
         const int base_items = n_items;
         const int k = gemm_problems(hs[j], adjoint, in[j], out[j], done[j], a + np, items, item_cap, n_items);
         if (k < 0) return -1;
         for (int i = base_items; i < n_items; ++i) items[i].x += np;
+        for (int i = 0; i < k; ++i) {
+            int st = 0;
+            smem = std::max(smem, smem_for(a[np + i].BN, st));
+        }
         np += k;
     }
     return np;
 }
 
-void col_batch_launch(const void *dargs, const int4 *ditems, int n_items, cudaStream_t st) {
+void col_batch_launch(const void *dargs, const int4 *ditems, int n_items, size_t smem, cudaStream_t st) {
     if (n_items <= 0) return;
-    k_gemm_batch<<<n_items, 192, 227 * 1024, st>>>(reinterpret_cast<const GemmArgs *>(dargs), ditems);
+    k_gemm_batch<<<n_items, kGemmThreads, smem, st>>>(reinterpret_cast<const GemmArgs *>(dargs), ditems);
 }
 
 void col_batch_init() {

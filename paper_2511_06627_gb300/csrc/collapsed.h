@@ -1,5 +1,5 @@
 // Collapsed line operator (collapsed.cu): S D_Gamma F V E (and optionally H) as one
-// precomputed matrix per trajectory, applied with a split-bf16 tcgen05 GEMM.
+// precomputed matrix per trajectory, applied with a split-bf16 (or split-tf32) tcgen05 GEMM.
 #pragma once
 
 #include "internal.h"
@@ -16,11 +16,13 @@ void col_adjoint(mpi_ffl_handle *h, const float *data, bool full, const float *g
 
 // Batched full-GEMM line stages (continuous batching): fill host staging arrays of
 // GEMM problems and (problem, m tile, n tile) items for handles hs[0..n); returns the
-// number of problems or -1 when the capacities are too small.
+// number of problems or -1 when the capacities are too small, and in smem the dynamic
+// shared memory the launch needs.
 size_t gemm_args_size();
 int col_batch_prepare(mpi_ffl_handle *const *hs, const float *const *in, float *const *out, const int *const *done,
-                      int n, bool adjoint, void *args, int4 *items, int arg_cap, int item_cap, int &n_items);
-void col_batch_launch(const void *dargs, const int4 *ditems, int n_items, cudaStream_t st);
+                      int n, bool adjoint, void *args, int4 *items, int arg_cap, int item_cap, int &n_items,
+                      size_t &smem);
+void col_batch_launch(const void *dargs, const int4 *ditems, int n_items, size_t smem, cudaStream_t st);
 void col_batch_init();
 
 // host-side model pieces shared with the table builders (api.cu)
