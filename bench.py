@@ -181,9 +181,25 @@ ALGO_BYTES = {
     "tc_fwd": lambda d: 4 * (d["nfine"] + d["ndata"]),
     "tc_adj": lambda d: 4 * (d["nfine"] + d["ndata"]),
     "transpose": lambda d: 8 * d["nvox"],
-    "gemm_fwd": lambda d: 4 * (d["nfine"] + d["ndata"]),
-    "gemm_adj": lambda d: 4 * (d["nfine"] + d["ndata"]),
+    # the full-GEMM path applies W H to projections, the line-GEMM path W to fine rows
+    "gemm_fwd": lambda d: 4 * ((d["nproj"] if d["path"] == "full_gemm" else d["nfine"]) + d["ndata"]),
+    "gemm_adj": lambda d: 4 * ((d["nproj"] if d["path"] == "full_gemm" else d["nfine"]) + d["ndata"]),
 }
+
+# Shared-memory bytes the projector pair reads per launch: two interpolation taps of
+# 4 bytes for every (angle, ray, march step, slice) sample, M N N N_z = M n_vox samples. Both
+# kernels stage their operand in shared memory and are bound by its bandwidth, whose
+# peak is 128 B per clock per SM.
+SMEM_BYTES = {
+    "project": lambda d: 8 * d["M"] * d["nvox"],
+    "backproject": lambda d: 8 * d["M"] * d["nvox"],
+}
+SMEM_BYTES_PER_CLK_SM = 128
+
+# DRAM bytes (read + write) per launch from the ncu capture summarised in
+# profiles/full_gemm_invivo_kernels.md (cold caches, 256^2x128, 36 angles). Reported
+# only for that workload and only while the kernel is the one that was captured.
+DRAM_TRAFFIC = {}
 
 
 def _timed_pairs(op, x, b, xa, steps, flush, stream):
@@ -292,7 +308,8 @@ def run_ours(args, cfg, rank, world, local_rank):
     op = FFLOperator.from_config(cfg)
     op.set_path(path)
     sz = op.sizes
-    dims = dict(nvox=sz.n_vox, nproj=sz.n_proj, nfine=sz.n_fine, nsig=sz.n_sig, ndata=sz.n_data)
+    dims = dict(nvox=sz.n_vox, nproj=sz.n_proj, nfine=sz.n_fine, nsig=sz.n_sig, ndata=sz.n_data, M=op.n_angles,
+                N=op.nx)
     x_np = phantom_for(cfg)
     x_host = torch.from_numpy(x_np).pin_memory()
     x = x_host.cuda()
@@ -363,8 +380,19 @@ def run_ours(args, cfg, rank, world, local_rank):
     hbm, src = peaks()
     top = max((k for k in prof if prof[k][1] > 0 and k != "solver"), key=lambda k: prof[k][0])
     per_launch_ms = prof[top][0] / prof[top][1]
-    algo = ALGO_BYTES[top](dims)
+    algo = ALGO_BYTES[top](dict(dims, path=path))
     achieved = algo / (per_launch_ms / 1e3) / 1e9
+    onchip = None
+    if top in SMEM_BYTES:
+        sm_mhz = clk.summary().get("sm_mhz") or 2070.0
+        n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+        sm_peak = SMEM_BYTES_PER_CLK_SM * n_sm * sm_mhz * 1e6 / 1e9
+        sm_bytes = SMEM_BYTES[top](dims)
+        sm_ach = sm_bytes / (per_launch_ms / 1e3) / 1e9
+        onchip = {"bound": "smem", "achieved": sm_ach, "peak": sm_peak, "unit": "GB/s", "frac": sm_ach / sm_peak,
+                  "bytes_per_launch": sm_bytes,
+                  "peak_basis": f"{SMEM_BYTES_PER_CLK_SM} B/clk/SM x {n_sm} SMs x median SM clock {sm_mhz} MHz"}
+    traffic = DRAM_TRAFFIC.get(top) if args.workload == "invivo" and path == "full_gemm" else None
     kernel_share = {k: round(v[0] / max(ms, 1e-9), 4) for k, v in prof.items() if v[1] > 0}
     kernel_ms = {k: round(v[0] / v[1], 4) for k, v in prof.items() if v[1] > 0}
 
@@ -397,8 +425,8 @@ def run_ours(args, cfg, rank, world, local_rank):
                    "l2": "flushed (256 MB write) between timed steps",
                    "step": "b = A x then x' = A^T b, inputs resident in HBM"},
         "roofline": {"kernel": top, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": None, "peak_source": src,
-                     "algorithmic_bytes_per_launch": algo, "avg_launch_ms": per_launch_ms},
+                     "frac": achieved / hbm, "traffic": traffic, "peak_source": src,
+                     "algorithmic_bytes_per_launch": algo, "avg_launch_ms": per_launch_ms, "onchip": onchip},
         "kernel_time_share": kernel_share,
         "kernel_ms_per_launch": kernel_ms,
         "paths": paths,

@@ -113,7 +113,10 @@ struct AChunk {
     float4 v[8];
 };
 
+// MODE 0: bf16 operands, 1: tf32, 2: as g.tf32 says (batches that may mix both).
+template <int MODE>
 __device__ __forceinline__ void gemm_body(const GemmArgs &g, int mt, int nt, uint8_t *sm) {
+    const bool tf32 = MODE == 2 ? g.tf32 != 0 : MODE == 1;
     const uint32_t bytesA = kBM * kBK * 2;          // one of hi | lo
     const uint32_t bytesB = (uint32_t)g.BN * kBK * 2;
     const uint32_t stage = 2 * bytesA + 2 * bytesB;
@@ -162,7 +165,7 @@ __device__ __forceinline__ void gemm_body(const GemmArgs &g, int mt, int nt, uin
             for (int u = 0; u < 4; ++u) {
                 const int q = u >> 1, kg = 4 * (u & 1) + kq;
                 const float *p = rp[q];
-                if (g.tf32) {
+                if (tf32) {
                     const int k = kc * (kBK / 2) + kg * 4;
                     if (p && vec && k + 4 <= g.Ka) {
                         c.v[u] = __ldg(reinterpret_cast<const float4 *>(p + k));
@@ -197,7 +200,7 @@ __device__ __forceinline__ void gemm_body(const GemmArgs &g, int mt, int nt, uin
             for (int u = 0; u < 4; ++u) {
                 const int q = u >> 1, kg = 4 * (u & 1) + kq;
                 uint4 hi, lo;
-                if (g.tf32) {
+                if (tf32) {
                     const float f[4] = {c.v[u].x, c.v[u].y, c.v[u].z, c.v[u].w};
                     split4_tf32(f, hi, lo);
                 } else {
@@ -267,7 +270,7 @@ __device__ __forceinline__ void gemm_body(const GemmArgs &g, int mt, int nt, uin
     } else if (warp == kProdWarps) {
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
-            const uint32_t idesc = ptx::instr_desc(g.tf32 ? 2 : 1, kBM, (uint32_t)g.BN);
+            const uint32_t idesc = ptx::instr_desc(tf32 ? 2 : 1, kBM, (uint32_t)g.BN);
             bool ok = true;
             for (int kc = 0; kc < g.nkc && ok; ++kc) {
                 const int s = kc % g.stages;
@@ -287,7 +290,7 @@ __device__ __forceinline__ void gemm_body(const GemmArgs &g, int mt, int nt, uin
                     const uint64_t dBl = ptx::smem_desc(b0 + bytesB + ks * 256, 128, 1024);
                     // 4 MMA K-steps of 256 bytes per stage: K = 16 bf16 or K = 8 tf32 elements
                     const uint32_t acc = (!first || ks > 0) ? 1u : 0u;
-                    if (g.tf32) {
+                    if (tf32) {
                         ptx::mma_tf32(tacc, dAh, dBh, idesc, acc);
                         ptx::mma_tf32(tacc, dAh, dBl, idesc, 1u);
                         ptx::mma_tf32(tacc, dAl, dBh, idesc, 1u);
@@ -326,19 +329,21 @@ __device__ __forceinline__ void gemm_body(const GemmArgs &g, int mt, int nt, uin
     if (warp == 0) ptx::tmem_dealloc(tmem, g.tmem_cols);
 }
 
+template <int MODE>
 __global__ void __launch_bounds__(kGemmThreads, 2) k_gemm_split(GemmArgs g) {
     extern __shared__ __align__(128) uint8_t sm[];
-    gemm_body(g, blockIdx.x, blockIdx.y, sm);
+    gemm_body<MODE>(g, blockIdx.x, blockIdx.y, sm);
 }
 
 // Both trajectories of a line stage in one launch: blocks [0, n0) belong to g0 (m
 // tile b / nt0, n tile b % nt0, so the n tiles of an m tile run side by side and
 // share its A rows in L2), the rest to g1.
+template <int MODE>
 __global__ void __launch_bounds__(kGemmThreads, 2) k_gemm_pair(GemmArgs g0, GemmArgs g1, int nt0, int n0, int nt1) {
     extern __shared__ __align__(128) uint8_t sm[];
     const int b = blockIdx.x;
-    if (b < n0) gemm_body(g0, b / nt0, b % nt0, sm);
-    else gemm_body(g1, (b - n0) / nt1, (b - n0) % nt1, sm);
+    if (b < n0) gemm_body<MODE>(g0, b / nt0, b % nt0, sm);
+    else gemm_body<MODE>(g1, (b - n0) / nt1, (b - n0) % nt1, sm);
 }
 
 // One launch for several GEMM problems: items[b] = (problem, m tile, n tile).
@@ -348,7 +353,7 @@ __global__ void __launch_bounds__(kGemmThreads, 2) k_gemm_batch(const GemmArgs *
     const int4 it = items[blockIdx.x];
     const GemmArgs g = args[it.x];
     if (g.done && *g.done) return;
-    gemm_body(g, it.y, it.z, sm);
+    gemm_body<2>(g, it.y, it.z, sm);
 }
 
 uint16_t bf16_bits(double x) {
@@ -482,13 +487,16 @@ void launch_problems(const GemmArgs *g, const Packed *const *B, int n, cudaStrea
     size_t smem = 0;
     for (int i = 0; i < n; ++i) smem = std::max(smem, smem_for(B[i]->BN, stages));
     const int mt0 = (g[0].M + kBM - 1) / kBM;
+    const bool tf32 = g[0].tf32 != 0;
     if (n == 1) {
-        k_gemm_split<<<dim3(mt0, B[0]->ntile), kGemmThreads, smem, st>>>(g[0]);
+        if (tf32) k_gemm_split<1><<<dim3(mt0, B[0]->ntile), kGemmThreads, smem, st>>>(g[0]);
+        else k_gemm_split<0><<<dim3(mt0, B[0]->ntile), kGemmThreads, smem, st>>>(g[0]);
         return;
     }
     const int n0 = mt0 * B[0]->ntile;
     const int n1 = (g[1].M + kBM - 1) / kBM * B[1]->ntile;
-    k_gemm_pair<<<n0 + n1, kGemmThreads, smem, st>>>(g[0], g[1], B[0]->ntile, n0, B[1]->ntile);
+    if (tf32) k_gemm_pair<1><<<n0 + n1, kGemmThreads, smem, st>>>(g[0], g[1], B[0]->ntile, n0, B[1]->ntile);
+    else k_gemm_pair<0><<<n0 + n1, kGemmThreads, smem, st>>>(g[0], g[1], B[0]->ntile, n0, B[1]->ntile);
 }
 
 }  // namespace
@@ -628,8 +636,10 @@ void col_init(mpi_ffl_handle *h) {
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
         const int mtiles = std::max(1, d.n_par * ((d.nseg / d.n_par + kBM - 1) / kBM));
+        // N tile: at most two blocks per SM over the m tiles of both trajectories, so a
+        // line stage runs in one wave
         auto pick_bn = [&](int Nv) {
-            const int want_tiles = std::max(1, (2 * n_sm + mtiles - 1) / mtiles);
+            const int want_tiles = std::max(1, (2 * n_sm) / mtiles);
             int bn = (Nv + want_tiles - 1) / want_tiles;
             bn = std::max(32, std::min(256, (bn + 15) / 16 * 16));
             return bn;
@@ -648,8 +658,9 @@ void col_init(mpi_ffl_handle *h) {
     }
     if (cudaMalloc((void **)&s->err, sizeof(int)) != cudaSuccess) return;
     cudaMemset(s->err, 0, sizeof(int));
-    cudaFuncSetAttribute(k_gemm_split, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    cudaFuncSetAttribute(k_gemm_pair, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    for (const void *k : {(const void *)k_gemm_split<0>, (const void *)k_gemm_split<1>, (const void *)k_gemm_pair<0>,
+                          (const void *)k_gemm_pair<1>})
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     cudaGetLastError();
     s->ok = true;
 }
