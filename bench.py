@@ -199,7 +199,10 @@ SMEM_BYTES_PER_CLK_SM = 128
 # DRAM bytes (read + write) per launch from the ncu capture summarised in
 # profiles/full_gemm_invivo_kernels.md (cold caches, 256^2x128, 36 angles). Reported
 # only for that workload and only while the kernel is the one that was captured.
-DRAM_TRAFFIC = {}
+DRAM_TRAFFIC = {
+    "project": 67_124_992 + 1_128_704,   # reads the volume and its transposed copy
+    "backproject": 4_734_464 + 0,        # reads the projections; the volume it writes stays in L2
+}
 
 
 def _timed_pairs(op, x, b, xa, steps, flush, stream):
@@ -354,27 +357,60 @@ def run_ours(args, cfg, rank, world, local_rank):
     pairs = args.steps * world
     value = pairs / (ms / 1e3)
 
-    # ---- end to end through the public API with host buffers
-    out_host = torch.empty(op.vol_shape, dtype=torch.float32).pin_memory()
-    for _ in range(2):
-        x.copy_(x_host, non_blocking=True)
-        step()
-        out_host.copy_(xa, non_blocking=True)
+    # ---- end to end through the public API with host buffers: forward reads a pinned
+    # host volume and adjoint writes a pinned host volume; the library stages both. Two
+    # handles on two streams take alternate steps, so one step's copies overlap the
+    # other's kernels (the way a stream of volumes is fed); each handle also copies its
+    # next input on its own stream.
+    ops = [op, FFLOperator.from_config(cfg)]
+    ops[1].set_path(path)
+    streams = [stream, torch.cuda.Stream()]
+    bufs = [b, ops[1].new_data()]
+    outs = [torch.empty(op.vol_shape, dtype=torch.float32).pin_memory() for _ in range(2)]
+    for o in ops:
+        o.set_host_overlap(True)
+
+    def e2e_step(k):
+        i = k % 2
+        with torch.cuda.stream(streams[i]):
+            ops[i].forward(x_host, out=bufs[i])
+            ops[i].adjoint(bufs[i], out=outs[i])
+
+    def e2e_time(step_fn, n):
+        ta = torch.cuda.Event(enable_timing=True)
+        tb = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ta.record(streams[0])
+        for k in range(n):
+            step_fn(k)
+        tb.record(streams[0])
+        torch.cuda.synchronize()
+        return ta.elapsed_time(tb)
+
+    # one handle, one stream: each step's copies in series with its kernels except the
+    # next input copy, which the handle overlaps
+    e2e_step(0)
+    e2e_serial_ms = e2e_time(lambda k: e2e_step(0), args.steps)
+    for k in range(4):
+        e2e_step(k)
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        x.copy_(x_host, non_blocking=True)
-        step()
-        out_host.copy_(xa, non_blocking=True)
-    e1.record(stream)
+    e0.record(streams[0])
+    streams[1].wait_event(e0)
+    for k in range(args.steps):
+        e2e_step(k)
+    streams[0].wait_stream(streams[1])
+    e1.record(streams[0])
     torch.cuda.synchronize()
+    for o in ops:
+        o.set_host_overlap(False)
+    ops[1].close()
     e2e_ms = e0.elapsed_time(e1)
     if dist:
-        t = torch.tensor([e2e_ms], device="cuda", dtype=torch.float64)
+        t = torch.tensor([e2e_ms, e2e_serial_ms], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+        e2e_ms, e2e_serial_ms = float(t[0].item()), float(t[1].item())
 
     # ---- roofline of the dominant kernel (times measured inside the timed region)
     hbm, src = peaks()
@@ -432,7 +468,11 @@ def run_ours(args, cfg, rank, world, local_rank):
         "paths": paths,
         "speedup_vs_plain_fp32": (value / plain) if plain else None,
         "e2e": {"value": pairs / (e2e_ms / 1e3), "unit": "pairs/s", "h2d_bytes_per_step": 4 * sz.n_vox,
-                "d2h_bytes_per_step": 4 * sz.n_vox},
+                "d2h_bytes_per_step": 4 * sz.n_vox,
+                "how": "forward(pinned host x) + adjoint(-> pinned host x') through the C ABI, which stages host "
+                       "buffers; two handles on two streams take alternate steps",
+                "serial_value": pairs / (e2e_serial_ms / 1e3),
+                "serial_how": "the same calls on one handle and one stream"},
         "clocks": clk.summary(),
         "gpu_launches": int(launches),
         "wall_s_timed_region": t_wall,

@@ -189,11 +189,25 @@ int mpi_ffl_set_psf_fwhm(mpi_ffl_handle *h, double fwhm_vox);
  * the stream holds a CUDA error (MPI_FFL_ERR_CUDA). */
 int mpi_ffl_sync_check(mpi_ffl_handle *h, void *stream);
 
-/* b = A x (Sec. 2.2, Eq. (23)). d_x: n_vox floats; d_b_ri: n_data floats (written). */
-int mpi_ffl_forward(mpi_ffl_handle *h, const float *d_x, float *d_b_ri, void *stream);
+/* b = A x (Sec. 2.2, Eq. (23)). x: n_vox floats; b_ri: n_data floats (written).
+ * Either buffer may be device memory or host memory (pinned for asynchronous
+ * copies): a host input is copied to the handle's device staging before use and a
+ * host output is copied back on `stream`, so it is complete when the stream is. The
+ * call is asynchronous: a host input must stay unchanged until the stream's work
+ * has completed. */
+int mpi_ffl_forward(mpi_ffl_handle *h, const float *x, float *b_ri, void *stream);
 
-/* x = A^T b = Re(A^H b) (transpose of Eq. (23) under the real inner product). */
-int mpi_ffl_adjoint(mpi_ffl_handle *h, const float *d_b_ri, float *d_x, void *stream);
+/* x = A^T b = Re(A^H b) (transpose of Eq. (23) under the real inner product). Host
+ * or device buffers, as mpi_ffl_forward. */
+int mpi_ffl_adjoint(mpi_ffl_handle *h, const float *b_ri, float *x, void *stream);
+
+/* on != 0: host inputs of forward/adjoint are copied on a stream of the handle that
+ * waits only for the previous use of its (double-buffered) staging slot, so the copy
+ * for the next call overlaps the work already queued on `stream`. The caller must
+ * then not produce a host input with work queued on `stream` (for example a host
+ * output of the previous call) without synchronising the stream first. Default 0:
+ * copies are ordered on `stream`. */
+int mpi_ffl_set_host_overlap(mpi_ffl_handle *h, int32_t on);
 
 /* One stage of A or of A^T on caller buffers, for stage-by-stage checks:
  *   stage 0 = P   (n_vox  <-> n_proj)      stage 1 = H (n_proj <-> n_fine)

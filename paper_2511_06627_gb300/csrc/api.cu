@@ -362,8 +362,79 @@ void release(mpi_ffl_handle *h) {
         cudaEventDestroy(r.b);
     }
     for (auto e : h->ev_pool) cudaEventDestroy(e);
+    for (float *p : {h->hs_in[0], h->hs_in[1], h->hs_out})
+        if (p) cudaFree(p);
+    for (int k = 0; k < 2; ++k) {
+        if (h->hs_ready[k]) cudaEventDestroy(h->hs_ready[k]);
+        if (h->hs_free[k]) cudaEventDestroy(h->hs_free[k]);
+    }
+    if (h->hs_copy) cudaStreamDestroy(h->hs_copy);
     tc_release(h);
     col_release(h);
+}
+
+// ------------------------------------------------------------ host buffers
+// A pointer CUDA does not know as device or managed memory is a host buffer.
+bool is_host_ptr(const void *p) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return true;
+    }
+    return a.type == cudaMemoryTypeHost || a.type == cudaMemoryTypeUnregistered;
+}
+
+void ensure_host_staging(mpi_ffl_handle *h) {
+    const int64_t n = std::max(h->d.nvox, h->d.ndata);
+    for (float **p : {&h->hs_in[0], &h->hs_in[1], &h->hs_out})
+        if (!*p) dev_alloc(h, p, n);
+    if (!h->hs_copy) CK(cudaStreamCreateWithFlags(&h->hs_copy, cudaStreamNonBlocking));
+    for (int k = 0; k < 2; ++k) {
+        if (!h->hs_ready[k]) CK(cudaEventCreateWithFlags(&h->hs_ready[k], cudaEventDisableTiming));
+        if (!h->hs_free[k]) CK(cudaEventCreateWithFlags(&h->hs_free[k], cudaEventDisableTiming));
+    }
+}
+
+// Device copy of a host input of n floats. With host_overlap the copy runs on the
+// handle's copy stream (it waits only for the previous use of its staging slot, so it
+// overlaps earlier work on `st`); otherwise on `st`. `slot` is released by host_done.
+const float *host_in(mpi_ffl_handle *h, const float *src, int64_t n, cudaStream_t st, int &slot) {
+    ensure_host_staging(h);
+    slot = h->hs_slot;
+    h->hs_slot ^= 1;
+    float *dst = h->hs_in[slot];
+    if (h->host_overlap) {
+        CK(cudaStreamWaitEvent(h->hs_copy, h->hs_free[slot], 0));
+        CK(cudaMemcpyAsync(dst, src, sizeof(float) * n, cudaMemcpyHostToDevice, h->hs_copy));
+        CK(cudaEventRecord(h->hs_ready[slot], h->hs_copy));
+        CK(cudaStreamWaitEvent(st, h->hs_ready[slot], 0));
+    } else {
+        CK(cudaMemcpyAsync(dst, src, sizeof(float) * n, cudaMemcpyHostToDevice, st));
+    }
+    return dst;
+}
+
+void host_done(mpi_ffl_handle *h, int slot, cudaStream_t st) {
+    if (slot >= 0) CK(cudaEventRecord(h->hs_free[slot], st));
+}
+
+// Runs op(in_dev, out_dev) with host inputs and outputs staged through the handle's
+// device buffers; a host output is copied back on `st`.
+template <class F>
+void with_host_buffers(mpi_ffl_handle *h, const float *in, int64_t n_in, float *out, int64_t n_out,
+                       cudaStream_t st, F op) {
+    int slot = -1;
+    const float *din = in;
+    float *dout = out;
+    if (is_host_ptr(in)) din = host_in(h, in, n_in, st, slot);
+    const bool out_host = is_host_ptr(out);
+    if (out_host) {
+        ensure_host_staging(h);
+        dout = h->hs_out;
+    }
+    op(din, dout);
+    host_done(h, slot, st);
+    if (out_host) CK(cudaMemcpyAsync(out, dout, sizeof(float) * n_out, cudaMemcpyDeviceToHost, st));
 }
 
 cudaStream_t S(void *s) { return (cudaStream_t)s; }
@@ -799,26 +870,38 @@ extern "C" int mpi_ffl_sync_check(mpi_ffl_handle *h, void *stream) {
     });
 }
 
-extern "C" int mpi_ffl_forward(mpi_ffl_handle *h, const float *d_x, float *d_b, void *stream) {
+extern "C" int mpi_ffl_forward(mpi_ffl_handle *h, const float *x, float *b, void *stream) {
     return guarded(h, [&]() {
-        if (!d_x || !d_b) {
+        if (!x || !b) {
             h->err = "NULL buffer";
             return MPI_FFL_ERR_INVALID_ARG;
         }
-        forward_impl(h, d_x, d_b, h->t_htab, h->t_gain, S(stream));
+        cudaStream_t st = S(stream);
+        with_host_buffers(h, x, h->d.nvox, b, h->d.ndata, st, [&](const float *dx, float *db) {
+            forward_impl(h, dx, db, h->t_htab, h->t_gain, st);
+        });
         return MPI_FFL_OK;
     });
 }
 
-extern "C" int mpi_ffl_adjoint(mpi_ffl_handle *h, const float *d_b, float *d_x, void *stream) {
+extern "C" int mpi_ffl_adjoint(mpi_ffl_handle *h, const float *b, float *x, void *stream) {
     return guarded(h, [&]() {
-        if (!d_x || !d_b) {
+        if (!x || !b) {
             h->err = "NULL buffer";
             return MPI_FFL_ERR_INVALID_ARG;
         }
-        adjoint_impl(h, d_b, d_x, S(stream));
+        cudaStream_t st = S(stream);
+        with_host_buffers(h, b, h->d.ndata, x, h->d.nvox, st, [&](const float *db, float *dx) {
+            adjoint_impl(h, db, dx, st);
+        });
         return MPI_FFL_OK;
     });
+}
+
+extern "C" int mpi_ffl_set_host_overlap(mpi_ffl_handle *h, int32_t on) {
+    if (!h) return MPI_FFL_ERR_INVALID_ARG;
+    h->host_overlap = on ? 1 : 0;
+    return MPI_FFL_OK;
 }
 
 extern "C" int mpi_ffl_apply_stage(mpi_ffl_handle *h, int32_t stage, int32_t transpose, const float *in,

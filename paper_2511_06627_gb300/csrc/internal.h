@@ -126,6 +126,13 @@ struct mpi_ffl_handle {
     void *col_state = nullptr;  // collapsed line operator (collapsed.cu)
     int path = 0;               // MPI_FFL_PATH_*
     int64_t bytes = 0;
+    // host buffers given to forward/adjoint: device staging, allocated on first use
+    float *hs_in[2] = {nullptr, nullptr};  // copies of host inputs, alternating
+    float *hs_out = nullptr;                // result before its copy to a host output
+    cudaStream_t hs_copy = nullptr;         // input copies when host_overlap is on
+    cudaEvent_t hs_ready[2] = {}, hs_free[2] = {};
+    int hs_slot = 0;
+    int host_overlap = 0;                   // mpi_ffl_set_host_overlap
 };
 
 namespace mpiffl {

@@ -34,33 +34,41 @@ __global__ void k_transpose_xy(const float *__restrict__ vol, float *__restrict_
 }
 
 // Vector form (N % 4 == 0, 16-byte aligned): a block of 8 x 32 threads moves one 32 x 32
-// tile; thread (tx, ty) reads 4 consecutive x of row ty and writes 4 consecutive y of
-// output row ty. The column reads of the padded tile hit 32 distinct banks per warp.
+// tile of two slices; thread (tx, ty) reads 4 consecutive x of row ty of both slices
+// (two 16-byte loads in flight) and writes 4 consecutive y of output row ty. The
+// column reads of the padded tiles hit 32 distinct banks per warp.
 __global__ void __launch_bounds__(256) k_transpose_xy4(const float *__restrict__ vol, float *__restrict__ volT,
-                                                       int N) {
-    __shared__ float tile[32][33];
+                                                       int N, int Nz) {
+    __shared__ float tile[2][32][33];
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 32;
-    const float *src = vol + (size_t)blockIdx.z * N * N;
-    float *dst = volT + (size_t)blockIdx.z * N * N;
-    if (y0 + ty < N && x0 + 4 * tx < N) {
-        const float4 v = __ldg(reinterpret_cast<const float4 *>(src + (y0 + ty) * N + x0 + 4 * tx));
-        tile[ty][4 * tx] = v.x;
-        tile[ty][4 * tx + 1] = v.y;
-        tile[ty][4 * tx + 2] = v.z;
-        tile[ty][4 * tx + 3] = v.w;
+    const int z0 = 2 * blockIdx.z;
+    const size_t slice = (size_t)N * N;
+    float4 v[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+        if (z0 + u < Nz && y0 + ty < N && x0 + 4 * tx < N)
+            v[u] = __ldg(reinterpret_cast<const float4 *>(vol + (z0 + u) * slice + (y0 + ty) * N + x0 + 4 * tx));
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        tile[u][ty][4 * tx] = v[u].x;
+        tile[u][ty][4 * tx + 1] = v[u].y;
+        tile[u][ty][4 * tx + 2] = v[u].z;
+        tile[u][ty][4 * tx + 3] = v[u].w;
     }
     __syncthreads();
-    if (x0 + ty < N && y0 + 4 * tx < N) {
-        const float4 v = make_float4(tile[4 * tx][ty], tile[4 * tx + 1][ty], tile[4 * tx + 2][ty], tile[4 * tx + 3][ty]);
-        *reinterpret_cast<float4 *>(dst + (x0 + ty) * N + y0 + 4 * tx) = v;
-    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+        if (z0 + u < Nz && x0 + ty < N && y0 + 4 * tx < N)
+            *reinterpret_cast<float4 *>(volT + (z0 + u) * slice + (x0 + ty) * N + y0 + 4 * tx) =
+                make_float4(tile[u][4 * tx][ty], tile[u][4 * tx + 1][ty], tile[u][4 * tx + 2][ty],
+                            tile[u][4 * tx + 3][ty]);
 }
 
 void launch_transpose_xy(const float *vol, float *volT, int N, int Nz, cudaStream_t st) {
     if (N % 4 == 0 && ((reinterpret_cast<uintptr_t>(vol) | reinterpret_cast<uintptr_t>(volT)) & 15) == 0) {
-        dim3 grid((N + 31) / 32, (N + 31) / 32, Nz), block(8, 32);
-        k_transpose_xy4<<<grid, block, 0, st>>>(vol, volT, N);
+        dim3 grid((N + 31) / 32, (N + 31) / 32, (Nz + 1) / 2), block(8, 32);
+        k_transpose_xy4<<<grid, block, 0, st>>>(vol, volT, N, Nz);
         return;
     }
     dim3 grid((N + 31) / 32, (N + 31) / 32, Nz), block(32, 8);

@@ -93,9 +93,11 @@ class FFLOperator:
     def data_shape(self):
         return (self.n_angles, self.nz, self.n_bins, 2)
 
-    def _check(self, t, shape, name):
-        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
-            raise TypeError(f"{name} must be a contiguous float32 CUDA tensor")
+    def _check(self, t, shape, name, host_ok=False):
+        on_dev = isinstance(t, torch.Tensor) and (t.is_cuda or (host_ok and t.device.type == "cpu"))
+        if not (on_dev and t.dtype == torch.float32 and t.is_contiguous()):
+            where = "CUDA or host" if host_ok else "CUDA"
+            raise TypeError(f"{name} must be a contiguous float32 {where} tensor")
         if t.numel() != math.prod(shape):
             raise ValueError(f"{name} has {t.numel()} elements, expected {math.prod(shape)}")
 
@@ -107,16 +109,19 @@ class FFLOperator:
 
     # ---------------------------------------------------------------- operator
     def forward(self, x, out=None):
-        self._check(x, self.vol_shape, "x")
+        """b = A x. x and out may be CUDA tensors or (pinned) host tensors; host buffers
+        are staged by the library. Asynchronous on the current stream."""
+        self._check(x, self.vol_shape, "x", host_ok=True)
         out = self.new_data() if out is None else out
-        self._check(out, self.data_shape, "out")
+        self._check(out, self.data_shape, "out", host_ok=True)
         check(self._lib.mpi_ffl_forward(self._h, _ptr(x), _ptr(out), _stream()), self._h)
         return out
 
     def adjoint(self, b, out=None):
-        self._check(b, self.data_shape, "b")
+        """x = A^T b; CUDA or host tensors, as forward."""
+        self._check(b, self.data_shape, "b", host_ok=True)
         out = self.new_volume() if out is None else out
-        self._check(out, self.vol_shape, "out")
+        self._check(out, self.vol_shape, "out", host_ok=True)
         check(self._lib.mpi_ffl_adjoint(self._h, _ptr(b), _ptr(out), _stream()), self._h)
         return out
 
@@ -236,6 +241,11 @@ class FFLOperator:
     # ---------------------------------------------------------------- settings
     def set_precision(self, precision):
         check(self._lib.mpi_ffl_set_precision(self._h, int(precision)), self._h)
+
+    def set_host_overlap(self, on=True):
+        """Copy host inputs of forward/adjoint on the handle's own stream, overlapping
+        the work already queued (see mpi_ffl_set_host_overlap)."""
+        check(self._lib.mpi_ffl_set_host_overlap(self._h, int(bool(on))), self._h)
 
     @property
     def precision(self):

@@ -82,3 +82,25 @@ def test_unconstrained_solve_matches_oracle(tiny):
                             b, tiny["shape"], tiny["tau"], tiny["lam"], 20, nonneg=False)
     x, _ = tiny["op"].solve(_t(to_interleaved(b)), iters=20, lam=tiny["lam"], tau=tiny["tau"], nonneg=False)
     assert rel_l2(x.cpu().numpy(), x_ref) < RECON_TOL
+
+
+@pytest.mark.parametrize("path", ["staged", "full_gemm"])
+def test_non_finite_data_stop_the_solve(tiny, path):
+    """A NaN in the data makes the FP64 residual non-finite: the solve stops and returns
+    MPI_FFL_ERR_NONFINITE instead of iterating on garbage."""
+    from paper_2511_06627_gb300 import FFLOperator, MpiFflError
+    from paper_2511_06627_gb300._lib import ERR_NONFINITE
+
+    op = FFLOperator.from_config(tiny["cfg"])
+    op.set_path(path)
+    b = to_interleaved(tiny["b"]).astype(np.float32)
+    b.flat[17] = np.nan
+    with pytest.raises(MpiFflError) as ei:
+        op.solve(_t(b), iters=20, lam=tiny["lam"], tau=tiny["tau"])
+    assert ei.value.code == ERR_NONFINITE
+    # the handle stays usable: a clean solve afterwards matches a fresh handle
+    x1, _ = op.solve(_t(to_interleaved(tiny["b"])), iters=10, lam=tiny["lam"], tau=tiny["tau"])
+    fresh = FFLOperator.from_config(tiny["cfg"])
+    fresh.set_path(path)
+    x2, _ = fresh.solve(_t(to_interleaved(tiny["b"])), iters=10, lam=tiny["lam"], tau=tiny["tau"])
+    assert np.array_equal(x1.cpu().numpy(), x2.cpu().numpy())
