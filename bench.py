@@ -205,6 +205,55 @@ DRAM_TRAFFIC = {
 }
 
 
+def use_path(op, key):
+    """Select an evaluation path by key ('full_gemm', 'full_gemm_tf32', ...) with its
+    precision set explicitly (set_path keeps TF32 between the two GEMM paths)."""
+    from paper_2511_06627_gb300 import PREC_BF16X3, PREC_TF32
+
+    tf32 = key.endswith("_tf32")
+    p = key[: -len("_tf32")] if tf32 else key
+    op.set_path(p)
+    if p in ("line_gemm", "full_gemm"):
+        op.set_precision(PREC_TF32 if tf32 else PREC_BF16X3)
+
+
+def bf16_peak_tflops():
+    try:
+        with open(PEAKS_PATH) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured"
+    except Exception:
+        return 1900.0, "fallback"
+
+
+def kernel_rooflines(prof, d, hbm, sm_mhz):
+    """Per kernel kind of the timed region: achieved algorithmic HBM GB/s against the
+    measured copy peak; for the projector pair also the shared-memory roofline; for the
+    GEMMs the tensor rate (3 bf16 products of 2 M N K flops) against the measured bf16
+    peak."""
+    import torch
+
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    sm_peak = SMEM_BYTES_PER_CLK_SM * n_sm * sm_mhz * 1e6 / 1e9
+    bf16, _ = bf16_peak_tflops()
+    nz = d["nvox"] // (d["N"] * d["N"])
+    nseg = d["M"] * nz
+    rows_k = d["N"] if d["path"] == "full_gemm" else d["nfine"] // nseg
+    out = {}
+    for k, (t_ms, n) in prof.items():
+        if n <= 0 or k not in ALGO_BYTES:
+            continue
+        sec = t_ms / n / 1e3
+        e = {"ms_per_launch": t_ms / n, "hbm_frac": ALGO_BYTES[k](d) / sec / 1e9 / hbm}
+        if k in SMEM_BYTES:
+            e["smem_frac"] = SMEM_BYTES[k](d) / sec / 1e9 / sm_peak
+        if k in ("gemm_fwd", "gemm_adj"):
+            flops = 3 * 2 * nseg * (d["ndata"] // nseg) * rows_k
+            e["tensor_tflops"] = flops / sec / 1e12
+            e["tensor_frac"] = e["tensor_tflops"] / bf16
+        out[k] = {kk: round(vv, 5) for kk, vv in e.items()}
+    return out
+
+
 def _timed_pairs(op, x, b, xa, steps, flush, stream):
     """Time `steps` A+A^T pairs (CUDA events per step, L2 flushed between steps); returns ms."""
     import torch
@@ -226,7 +275,8 @@ def serving_bench(n_requests, iters, seed=0):
 
     Requests follow the serving recipe (64^3 .. 256^2x128 volumes, 8-36 angles,
     harmonics 1..K, K in 8..16); data are b = A x + complex Gaussian noise (0.5 % of
-    max |b|) from seeded phantoms, computed on the GPU before the run. The sequential
+    max |b|) from seeded phantoms, computed on the GPU before the run. Each job runs 100
+    iterations or stops when its residual changes by at most 1e-3. The sequential
     plain-FP32 baseline solves one request at a time with the staged FP32 path; the
     arrival rate is 1.5x its measured throughput and its latencies follow from its
     measured per-request service times (single FIFO server). The batched server then
@@ -255,15 +305,17 @@ def serving_bench(n_requests, iters, seed=0):
         b += sig * torch.randn(b.shape, device="cuda", generator=gen)
         torch.cuda.synchronize()
         op.close()
-        reqs.append(Request(geometry=g, data=b, iters=iters, n_power=20, name=f"req{i}"))
+        reqs.append(Request(geometry=g, data=b, iters=iters, n_power=20, stop_rel=1e-3, name=f"req{i}"))
     # sequential plain FP32: measured service time per request (handle set-up + solve)
-    service = []
+    service, seq_x, seq_iters = [], {}, []
     for r in reqs:
         t0 = time.perf_counter()
         op = FFLOperator(**r.geometry)
-        op.solve(r.data, iters=r.iters, n_power=r.n_power, report=False)
+        xs_, rep = op.solve(r.data, iters=r.iters, n_power=r.n_power, stop_rel=r.stop_rel)
         torch.cuda.synchronize()
         service.append(time.perf_counter() - t0)
+        seq_x[r.name] = xs_.cpu()
+        seq_iters.append(rep["iters_done"])
         op.close()
     rate = 1.5 / (sum(service) / len(service))
     rng = np.random.default_rng(seed + 1)
@@ -278,20 +330,31 @@ def serving_bench(n_requests, iters, seed=0):
     for r, a in zip(reqs, arrivals):
         r.arrival = float(a)
     server = ReconServer(hbm_budget_bytes=150 * 2**30, path="full_gemm", max_active=64, poll_every=4,
-                         keep_results=False)
+                         keep_results=True)
     t0 = time.perf_counter()
     done = server.run(reqs)
     makespan = time.perf_counter() - t0
     lat = [r.latency for r in done]
+    # each batched result against the same request solved alone on the plain FP32 path
+    diffs = []
+    for r in done:
+        a_ = r.result.double().cpu()
+        b_ = seq_x[r.name].double()
+        diffs.append(float((a_ - b_).norm() / max(float(b_.norm()), 1e-300)))
+        r.result = None
     return {
         "requests": len(reqs), "iters_per_request": iters, "arrival_rate_per_s": rate,
         "batched": {"recons_per_s": len(done) / makespan, "p50_s": percentile(lat, 50), "p99_s": percentile(lat, 99),
                     "path": "full_gemm (bf16x3 tensor cores), continuous batching", "peak_hbm_bytes": server.peak_bytes,
-                    "batched_steps": server.steps},
+                    "batched_steps": server.steps,
+                    "iters_done_mean": float(np.mean([r.status["iters_done"] for r in done])),
+                    "max_rel_l2_vs_sequential": max(diffs), "median_rel_l2_vs_sequential": float(np.median(diffs))},
         "sequential_plain_fp32": {"recons_per_s": len(reqs) / seq_makespan, "p50_s": percentile(seq_lat, 50),
                                   "p99_s": percentile(seq_lat, 99),
+                                  "iters_done_mean": float(np.mean(seq_iters)),
                                   "note": "staged FP32 path, one request at a time; latencies from measured service "
                                           "times under the same arrivals"},
+        "stop_rule": "100 iterations, or earlier when the FP64 residual changes by <= 1e-3 between iterations",
         "hbm_budget_bytes": 150 * 2**30,
     }
 
@@ -430,25 +493,26 @@ def run_ours(args, cfg, rank, world, local_rank):
                   "peak_basis": f"{SMEM_BYTES_PER_CLK_SM} B/clk/SM x {n_sm} SMs x median SM clock {sm_mhz} MHz"}
     traffic = DRAM_TRAFFIC.get(top) if args.workload == "invivo" and path == "full_gemm" else None
     kernel_share = {k: round(v[0] / max(ms, 1e-9), 4) for k, v in prof.items() if v[1] > 0}
+    kernel_roof = kernel_rooflines(prof, dict(dims, path=path), hbm, clk.summary().get("sm_mhz") or 2070.0)
     kernel_ms = {k: round(v[0] / v[1], 4) for k, v in prof.items() if v[1] > 0}
 
     # ---- the other evaluation paths of the same operator (same inputs, same timing rules)
     paths = {path: {"pairs_per_s": value, "ms_per_pair": ms / args.steps}}
     if not args.quick:
-        for p in ("staged", "fused", "line_gemm", "full_gemm"):
-            if p in paths:
+        for key in ("staged", "fused", "line_gemm", "full_gemm", "line_gemm_tf32", "full_gemm_tf32"):
+            if key in paths:
                 continue
             try:
-                op.set_path(p)
+                use_path(op, key)
             except Exception as exc:  # shape not taken by that path
-                paths[p] = {"unsupported": str(exc)}
+                paths[key] = {"unsupported": str(exc)}
                 continue
             for _ in range(2):
                 step()
             pm = _timed_pairs(op, x, b, xa, max(3, args.steps // 2), flush, stream)
             n = max(3, args.steps // 2)
-            paths[p] = {"pairs_per_s": n / (pm / 1e3), "ms_per_pair": pm / n}
-        op.set_path(path)
+            paths[key] = {"pairs_per_s": n / (pm / 1e3), "ms_per_pair": pm / n}
+        use_path(op, path)
     plain = paths.get("staged", {}).get("pairs_per_s")
 
     result = {
@@ -465,6 +529,7 @@ def run_ours(args, cfg, rank, world, local_rank):
                      "algorithmic_bytes_per_launch": algo, "avg_launch_ms": per_launch_ms, "onchip": onchip},
         "kernel_time_share": kernel_share,
         "kernel_ms_per_launch": kernel_ms,
+        "kernel_roofline": kernel_roof,
         "paths": paths,
         "speedup_vs_plain_fp32": (value / plain) if plain else None,
         "e2e": {"value": pairs / (e2e_ms / 1e3), "unit": "pairs/s", "h2d_bytes_per_step": 4 * sz.n_vox,
@@ -482,8 +547,11 @@ def run_ours(args, cfg, rank, world, local_rank):
         bd = op.forward(x).clone()
         rec = {}
         xs = {}
-        for p in ([path, "staged"] if path != "staged" else ["staged"]):
-            op.set_path(p)
+        runs = [path, "staged"] if path != "staged" else ["staged"]
+        if path in ("full_gemm", "line_gemm"):
+            runs.append(path + "_tf32")
+        for p in runs:
+            use_path(op, p)
             ata = op.power_norm(20, 1234)
             torch.cuda.synchronize()
             r0 = torch.cuda.Event(enable_timing=True)
@@ -494,12 +562,13 @@ def run_ours(args, cfg, rank, world, local_rank):
             torch.cuda.synchronize()
             xs[p] = xr
             rec[p] = {"s_per_recon": r0.elapsed_time(r1) / 1e3, "iters": args.recon_iters}
-        if len(xs) == 2:
-            a_, b_ = xs[path].double(), xs["staged"].double()
-            rec["rel_l2_between_paths"] = float((a_ - b_).norm() / b_.norm())
+        if "staged" in xs:
+            ref_x = xs["staged"].double()
+            rec["rel_l2_vs_staged_fp32"] = {p: float((xs[p].double() - ref_x).norm() / ref_x.norm())
+                                            for p in xs if p != "staged"}
         rec["note"] = "tau from a 20-step power iteration done before the timed solve"
         result["recon"] = rec
-        op.set_path(path)
+        use_path(op, path)
     if args.serving_requests > 0 and world == 1:
         result["serving"] = serving_bench(args.serving_requests, args.serving_iters)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -513,8 +582,10 @@ def run_ours(args, cfg, rank, world, local_rank):
 
 def cpu_baseline_leg(cfg, x_np, op, args):
     """The FP64 oracle timed on the host cores on a bounded sample (a subset of the
-    angles), plus the error of every GPU evaluation path against the oracle on that
-    same sample (one angle of A x and the matching one-angle A^T y)."""
+    angles), plus the error of every GPU evaluation path against the oracle on sampled
+    angles: theta = 0 (row-marched) and the first angle past 90 degrees (column-marched),
+    each with A x on the phantom and A^T y for random y on that angle alone; the worst
+    of the angles is reported. Per stage: the staged path's own intermediates."""
     import torch
 
     from oracle import Setup, operator
@@ -523,30 +594,53 @@ def cpu_baseline_leg(cfg, x_np, op, args):
     nang = max(1, min(cfg["n_angles"], args.oracle_angles))
     per, text = oracle_pair_seconds(cfg, xo, nang)
     st = Setup.from_config(cfg)
-    m = 0
-    fs = operator.forward_stages(xo, st, angles=np.array([m]))
-    ref_b = fs["data"][0]
+    M = st.n_angles
+    sample = sorted({0, min(M - 1, M // 2 + 1)})
     rng = np.random.default_rng(9)
-    y = rng.standard_normal(ref_b.shape) + 1j * rng.standard_normal(ref_b.shape)
-    ref_x = operator.adjoint_stages(y[None], st, angles=np.array([m]))["vol"]
-    y_full = np.zeros(st.data_shape, dtype=np.complex128)
-    y_full[m] = y
-    y_dev = torch.from_numpy(np.stack([y_full.real, y_full.imag], -1).astype(np.float32)).cuda()
+    refs = {}
+    for m in sample:
+        fs = operator.forward_stages(xo, st, angles=np.array([m]))
+        y = rng.standard_normal(fs["data"][0].shape) + 1j * rng.standard_normal(fs["data"][0].shape)
+        y_full = np.zeros(st.data_shape, dtype=np.complex128)
+        y_full[m] = y
+        refs[m] = dict(stages=fs, ref_b=fs["data"][0],
+                       ref_x=operator.adjoint_stages(y[None], st, angles=np.array([m]))["vol"],
+                       y_dev=torch.from_numpy(np.stack([y_full.real, y_full.imag], -1).astype(np.float32)).cuda())
     x_dev = torch.from_numpy(x_np).cuda()
     errs = {}
-    for p in ("staged", "fused", "line_gemm", "full_gemm"):
+    for key in ("staged", "fused", "line_gemm", "full_gemm", "line_gemm_tf32", "full_gemm_tf32"):
         try:
-            op.set_path(p)
+            use_path(op, key)
         except Exception:
             continue
-        bb = op.forward(x_dev)[m].cpu().numpy().astype(np.float64)
-        xx = op.adjoint(y_dev).cpu().numpy().astype(np.float64)
-        got_b = bb[..., 0] + 1j * bb[..., 1]
-        errs[p] = {"forward_rel_l2": float(np.linalg.norm(got_b - ref_b) / np.linalg.norm(ref_b)),
-                   "adjoint_rel_l2": float(np.linalg.norm(xx - ref_x) / np.linalg.norm(ref_x))}
+        b_all = op.forward(x_dev).cpu().numpy().astype(np.float64)
+        ef, ea = 0.0, 0.0
+        for m, r in refs.items():
+            got_b = b_all[m, ..., 0] + 1j * b_all[m, ..., 1]
+            xx = op.adjoint(r["y_dev"]).cpu().numpy().astype(np.float64)
+            ef = max(ef, float(np.linalg.norm(got_b - r["ref_b"]) / np.linalg.norm(r["ref_b"])))
+            ea = max(ea, float(np.linalg.norm(xx - r["ref_x"]) / np.linalg.norm(r["ref_x"])))
+        errs[key] = {"forward_rel_l2": ef, "adjoint_rel_l2": ea}
+    # per stage: the staged FP32 path's own intermediates against the oracle's
+    op.set_path("staged")
+    stages = {}
+    cur = x_dev
+    for k, name in enumerate(("proj", "fine", "sig", "data")):
+        cur = op.apply_stage(k, cur)
+        worst = 0.0
+        for m, r in refs.items():
+            got = cur[m].cpu().numpy().astype(np.float64)
+            ref = r["stages"][name][0]
+            if name == "data":
+                got = got[..., 0] + 1j * got[..., 1]
+            worst = max(worst, float(np.linalg.norm(got - ref) / np.linalg.norm(ref)))
+        stages[name] = worst
+    del cur
     return {"value": 1.0 / per, "unit": "pairs/s", "cores": cores(), "kind": "oracle", "sample": text,
             "gpu_error_vs_oracle": errs,
-            "error_sample": f"angle {m}: A x on the phantom, A^T y for random y on that angle"}
+            "staged_error_per_stage": stages,
+            "error_sample": f"angles {sample}: A x on the phantom and A^T y for random y on each angle alone, "
+                            "worst angle; per stage: P, H, E V B, S D F of the staged path chained from x"}
 
 
 def main():

@@ -231,14 +231,18 @@ int compute_dims(const mpi_ffl_geometry *g, const mpi_ffl_trajectory *t, const m
 void angle_table(mpi_ffl_handle *h) {
     const Dims &d = h->d;
     std::vector<AngleParam> a(d.M);
+    const double ctr = 0.5 * (d.N - 1);
+    auto fx = [](double v) { return (long long)std::llround(std::ldexp(v, 32)); };
     for (int m = 0; m < d.M; ++m) {
         const double th = h->angles[m];
         const double c = std::cos(th), s = std::sin(th);
-        if (std::fabs(c) >= std::fabs(s) - 1e-9) {
-            a[m] = AngleParam{(float)(1.0 / c), (float)(s / c), (float)(1.0 / std::fabs(c)), 1, (float)c};
-        } else {
-            a[m] = AngleParam{(float)(-1.0 / s), (float)(c / s), (float)(1.0 / std::fabs(s)), 0, (float)(-s)};
-        }
+        const bool rows = std::fabs(c) >= std::fabs(s) - 1e-9;
+        const double inv_c = rows ? 1.0 / c : -1.0 / s;
+        const double slope = rows ? s / c : c / s;
+        const double scale = rows ? 1.0 / std::fabs(c) : 1.0 / std::fabs(s);
+        // f_i(s) = ctr + inv_c (i - ctr) + slope (s - ctr) = f_0(0) + inv_c i + slope s
+        a[m] = AngleParam{(float)inv_c, (float)slope, (float)scale, rows ? 1 : 0, (float)(rows ? c : -s), 0,
+                          fx(ctr - inv_c * ctr - slope * ctr), fx(inv_c), fx(slope)};
     }
     upload(h, &h->t_ang, a);
     // projector blocks hold kProjAnglesPerBlock angles of one orientation

@@ -10,6 +10,14 @@
 
 namespace mpiffl {
 
+// Cell and fraction of a Q32.32 position: floor and f - floor, the fraction rounded
+// to FP32 (it may round up to 1.0f, which weights the next cell fully in both the
+// projector and its transpose).
+__device__ __forceinline__ void fx_split(long long f, int &k, float &t) {
+    k = (int)(f >> 32);
+    t = __uint2float_rn((unsigned)(f & 0xffffffffll)) * 0x1p-32f;
+}
+
 __device__ __forceinline__ void transpose_body(const float *__restrict__ vol, float *__restrict__ volT, int N,
                                                int bx, int by, int bz) {
     __shared__ float tile[32][33];
@@ -96,8 +104,7 @@ __global__ void __launch_bounds__(1024) k_project(const float *__restrict__ vol,
     const bool active = (m >= 0) && (i < N);
     const AngleParam ap = ang[m >= 0 ? m : agroups[blockIdx.x * kProjAnglesPerBlock]];
     const float *src = ap.row_major ? vol : volT;  // one orientation per block
-    const float c = 0.5f * (float)(N - 1);
-    const float fi = fmaf(ap.inv_c, (float)i - c, c);
+    const long long f0 = ap.fx_a + (long long)i * ap.fx_d;
     const int nld = kZc * N;
     float acc[kZc];
 #pragma unroll
@@ -125,10 +132,9 @@ __global__ void __launch_bounds__(1024) k_project(const float *__restrict__ vol,
         const float *cur = sm + (s & 1) * nld;
         if (s + 1 < N) fetch(s + 1);
         if (active) {
-            const float f = fmaf(ap.slope, (float)s - c, fi);
-            const float fl = floorf(f);
-            const int k = (int)fl;
-            const float t = f - fl;
+            int k;
+            float t;
+            fx_split(f0 + (long long)s * ap.fx_b, k, t);
             const float w0 = (k >= 0 && k < N) ? 1.f - t : 0.f;
             const float w1 = (k + 1 >= 0 && k + 1 < N) ? t : 0.f;
             const int k0 = min(max(k, 0), N - 1);
@@ -217,22 +223,21 @@ __device__ __forceinline__ void project_pipe_body(const float *__restrict__ vol,
     const int m = agroups[bx * kProjAnglesPerBlock + slot];
     const bool active = (m >= 0) && (i < N);
     const AngleParam ap = ang[m >= 0 ? m : agroups[bx * kProjAnglesPerBlock]];
-    const float c = 0.5f * (float)(N - 1);
-    const float fi = fmaf(ap.inv_c, (float)i - c, c);
+    long long fs = ap.fx_a + (long long)i * ap.fx_d;  // position of ray i at march step s
     float acc[kZc];
 #pragma unroll
     for (int zz = 0; zz < kZc; ++zz) acc[zz] = 0.f;
     bool good = true;
-    for (int s = 0; s < N; ++s) {
+    for (int s = 0; s < N; ++s, fs += ap.fx_b) {
         const int k = s % kPStages;
         if (!ptx::mbar_wait_bounded(&bars[k], (s / kPStages) & 1, 1u << 24)) {
             good = false;
             break;
         }
-        const float f = fmaf(ap.slope, (float)s - c, fi);
-        const float fl = floorf(f);
-        const float t = f - fl;
-        const int kk = min(max((int)fl, -2), N);
+        int cell;
+        float t;
+        fx_split(fs, cell, t);
+        const int kk = min(max(cell, -2), N);
         const float *p = psm + k * kZc * LD + kPad + kk;
 #pragma unroll
         for (int zz = 0; zz < kZc; ++zz) acc[zz] = fmaf(1.f - t, p[zz * LD], fmaf(t, p[zz * LD + 1], acc[zz]));
@@ -344,7 +349,7 @@ __device__ __forceinline__ void backproject_body(const float *__restrict__ proj,
     const int xlo = bx * kBpTX, xhi = min(xlo + kBpTX, N) - 1;
     const int ylo = by * kBpTY, yhi = min(ylo + kBpTY, N) - 1;
     // threads past the grid edge follow the loop on the edge voxel and store nothing
-    const float fx = (float)min(x, N - 1), fy = (float)min(y, N - 1);
+    const int ix = min(x, N - 1), iy = min(y, N - 1);
     float acc[kBpZ];
 #pragma unroll
     for (int zz = 0; zz < kBpZ; ++zz) acc[zz] = 0.f;
@@ -373,17 +378,22 @@ __device__ __forceinline__ void backproject_body(const float *__restrict__ proj,
         __syncthreads();
         for (int a = 0; a < na; ++a) {
             const AngleParam A = S.ang[a];
-            const float sm = (A.row_major ? fy : fx) - c;  // march step holding this voxel, centred
-            const float q = A.row_major ? fx : fy;          // its index along the step's line
-            // nearest ray: inv_c (i - c) + slope (s - c) + c = q
-            const int i1 = __float2int_rn(fmaf(q - fmaf(A.slope, sm, c), A.inv_c_rcp, c));
-            const float d1 = (float)i1 - c;  // exact, as are d1 - 1 and d1 + 1
-            const float f0 = fmaf(A.slope, sm, fmaf(A.inv_c, d1 - 1.f, c));  // the forward's f
-            const float f1 = fmaf(A.slope, sm, fmaf(A.inv_c, d1, c));
-            const float f2 = fmaf(A.slope, sm, fmaf(A.inv_c, d1 + 1.f, c));
-            const float w0 = fmaxf(0.f, 1.f - fabsf(f0 - q));
-            const float w1 = fmaxf(0.f, 1.f - fabsf(f1 - q));
-            const float w2 = fmaxf(0.f, 1.f - fabsf(f2 - q));
+            const int s = A.row_major ? iy : ix;  // march step holding this voxel
+            const int q = A.row_major ? ix : iy;  // its index along the step's line
+            // nearest ray (estimate): inv_c (i - c) + slope (s - c) + c = q
+            const int i1 = __float2int_rn(fmaf((float)q - fmaf(A.slope, (float)s - c, c), A.inv_c_rcp, c));
+            // the forward's fixed-point positions of rays i1-1, i1, i1+1 at step s, and
+            // the weights it gives cell q: 1 - t from a ray in cell q, t from one in q-1
+            long long g = A.fx_a + (long long)s * A.fx_b + (long long)(i1 - 1) * A.fx_d;
+            float w[3];
+#pragma unroll
+            for (int u = 0; u < 3; ++u, g += A.fx_d) {
+                int k;
+                float t;
+                fx_split(g, k, t);
+                w[u] = k == q ? 1.f - t : (k == q - 1 ? t : 0.f);
+            }
+            const float w0 = w[0], w1 = w[1], w2 = w[2];
             // two consecutive rays carry the weight: (i1-1, i1) or (i1, i1+1)
             const bool lo = w0 != 0.f;
             const float wA = lo ? w0 : w1, wB = lo ? w1 : w2;
