@@ -182,8 +182,8 @@ ALGO_BYTES = {
     "tc_adj": lambda d: 4 * (d["nfine"] + d["ndata"]),
     "transpose": lambda d: 8 * d["nvox"],
     # the full-GEMM path applies W H to projections, the line-GEMM path W to fine rows
-    "gemm_fwd": lambda d: 4 * ((d["nproj"] if d["path"] == "full_gemm" else d["nfine"]) + d["ndata"]),
-    "gemm_adj": lambda d: 4 * ((d["nproj"] if d["path"] == "full_gemm" else d["nfine"]) + d["ndata"]),
+    "gemm_fwd": lambda d: 4 * ((d["nproj"] if d["path"].startswith("full_gemm") else d["nfine"]) + d["ndata"]),
+    "gemm_adj": lambda d: 4 * ((d["nproj"] if d["path"].startswith("full_gemm") else d["nfine"]) + d["ndata"]),
 }
 
 # Shared-memory bytes the projector pair reads per launch: two interpolation taps of
@@ -228,8 +228,8 @@ def bf16_peak_tflops():
 def kernel_rooflines(prof, d, hbm, sm_mhz):
     """Per kernel kind of the timed region: achieved algorithmic HBM GB/s against the
     measured copy peak; for the projector pair also the shared-memory roofline; for the
-    GEMMs the tensor rate (3 bf16 products of 2 M N K flops) against the measured bf16
-    peak."""
+    GEMMs the tensor rate (3 products of 2 M N K flops) against the peak of the operand
+    type (measured bf16; tf32 from it by the nominal ratio)."""
     import torch
 
     n_sm = torch.cuda.get_device_properties(0).multi_processor_count
@@ -237,7 +237,9 @@ def kernel_rooflines(prof, d, hbm, sm_mhz):
     bf16, _ = bf16_peak_tflops()
     nz = d["nvox"] // (d["N"] * d["N"])
     nseg = d["M"] * nz
-    rows_k = d["N"] if d["path"] == "full_gemm" else d["nfine"] // nseg
+    rows_k = d["N"] if d["path"].startswith("full_gemm") else d["nfine"] // nseg
+    # tf32 operands: the measured bf16 peak times the nominal tf32/bf16 ratio (1.1 / 2.25 PFLOP/s)
+    tensor_peak = bf16 * (1.1 / 2.25) if d["path"].endswith("_tf32") else bf16
     out = {}
     for k, (t_ms, n) in prof.items():
         if n <= 0 or k not in ALGO_BYTES:
@@ -249,7 +251,7 @@ def kernel_rooflines(prof, d, hbm, sm_mhz):
         if k in ("gemm_fwd", "gemm_adj"):
             flops = 3 * 2 * nseg * (d["ndata"] // nseg) * rows_k
             e["tensor_tflops"] = flops / sec / 1e12
-            e["tensor_frac"] = e["tensor_tflops"] / bf16
+            e["tensor_frac"] = e["tensor_tflops"] / tensor_peak
         out[k] = {kk: round(vv, 5) for kk, vv in e.items()}
     return out
 
@@ -345,7 +347,7 @@ def serving_bench(n_requests, iters, seed=0):
     return {
         "requests": len(reqs), "iters_per_request": iters, "arrival_rate_per_s": rate,
         "batched": {"recons_per_s": len(done) / makespan, "p50_s": percentile(lat, 50), "p99_s": percentile(lat, 99),
-                    "path": "full_gemm (bf16x3 tensor cores), continuous batching", "peak_hbm_bytes": server.peak_bytes,
+                    "path": "full_gemm (bf16 hi+lo tensor cores), continuous batching", "peak_hbm_bytes": server.peak_bytes,
                     "batched_steps": server.steps,
                     "iters_done_mean": float(np.mean([r.status["iters_done"] for r in done])),
                     "max_rel_l2_vs_sequential": max(diffs), "median_rel_l2_vs_sequential": float(np.median(diffs))},
@@ -370,9 +372,11 @@ def run_ours(args, cfg, rank, world, local_rank):
         import torch.distributed as dist
 
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    # headline: the full-GEMM path with bf16 hi+lo operands (tf32 hi+lo is reported
+    # beside it under "paths")
     path = args.path or ("staged" if args.plain else "full_gemm")
     op = FFLOperator.from_config(cfg)
-    op.set_path(path)
+    use_path(op, path)
     sz = op.sizes
     dims = dict(nvox=sz.n_vox, nproj=sz.n_proj, nfine=sz.n_fine, nsig=sz.n_sig, ndata=sz.n_data, M=op.n_angles,
                 N=op.nx)
@@ -396,8 +400,6 @@ def run_ours(args, cfg, rank, world, local_rank):
     # ---- timed region: K steps, L2 flushed between steps (outside the events)
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    op.profile(True)
-    op.profile_read()
     launches0 = op.launch_count()
     with ClockSampler(local_rank) as clk:
         t_wall0 = time.perf_counter()
@@ -408,10 +410,22 @@ def run_ours(args, cfg, rank, world, local_rank):
             ends[k].record(stream)
         torch.cuda.synchronize()
         t_wall = time.perf_counter() - t_wall0
-    launches = op.launch_count() - launches0
-    prof = op.profile_read()
-    op.profile(False)
-    ms = sum(s_.elapsed_time(e) for s_, e in zip(starts, ends))
+        launches = op.launch_count() - launches0
+        ms = sum(s_.elapsed_time(e) for s_, e in zip(starts, ends))
+        # the same K steps again with the library's CUDA events around every launch (on
+        # the launching stream): per-kernel durations for the shares and the rooflines.
+        # The events cost a little time, so the headline comes from the pass above.
+        op.profile(True)
+        op.profile_read()
+        for k in range(args.steps):
+            flush.zero_()
+            starts[k].record(stream)
+            step()
+            ends[k].record(stream)
+        torch.cuda.synchronize()
+        prof = op.profile_read()
+        op.profile(False)
+        ms_prof = sum(s_.elapsed_time(e) for s_, e in zip(starts, ends))
     if dist:
         t = torch.tensor([ms], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -426,7 +440,7 @@ def run_ours(args, cfg, rank, world, local_rank):
     # other's kernels (the way a stream of volumes is fed); each handle also copies its
     # next input on its own stream.
     ops = [op, FFLOperator.from_config(cfg)]
-    ops[1].set_path(path)
+    use_path(ops[1], path)
     streams = [stream, torch.cuda.Stream()]
     bufs = [b, ops[1].new_data()]
     outs = [torch.empty(op.vol_shape, dtype=torch.float32).pin_memory() for _ in range(2)]
@@ -491,8 +505,8 @@ def run_ours(args, cfg, rank, world, local_rank):
         onchip = {"bound": "smem", "achieved": sm_ach, "peak": sm_peak, "unit": "GB/s", "frac": sm_ach / sm_peak,
                   "bytes_per_launch": sm_bytes,
                   "peak_basis": f"{SMEM_BYTES_PER_CLK_SM} B/clk/SM x {n_sm} SMs x median SM clock {sm_mhz} MHz"}
-    traffic = DRAM_TRAFFIC.get(top) if args.workload == "invivo" and path == "full_gemm" else None
-    kernel_share = {k: round(v[0] / max(ms, 1e-9), 4) for k, v in prof.items() if v[1] > 0}
+    traffic = DRAM_TRAFFIC.get(top) if args.workload == "invivo" and path.startswith("full_gemm") else None
+    kernel_share = {k: round(v[0] / max(ms_prof, 1e-9), 4) for k, v in prof.items() if v[1] > 0}
     kernel_roof = kernel_rooflines(prof, dict(dims, path=path), hbm, clk.summary().get("sm_mhz") or 2070.0)
     kernel_ms = {k: round(v[0] / v[1], 4) for k, v in prof.items() if v[1] > 0}
 
@@ -519,7 +533,9 @@ def run_ours(args, cfg, rank, world, local_rank):
         "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32" if path == "staged" else "f32 (line stage on tensor cores as bf16 hi+lo, 3 products, f32 acc)",
+        "dtype": ("f32" if path == "staged" else
+                  "f32 (line stage on tensor cores as %s hi+lo, 3 products, f32 acc)"
+                  % ("tf32" if path.endswith("_tf32") else "bf16")),
         "data": "synthetic",
         "config": {"workload": workload_desc(cfg), "path": path,
                    "l2": "flushed (256 MB write) between timed steps",
@@ -528,6 +544,7 @@ def run_ours(args, cfg, rank, world, local_rank):
                      "frac": achieved / hbm, "traffic": traffic, "peak_source": src,
                      "algorithmic_bytes_per_launch": algo, "avg_launch_ms": per_launch_ms, "onchip": onchip},
         "kernel_time_share": kernel_share,
+        "profiled_ms_per_step": ms_prof / args.steps,
         "kernel_ms_per_launch": kernel_ms,
         "kernel_roofline": kernel_roof,
         "paths": paths,
@@ -548,8 +565,10 @@ def run_ours(args, cfg, rank, world, local_rank):
         rec = {}
         xs = {}
         runs = [path, "staged"] if path != "staged" else ["staged"]
-        if path in ("full_gemm", "line_gemm"):
+        if path.endswith("gemm"):
             runs.append(path + "_tf32")
+        elif path.endswith("_tf32"):
+            runs.append(path[: -len("_tf32")])
         for p in runs:
             use_path(op, p)
             ata = op.power_norm(20, 1234)
@@ -649,7 +668,8 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--path", default=None, choices=["staged", "fused", "line_gemm", "full_gemm"])
+    ap.add_argument("--path", default=None,
+                    choices=["staged", "fused", "line_gemm", "full_gemm", "line_gemm_tf32", "full_gemm_tf32"])
     ap.add_argument("--workload", default="invivo", choices=["invivo", "phantom", "tiny"])
     ap.add_argument("--oracle-angles", type=int, default=1)
     ap.add_argument("--recon-iters", type=int, default=100)

@@ -62,7 +62,7 @@ class Job:
     own stream (handle tables, data copy, power iteration) so that preparing a new
     request overlaps the running batch."""
 
-    def __init__(self, req, path):
+    def __init__(self, req, path, precision=None):
         lib = _lib.load()
         _declare(lib)
         self.req = req
@@ -70,6 +70,8 @@ class Job:
         with torch.cuda.stream(self.prep_stream):
             self.op = FFLOperator(**req.geometry)
             self.op.set_path(path)
+            if precision is not None:
+                self.op.set_precision(precision)
             self.b = req.data.to(self.op.device, non_blocking=True).contiguous()
             p = _lib.SolveParams(int(req.iters), float(req.lam), float(req.tau), int(req.n_power), C.c_uint64(1234),
                                  1, float(req.stop_rel), 0.0)
@@ -125,8 +127,9 @@ class ReconServer:
     """
 
     def __init__(self, hbm_budget_bytes=150 * 2**30, path="full_gemm", max_active=64, poll_every=1,
-                 keep_results=True, prepare_workers=4):
+                 keep_results=True, prepare_workers=4, precision=None):
         self.prepare_workers = prepare_workers
+        self.precision = precision  # PREC_* for the jobs' handles, None = the path's default
         self.budget = int(hbm_budget_bytes)
         self.path = path
         self.max_active = max_active
@@ -153,7 +156,7 @@ class ReconServer:
 
         def prepare(req):
             torch.cuda.set_device(dev)
-            return Job(req, self.path)
+            return Job(req, self.path, self.precision)
 
         t0 = time.perf_counter()
         now = lambda: time.perf_counter() - t0  # noqa: E731

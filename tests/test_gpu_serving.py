@@ -68,9 +68,9 @@ def _result(lib, op, h):
     return x.cpu().numpy()
 
 
-@pytest.mark.parametrize("path", ["full_gemm", "line_gemm"])
+@pytest.mark.parametrize("path", ["full_gemm", "line_gemm", "full_gemm_tf32"])
 def test_jobs_alone_and_in_the_mix_agree(path):
-    from paper_2511_06627_gb300 import FFLOperator
+    from paper_2511_06627_gb300 import PREC_TF32, FFLOperator
 
     L, lib, _ = _job_api()
     iters = 30
@@ -78,7 +78,9 @@ def test_jobs_alone_and_in_the_mix_agree(path):
     for i, g in enumerate(GEOMS):
         st, x, b = _data(g, seed=60 + i)
         op = FFLOperator(**g)
-        op.set_path(path)
+        op.set_path(path.replace("_tf32", ""))
+        if path.endswith("_tf32"):
+            op.set_precision(PREC_TF32)
         ata = op.power_norm(40, 1234)
         lam = 1e-3 * ata / 10.0
         tau = 1.0 / (ata + lam * 12.0)
