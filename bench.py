@@ -142,6 +142,23 @@ def cores():
         return os.cpu_count()
 
 
+def over_ranks(values_ms, dist, device="cuda"):
+    """Each timing (ms) maximised over the ranks of the process group (the slowest rank
+    sets the job's time); unchanged without one."""
+    if dist is None:
+        return [float(v) for v in values_ms]
+    import torch
+
+    t = torch.tensor([float(v) for v in values_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def whole_job_rate(units_per_rank, world, max_ms):
+    """Units every rank processed, divided by the slowest rank's time (per second)."""
+    return units_per_rank * world / (max_ms / 1e3)
+
+
 def run_reference(args, cfg, rank):
     if rank != 0:
         return
@@ -426,13 +443,11 @@ def run_ours(args, cfg, rank, world, local_rank):
         prof = op.profile_read()
         op.profile(False)
         ms_prof = sum(s_.elapsed_time(e) for s_, e in zip(starts, ends))
+    (ms,) = over_ranks([ms], dist)
     if dist:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
     pairs = args.steps * world
-    value = pairs / (ms / 1e3)
+    value = whole_job_rate(args.steps, world, ms)
 
     # ---- end to end through the public API with host buffers: forward reads a pinned
     # host volume and adjoint writes a pinned host volume; the library stages both. Two
@@ -484,10 +499,7 @@ def run_ours(args, cfg, rank, world, local_rank):
         o.set_host_overlap(False)
     ops[1].close()
     e2e_ms = e0.elapsed_time(e1)
-    if dist:
-        t = torch.tensor([e2e_ms, e2e_serial_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms, e2e_serial_ms = float(t[0].item()), float(t[1].item())
+    e2e_ms, e2e_serial_ms = over_ranks([e2e_ms, e2e_serial_ms], dist)
 
     # ---- roofline of the dominant kernel (times measured inside the timed region)
     hbm, src = peaks()
