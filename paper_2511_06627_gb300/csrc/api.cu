@@ -1042,26 +1042,34 @@ extern "C" int mpi_ffl_solve(mpi_ffl_handle *h, const float *d_b, float *d_x, co
             dev_alloc(h, &h->s_hist, (size_t)p->iters + 1);
             h->s_hist_len = p->iters + 1;
         }
-        int *flags = h->s_flags;  // [0] stop flag, [1] iterations done
+        int *flags = h->s_flags;  // [0] stop flag, [1] iterations done, [2] frozen
         CK(cudaMemsetAsync(flags, 0, 4 * sizeof(int), st));
+        // With a stop rule the host looks at the flags every kPoll iterations only;
+        // iterations after the stop are frozen on the device (momentum, residual and
+        // update do nothing, the update keeps the final iterate), so the result does
+        // not depend on when the host looks.
+        constexpr int kPoll = 4;
+        const int *frozen = p->stop_rel > 0.0 ? flags + 2 : nullptr;
         CK(cudaMemcpyAsync(h->s_xp, d_x, sizeof(float) * d.nvox, cudaMemcpyDeviceToDevice, st));
         float *xc = d_x, *xp = h->s_xp;
         const int nbd = reduce_blocks(d.ndata);
         int done_host = 0, k_run = 0;
         for (int k = 1; k <= p->iters; ++k) {
             const double beta = (k - 1.0) / (k + 2.0);
-            TIMED(MPI_FFL_K_SOLVER, launch_momentum(xc, xp, h->s_y, beta, k, d.nvox, nullptr, st));
+            TIMED(MPI_FFL_K_SOLVER, launch_momentum(xc, xp, h->s_y, beta, k, d.nvox, frozen, st));
             forward_impl(h, h->s_y, h->s_r, h->t_htab, h->t_gain, st);
-            TIMED(MPI_FFL_K_SOLVER, launch_sub_norm(h->s_r, d_b, d.ndata, h->w_red, nbd, nullptr, st));
+            TIMED(MPI_FFL_K_SOLVER, launch_sub_norm(h->s_r, d_b, d.ndata, h->w_red, nbd, frozen, st));
             TIMED(MPI_FFL_K_SOLVER, launch_finalize(h->w_red, nbd, h->s_hist + (k - 1), st));
             TIMED(MPI_FFL_K_SOLVER, launch_stop_check(h->s_hist, k - 1, p->stop_rel, flags, flags + 1, st));
             adjoint_impl(h, h->s_r, h->s_g, st);
-            TIMED(MPI_FFL_K_SOLVER, launch_update(h->s_y, h->s_g, xp, (float)tau, (float)lam, p->nonneg ? 1 : 0, d.N, d.Nz, nullptr, st));
+            TIMED(MPI_FFL_K_SOLVER, launch_update(h->s_y, h->s_g, xp, (float)tau, (float)lam, p->nonneg ? 1 : 0,
+                                                  d.N, d.Nz, frozen, st, xc));
+            if (frozen) TIMED(MPI_FFL_K_SOLVER, launch_freeze(flags, flags + 2, st));
             check_launch(h, "solve iteration");
             std::swap(xc, xp);
             k_run = k;
-            if (p->stop_rel > 0.0) {
-                CK(cudaMemcpyAsync(&done_host, flags, sizeof(int), cudaMemcpyDeviceToHost, st));
+            if (frozen && (k % kPoll == 0 || k == p->iters)) {
+                CK(cudaMemcpyAsync(&done_host, flags + 2, sizeof(int), cudaMemcpyDeviceToHost, st));
                 CK(cudaStreamSynchronize(st));
                 if (done_host) break;
             }
@@ -1070,6 +1078,8 @@ extern "C" int mpi_ffl_solve(mpi_ffl_handle *h, const float *d_b, float *d_x, co
         if (rep || p->stop_rel > 0.0) {
             int fl[2] = {0, 0};
             CK(cudaMemcpyAsync(fl, flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            k_run = fl[1];  // iterations whose update ran (frozen ones excluded)
             double first = 0, last = 0;
             if (k_run > 0) {
                 CK(cudaMemcpyAsync(&first, h->s_hist, sizeof(double), cudaMemcpyDeviceToHost, st));

@@ -251,7 +251,8 @@ void launch_sub_norm(float *r, const float *b, int64_t n, double *partials, int 
 void launch_dot(const float *a, const float *b, int64_t n, double *partials, int nblk, cudaStream_t st);
 void launch_finalize(const double *partials, int nblk, double *out, cudaStream_t st);
 void launch_update(const float *y, const float *g, float *xout, float tau, float lam, int nonneg,
-                   int N, int Nz, const int *done, cudaStream_t st);
+                   int N, int Nz, const int *done, cudaStream_t st, const float *xcur = nullptr);
+void launch_freeze(const int *stop, int *frozen, cudaStream_t st);
 void launch_ttt(const float *x, float *out, int N, int Nz, cudaStream_t st);
 void launch_splitmix_fill(float *v, int64_t n, uint64_t seed, cudaStream_t st);
 void launch_scale_by_rsqrt(const float *in, float *out, int64_t n, const double *n2, cudaStream_t st);

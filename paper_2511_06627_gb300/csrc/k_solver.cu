@@ -159,14 +159,20 @@ void launch_ttt(const float *x, float *out, int N, int Nz, cudaStream_t st) {
     k_ttt<<<grid, 128, 0, st>>>(x, out, N, Nz);
 }
 
-// x_out = P(y - tau (g + lam T^T T y)), P = max(0, .) when nonneg
+// x_out = P(y - tau (g + lam T^T T y)), P = max(0, .) when nonneg. Once *done is set
+// the solve is frozen: x_out = xcur (the current iterate), so that the buffer swap of
+// the next iteration keeps the final iterate.
 __global__ void k_update(const float *__restrict__ y, const float *__restrict__ g, float *__restrict__ xo,
-                         float tau, float lam, int nonneg, int N, int Nz, const int *done) {
-    if (done && *done) return;
+                         float tau, float lam, int nonneg, int N, int Nz, const int *done,
+                         const float *__restrict__ xcur) {
     const int xx = blockIdx.x * blockDim.x + threadIdx.x;
     const int yy = blockIdx.y, z = blockIdx.z;
     if (xx >= N) return;
     const size_t i = ((size_t)z * N + yy) * N + xx;
+    if (done && *done) {
+        if (xcur) xo[i] = xcur[i];
+        return;
+    }
     const float grad = fmaf(lam, ttt_at(y, N, Nz, z, yy, xx), g[i]);
     float v = fmaf(-tau, grad, y[i]);
     if (nonneg) v = fmaxf(v, 0.f);
@@ -174,10 +180,17 @@ __global__ void k_update(const float *__restrict__ y, const float *__restrict__ 
 }
 
 void launch_update(const float *y, const float *g, float *xout, float tau, float lam, int nonneg,
-                   int N, int Nz, const int *done, cudaStream_t st) {
+                   int N, int Nz, const int *done, cudaStream_t st, const float *xcur) {
     dim3 grid((N + 127) / 128, N, Nz);
-    k_update<<<grid, 128, 0, st>>>(y, g, xout, tau, lam, nonneg, N, Nz, done);
+    k_update<<<grid, 128, 0, st>>>(y, g, xout, tau, lam, nonneg, N, Nz, done, xcur);
 }
+
+// frozen = stop (after the update of the stopping iteration)
+__global__ void k_freeze(const int *stop, int *frozen) {
+    if (*stop) *frozen = 1;
+}
+
+void launch_freeze(const int *stop, int *frozen, cudaStream_t st) { k_freeze<<<1, 1, 0, st>>>(stop, frozen); }
 
 // SplitMix64 (Steele, Lea, Flood 2014) evaluated at counter i + 1: u in [-1, 1).
 __global__ void k_splitmix_fill(float *v, int64_t n, uint64_t seed) {
