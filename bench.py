@@ -217,8 +217,8 @@ SMEM_BYTES_PER_CLK_SM = 128
 # profiles/full_gemm_invivo_kernels.md (cold caches, 256^2x128, 36 angles). Reported
 # only for that workload and only while the kernel is the one that was captured.
 DRAM_TRAFFIC = {
-    "project": 67_124_992 + 1_128_704,   # reads the volume and its transposed copy
-    "backproject": 4_734_464 + 0,        # reads the projections; the volume it writes stays in L2
+    "project": 67_126_016 + 1_203_456,   # reads the volume and its transposed copy
+    "backproject": 4_736_000 + 512,      # reads the projections; the volume it writes stays in L2
 }
 
 
