@@ -615,6 +615,21 @@ def run_ours(args, cfg, rank, world, local_rank):
         rec["note"] = "tau from a 20-step power iteration done before the timed solve"
         result["recon"] = rec
         use_path(op, path)
+    if not args.quick:
+        # compression analysis (Appendix A, Eq. (30)) on the phantom's time signal
+        Ks = [k for k in (1, 2, 4, 8, 16) if op.k_min <= k <= op.k_max]
+        ws = [w for w in (0, 1, 2, 4) if w <= op.half_width]
+        c0 = torch.cuda.Event(enable_timing=True)
+        c1 = torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        table = op.information_retained(x, Ks, ws)
+        c1.record(stream)
+        torch.cuda.synchronize()
+        result["compression_analysis"] = {
+            "information_retained": {f"K={K}": {f"w={w}": round(float(table[a, c]), 6) for c, w in enumerate(ws)}
+                                     for a, K in enumerate(Ks)},
+            "ms": c0.elapsed_time(c1),
+            "note": "I(s, S) of Eq. (30) over all segments, harmonics 1..K, |delta| <= w, each bin with its conjugate"}
     if args.serving_requests > 0 and world == 1:
         result["serving"] = serving_bench(args.serving_requests, args.serving_iters)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

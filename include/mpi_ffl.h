@@ -246,6 +246,18 @@ int mpi_ffl_param_grad_proj(mpi_ffl_handle *h, const float *d_proj, const float 
 int mpi_ffl_line_forward(mpi_ffl_handle *h, const float *d_proj, float *d_b_ri, void *stream);
 int mpi_ffl_line_adjoint(mpi_ffl_handle *h, const float *d_b_ri, float *d_proj, void *stream);
 
+/* Compression analysis (Appendix A, Eq. (30)). With s = E V B H P x the time signal
+ * of every segment (staged FP32 kernels), writes on the device, in FP64:
+ *   d_bin_energy[q] = sum over segments of |s_hat_w|^2, w = kP + delta the q-th kept
+ *                     bin (data order: k ascending, then delta ascending), s_hat the
+ *                     unitary DFT of Sec. 2.1 without D_Gamma (n_bins doubles);
+ *   d_total[0]      = sum over segments of ||s||^2.
+ * For a real signal the bin L - w carries the same energy as w, so the information a
+ * sub-band S' of the kept bins retains, counting each bin with its conjugate, is
+ * I = sqrt(2 sum_{q in S'} d_bin_energy[q] / d_total[0]). Uses the time-signal
+ * workspace (n_sig floats, allocated on first use). */
+int mpi_ffl_band_energy(mpi_ffl_handle *h, const float *d_x, double *d_bin_energy, double *d_total, void *stream);
+
 /* T^T T x (Sec. 3.3, Eq. (25)) on a volume. */
 int mpi_ffl_apply_ttt(mpi_ffl_handle *h, const float *d_x, float *d_out, void *stream);
 

@@ -90,6 +90,7 @@ PROTOTYPES = {
     "mpi_ffl_get_path": (C.c_int, [H]),
     "mpi_ffl_get_precision": (C.c_int, [H]),
     "mpi_ffl_set_host_overlap": (C.c_int, [H, C.c_int32]),
+    "mpi_ffl_band_energy": (C.c_int, [H, FP, FP, FP, FP]),
     "mpi_ffl_set_gain": (C.c_int, [H, C.POINTER(C.c_float)]),
     "mpi_ffl_set_psf_fwhm": (C.c_int, [H, C.c_double]),
     "mpi_ffl_sync_check": (C.c_int, [H, ST]),

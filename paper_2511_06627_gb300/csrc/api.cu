@@ -355,7 +355,7 @@ void group_table(mpi_ffl_handle *h) {
 
 void release(mpi_ffl_handle *h) {
     void *ptrs[] = {h->t_ang, h->t_gain, h->t_unit_gain, h->t_htab, h->t_dhtab, h->t_traj, h->t_csr_ptr,
-                    h->t_csr, h->t_tw1, h->t_tw2_ro, h->t_tw2_qr, h->t_dgam, h->t_groups, h->w_volT,
+                    h->t_csr, h->t_tw1, h->t_tw2_ro, h->t_tw2_qr, h->t_dgam, h->t_dgam_unit, h->t_groups, h->w_volT,
                     h->w_proj, h->w_fine, h->w_sig, h->w_data, h->w_vol2, h->w_red, h->w_scal,
                     h->s_xp, h->s_y, h->s_g, h->s_r, h->s_hist, h->s_flags, h->tc_twb, h->t_agroups,
                     h->t_tnf, h->t_vr, h->w_err};
@@ -992,6 +992,32 @@ extern "C" int mpi_ffl_dot_f64(mpi_ffl_handle *h, const float *d_a, const float 
         TIMED(MPI_FFL_K_SOLVER, launch_dot(d_a, d_b, n, h->w_red, nb, st));
         TIMED(MPI_FFL_K_SOLVER, launch_finalize(h->w_red, nb, d_out, st));
         check_launch(h, "dot");
+        return MPI_FFL_OK;
+    });
+}
+
+extern "C" int mpi_ffl_band_energy(mpi_ffl_handle *h, const float *d_x, double *d_bin_energy, double *d_total,
+                                   void *stream) {
+    return guarded(h, [&]() {
+        if (!d_x || !d_bin_energy || !d_total) {
+            h->err = "NULL buffer";
+            return MPI_FFL_ERR_INVALID_ARG;
+        }
+        const Dims &d = h->d;
+        cudaStream_t st = S(stream);
+        ensure_sig(h);
+        if (!h->t_dgam_unit) upload(h, &h->t_dgam_unit, std::vector<float2>(d.nb, make_float2(1.f, 0.f)));
+        // s = E V B H P x on the staged kernels (FP32), then its energy and its kept bins
+        stage_p(h, d_x, h->w_proj, st);
+        TIMED(MPI_FFL_K_PSF_FWD, launch_psf_fwd(h->w_proj, h->t_htab, h->w_fine, d, st));
+        TIMED(MPI_FFL_K_RESAMPLE_FWD, launch_resample_fwd(h->w_fine, h->t_traj, h->t_gain, h->t_groups, h->n_groups,
+                                                          h->w_sig, d, st));
+        const int nbr = reduce_blocks(d.nsig);
+        TIMED(MPI_FFL_K_SOLVER, launch_dot(h->w_sig, h->w_sig, d.nsig, h->w_red, nbr, st));
+        TIMED(MPI_FFL_K_SOLVER, launch_finalize(h->w_red, nbr, d_total, st));
+        TIMED(MPI_FFL_K_DFT_FWD, launch_dft_fwd(h->w_sig, h->t_tw1, h->t_tw2_ro, h->t_dgam_unit, h->w_data, d, st));
+        TIMED(MPI_FFL_K_SOLVER, launch_bin_energy(h->w_data, d.nseg, d.nb, d_bin_energy, st));
+        check_launch(h, "band energy");
         return MPI_FFL_OK;
     });
 }

@@ -97,6 +97,7 @@ struct mpi_ffl_handle {
     float2 *t_tw2_ro = nullptr;           // [r][q]: exp(+2 pi i w_q r / L)
     float2 *t_tw2_qr = nullptr;           // [q][r]
     float2 *t_dgam = nullptr;             // nb
+    float2 *t_dgam_unit = nullptr;        // nb ones (the bare DFT, for the compression analysis)
     mpiffl::SegGroup *t_groups = nullptr;
     int n_groups = 0;
     int *t_agroups = nullptr;  // projector angle groups: kProjAnglesPerBlock indices, -1 = empty
@@ -253,6 +254,7 @@ void launch_finalize(const double *partials, int nblk, double *out, cudaStream_t
 void launch_update(const float *y, const float *g, float *xout, float tau, float lam, int nonneg,
                    int N, int Nz, const int *done, cudaStream_t st, const float *xcur = nullptr);
 void launch_freeze(const int *stop, int *frozen, cudaStream_t st);
+void launch_bin_energy(const float *data, int nseg, int nb, double *out, cudaStream_t st);
 void launch_ttt(const float *x, float *out, int N, int Nz, cudaStream_t st);
 void launch_splitmix_fill(float *v, int64_t n, uint64_t seed, cudaStream_t st);
 void launch_scale_by_rsqrt(const float *in, float *out, int64_t n, const double *n2, cudaStream_t st);

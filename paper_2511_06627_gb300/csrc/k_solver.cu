@@ -185,6 +185,22 @@ void launch_update(const float *y, const float *g, float *xout, float tau, float
     k_update<<<grid, 128, 0, st>>>(y, g, xout, tau, lam, nonneg, N, Nz, done, xcur);
 }
 
+// Per kept bin q: sum over segments of |b[seg][q]|^2 in FP64, segments in order.
+__global__ void k_bin_energy(const float2 *__restrict__ data, int nseg, int nb, double *__restrict__ out) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nb) return;
+    double acc = 0.0;
+    for (int sgi = 0; sgi < nseg; ++sgi) {
+        const float2 v = data[(size_t)sgi * nb + q];
+        acc = fma((double)v.x, (double)v.x, fma((double)v.y, (double)v.y, acc));
+    }
+    out[q] = acc;
+}
+
+void launch_bin_energy(const float *data, int nseg, int nb, double *out, cudaStream_t st) {
+    k_bin_energy<<<(nb + 127) / 128, 128, 0, st>>>(reinterpret_cast<const float2 *>(data), nseg, nb, out);
+}
+
 // frozen = stop (after the update of the stopping iteration)
 __global__ void k_freeze(const int *stop, int *frozen) {
     if (*stop) *frozen = 1;

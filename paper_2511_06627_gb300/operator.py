@@ -68,6 +68,7 @@ class FFLOperator:
         self.L = sz.line_len
         self.fine_len = sz.fine_len
         self.S, self.P, self.Q = S, P, Q
+        self.k_min, self.k_max, self.half_width = k_min, k_max, half_width
         self.fwhm = fwhm
         self.params = dict(nx=nx, nz=nz, n_angles=n_angles, S=S, P=P, A=A, phi0=phi0, zigzag=zigzag,
                            Q=Q, fwhm=fwhm, k_min=k_min, k_max=k_max, half_width=half_width)
@@ -136,6 +137,34 @@ class FFLOperator:
         out = torch.empty(sout, device=self.device, dtype=torch.float32)
         check(self._lib.mpi_ffl_apply_stage(self._h, int(stage), int(bool(transpose)), _ptr(inp), _ptr(out),
                                             _stream()), self._h)
+        return out
+
+    def band_energy(self, x):
+        """Compression analysis (Appendix A, Eq. (30)): (per-kept-bin energy summed over
+        segments, total signal energy), FP64 numpy, for the time signal of x."""
+        self._check(x, self.vol_shape, "x")
+        e = torch.empty(self.n_bins, device=self.device, dtype=torch.float64)
+        tot = torch.empty((), device=self.device, dtype=torch.float64)
+        check(self._lib.mpi_ffl_band_energy(self._h, _ptr(x), _ptr(e), _ptr(tot), _stream()), self._h)
+        return e.cpu().numpy(), float(tot.item())
+
+    def information_retained(self, x, harmonics, half_widths):
+        """I(s, S) of Eq. (30) for the time signal of x, for every sub-band of the kept
+        bins with harmonics k_min..K (K in `harmonics`) and |delta| <= w (w in
+        `half_widths`), each bin counted with its conjugate L - omega. Returns a
+        [len(harmonics), len(half_widths)] numpy array."""
+        import numpy as np
+
+        e, tot = self.band_energy(x)
+        w_all = self.half_width
+        e = e.reshape(self.k_max - self.k_min + 1, 2 * w_all + 1)
+        out = np.zeros((len(harmonics), len(half_widths)))
+        for a, K in enumerate(harmonics):
+            for c, w in enumerate(half_widths):
+                if not (self.k_min <= K <= self.k_max and 0 <= w <= w_all):
+                    raise ValueError("sub-band outside the kept bins")
+                sub = e[: K - self.k_min + 1, w_all - w: w_all + w + 1].sum()
+                out[a, c] = math.sqrt(2.0 * sub / tot) if tot > 0 else 0.0
         return out
 
     def apply_ttt(self, x):

@@ -202,3 +202,31 @@ def test_host_buffers_equal_device_buffers(overlap, pinned):
     ref = op.adjoint(op.forward(torch.from_numpy(xs[0]).cuda()))
     torch.cuda.synchronize()
     assert np.array_equal(out_h.numpy(), ref.cpu().numpy())
+
+
+def test_compression_analysis_matches_the_oracle():
+    """I(s, S) of Eq. (30) from the GPU band energies, for every sub-band (harmonics
+    1..K, |delta| <= w) of the kept bins, against the oracle's literal Eq. (30) on the
+    symmetric bin set S u (L - S) of its FP64 time signal."""
+    from paper_2511_06627_gb300 import FFLOperator
+
+    cfg = config("tiny")
+    kw = {k: cfg[k] for k in ("nx", "nz", "n_angles", "S", "P", "A", "phi0", "zigzag", "Q", "fwhm",
+                              "k_min", "k_max", "half_width")}
+    st = Setup(**kw)
+    x = phantom_for(cfg)
+    op = FFLOperator(**kw)
+    Ks = list(range(cfg["k_min"], cfg["k_max"] + 1))
+    ws = list(range(0, cfg["half_width"] + 1))
+    got = op.information_retained(torch.from_numpy(x).cuda(), Ks, ws)
+    sig = operator.forward_stages(x.astype(np.float64), st)["sig"]
+    L = st.S * st.P
+    for a, K in enumerate(Ks):
+        for c, w in enumerate(ws):
+            k = np.arange(cfg["k_min"], K + 1)
+            d = np.arange(-w, w + 1)
+            bins = (k[:, None] * st.P + d[None, :]).reshape(-1)
+            ref = operator.information_retained(sig, np.concatenate([bins, L - bins]))
+            assert abs(got[a, c] - ref) <= 1e-5 * ref, (K, w, got[a, c], ref)
+    # monotone in both the harmonic count and the bandwidth, and at most 1
+    assert np.all(np.diff(got, axis=0) >= 0) and np.all(np.diff(got, axis=1) >= 0) and got.max() <= 1.0
