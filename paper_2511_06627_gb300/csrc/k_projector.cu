@@ -10,12 +10,13 @@
 
 namespace mpiffl {
 
-// Cell and fraction of a Q32.32 position: floor and f - floor, the fraction rounded
-// to FP32 (it may round up to 1.0f, which weights the next cell fully in both the
-// projector and its transpose).
+// Cell and fraction of a Q32.32 position: floor and f - floor, the fraction cut to
+// its top 23 bits. The float is assembled from the bits, 1 + m 2^-23 with m the
+// fraction's top 23 bits, minus 1: exact, in [0, 1), and on the integer and FMA pipes
+// rather than the conversion unit.
 __device__ __forceinline__ void fx_split(long long f, int &k, float &t) {
     k = (int)(f >> 32);
-    t = __uint2float_rn((unsigned)(f & 0xffffffffll)) * 0x1p-32f;
+    t = __uint_as_float(0x3f800000u | ((unsigned)f >> 9)) - 1.0f;
 }
 
 __device__ __forceinline__ void transpose_body(const float *__restrict__ vol, float *__restrict__ volT, int N,
