@@ -16,6 +16,7 @@ It follows the paper (arXiv 2511.06627) step by step, in float64:
                velocity of a sinusoidal drive plus a zig-zag slow raster
   operator     Sec. 1.3 Eq. (9), Sec. 2.1 Eqs. (11), (13), Sec. 2.2 Eq. (23),
                Appendix A Eq. (27): A = blockdiag(S D_Gamma F V E H B) [P_theta]
+  zdrive       Sec. 3.1: the z-drive scan of the dual-drive acquisition, A_z
   regularizer  Sec. 3.3, Eq. (25): finite-difference operator T
   solver       Sec. 3.3, Eqs. (25)-(26): accelerated projected gradient descent
   data         noisy compressed data for the synthetic workloads
@@ -27,4 +28,4 @@ itself (closed forms, special cases, brute force, library routines).
 """
 
 from .setup import Setup  # noqa: F401
-from . import projection, psf, trajectory, operator, regularizer, solver, data  # noqa: F401
+from . import projection, psf, trajectory, operator, regularizer, solver, data, zdrive  # noqa: F401
