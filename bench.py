@@ -616,6 +616,44 @@ def run_ours(args, cfg, rank, world, local_rank):
         result["recon"] = rec
         use_path(op, path)
     if not args.quick:
+        # dual-drive acquisition (Sec. 3.1): the x-drive scan on the headline path plus the
+        # z-drive scan (staged FP32); one step is [A; A_z] x then A^T b + A_z^T b_z
+        bz = op.new_data()
+        xz = op.new_volume()
+
+        def dual_step():
+            op.forward(x, out=b)
+            op.forward_zdrive(x, out=bz)
+            op.adjoint(b, out=xa)
+            op.adjoint_zdrive(bz, out=xz)
+            xa.add_(xz)
+
+        for _ in range(2):
+            dual_step()
+        n_dual = max(3, args.steps // 2)
+        d_starts = [torch.cuda.Event(enable_timing=True) for _ in range(n_dual)]
+        d_ends = [torch.cuda.Event(enable_timing=True) for _ in range(n_dual)]
+        for k in range(n_dual):
+            flush.zero_()
+            d_starts[k].record(stream)
+            dual_step()
+            d_ends[k].record(stream)
+        torch.cuda.synchronize()
+        dual_ms = sum(s_.elapsed_time(e) for s_, e in zip(d_starts, d_ends)) / n_dual
+        z_ms = {}
+        for name, fn in (("forward_zdrive", lambda: op.forward_zdrive(x, out=bz)),
+                         ("adjoint_zdrive", lambda: op.adjoint_zdrive(bz, out=xz))):
+            z0 = torch.cuda.Event(enable_timing=True)
+            z1 = torch.cuda.Event(enable_timing=True)
+            flush.zero_()
+            z0.record(stream)
+            fn()
+            z1.record(stream)
+            torch.cuda.synchronize()
+            z_ms[name] = z0.elapsed_time(z1)
+        result["dual_drive"] = {"pairs_per_s": 1e3 / dual_ms, "ms_per_pair": dual_ms, "z_drive_ms": z_ms,
+                                "x_drive_path": path, "z_drive_path": "staged FP32",
+                                "step": "[A; A_z] x then A^T b + A_z^T b_z"}
         # compression analysis (Appendix A, Eq. (30)) on the phantom's time signal
         Ks = [k for k in (1, 2, 4, 8, 16) if op.k_min <= k <= op.k_max]
         ws = [w for w in (0, 1, 2, 4) if w <= op.half_width]
@@ -682,6 +720,20 @@ def cpu_baseline_leg(cfg, x_np, op, args):
             ef = max(ef, float(np.linalg.norm(got_b - r["ref_b"]) / np.linalg.norm(r["ref_b"])))
             ea = max(ea, float(np.linalg.norm(xx - r["ref_x"]) / np.linalg.norm(r["ref_x"])))
         errs[key] = {"forward_rel_l2": ef, "adjoint_rel_l2": ea}
+    # the z-drive scan (staged FP32) on the same sampled angles
+    from oracle import zdrive
+
+    bz_all = op.forward_zdrive(x_dev).cpu().numpy().astype(np.float64)
+    ezf, eza = 0.0, 0.0
+    for m, r in refs.items():
+        ref_bz = zdrive.forward_stages_z(xo, st, angles=np.array([m]))["data"][0]
+        ezf = max(ezf, float(np.linalg.norm(bz_all[m, ..., 0] + 1j * bz_all[m, ..., 1] - ref_bz) /
+                             np.linalg.norm(ref_bz)))
+        y_m = r["y_dev"][m].cpu().numpy().astype(np.float64)
+        ref_xz = zdrive.adjoint_stages_z((y_m[..., 0] + 1j * y_m[..., 1])[None], st, angles=np.array([m]))["vol"]
+        xz = op.adjoint_zdrive(r["y_dev"]).cpu().numpy().astype(np.float64)
+        eza = max(eza, float(np.linalg.norm(xz - ref_xz) / np.linalg.norm(ref_xz)))
+    errs["z_drive_staged"] = {"forward_rel_l2": ezf, "adjoint_rel_l2": eza}
     # per stage: the staged FP32 path's own intermediates against the oracle's
     op.set_path("staged")
     stages = {}

@@ -142,6 +142,7 @@ typedef struct {
     int32_t fine_len;/* N_e = (nx-1) Q + 2 ceil(A Q) + 1                  */
     int32_t line_len;/* L = S P                                           */
     int64_t workspace_bytes; /* device memory the handle holds            */
+    int32_t fine_len_z; /* N_ez = (N_z - 1) Q + 2 D + 1: fine z grid of the z-drive scan */
 } mpi_ffl_sizes;
 
 /* Create a handle on the current CUDA device: validates the description, builds the
@@ -200,6 +201,29 @@ int mpi_ffl_forward(mpi_ffl_handle *h, const float *x, float *b_ri, void *stream
 /* x = A^T b = Re(A^H b) (transpose of Eq. (23) under the real inner product). Host
  * or device buffers, as mpi_ffl_forward. */
 int mpi_ffl_adjoint(mpi_ffl_handle *h, const float *b_ri, float *x, void *stream);
+
+/* The z-drive scan of the dual-drive acquisition (Sec. 3.1: at every angle one scan
+ * drives the FFL along x, one along z). Same raster, trajectory parameters, kept bins,
+ * D_Gamma and gains as the x-drive scan of mpi_ffl_forward; the drive and the 1D
+ * Langevin-derivative PSF act along z. Sample j of line l reads the z-convolved
+ * projection, evaluated on a grid Q times finer than the slices (N_ez =
+ * (N_z - 1) Q + 2 D + 1 points from -D/Q), bilinearly at detector position c_j (the
+ * slow raster) and height l + A sin(2 pi j / S + phi0), and is weighted by the drive
+ * velocity along z and the gain. b_z has the layout of b (n_data floats). The
+ * dual-drive operator is [A; A_z] with transpose A^T y + A_z^T y_z. Staged FP32
+ * kernels; the first call builds the z tables and allocates the z workspace (time
+ * signal n_sig floats, the transpose's per-phase partials M N_z N S floats, the fine
+ * z grid M N N_ez floats) and returns MPI_FFL_ERR_UNSUPPORTED when (N_z + 1) S floats
+ * exceed 200 KB. Host or device buffers, as mpi_ffl_forward. */
+int mpi_ffl_forward_zdrive(mpi_ffl_handle *h, const float *x, float *b_z_ri, void *stream);
+int mpi_ffl_adjoint_zdrive(mpi_ffl_handle *h, const float *b_z_ri, float *x, void *stream);
+
+/* Stages of the z-drive scan on caller device buffers (transpose = 1 for the
+ * transpose): stage 1 = H_z: proj [M][N_z][N] <-> fine_z [M][N][N_ez];
+ * stage 2 = E_z V_z B: fine_z <-> sig [M][N_z][L]. P and S D_Gamma F are the x-drive
+ * stages 0 and 3 of mpi_ffl_apply_stage. */
+int mpi_ffl_apply_stage_zdrive(mpi_ffl_handle *h, int32_t stage, int32_t transpose, const float *d_in,
+                               float *d_out, void *stream);
 
 /* on != 0: host inputs of forward/adjoint are copied on a stream of the handle that
  * waits only for the previous use of its (double-buffered) staging slot, so the copy
@@ -358,7 +382,8 @@ int mpi_ffl_dot_f64_noalloc(const float *d_a, const float *d_b, int64_t n, doubl
 #define MPI_FFL_K_SOLVER 11       /* momentum, residual, update and reductions      */
 #define MPI_FFL_K_GEMM_FWD 12     /* collapsed line operator, forward GEMM          */
 #define MPI_FFL_K_GEMM_ADJ 13     /* collapsed line operator, adjoint GEMM          */
-#define MPI_FFL_N_KERNEL_KINDS 14
+#define MPI_FFL_K_ZDRIVE 14       /* z-drive scan: column transposes, E_z V_z B and its transpose */
+#define MPI_FFL_N_KERNEL_KINDS 15
 
 /* enable != 0: record a CUDA event pair around every kernel the handle launches (on
  * the launching stream) until disabled; enable == 0 stops recording. */

@@ -105,20 +105,22 @@ def resample_fwd_z(cz, setup, angles=None):
 
 
 def resample_adj_z(sig, setup, angles=None):
-    """The literal transpose of resample_fwd_z (scatter with np.add.at)."""
+    """The literal transpose of resample_fwd_z: every sample scattered back onto the
+    four grid points it read, with the same weights (bincount sums the scatter)."""
     sig = np.asarray(sig, dtype=np.float64)
     M = sig.shape[0]
     N = setup.nx
+    nez = n_fine_z(setup)
     gains = setup.gains if angles is None else setup.gains[angles]
-    out = np.zeros((M, N + 1, n_fine_z(setup)))
+    out = np.zeros((M, (N + 1) * nez))
     for line in range(setup.nz):
         u0, a, n, f, v = _line_tables(setup, line)
+        idx = np.concatenate([u0 * nez + n, u0 * nez + n + 1, (u0 + 1) * nez + n, (u0 + 1) * nez + n + 1])
+        wts = np.concatenate([(1.0 - a) * (1.0 - f), (1.0 - a) * f, a * (1.0 - f), a * f])
         for m in range(M):
             w = gains[m] * v * sig[m, line]
-            for du, wu in ((0, 1.0 - a), (1, a)):
-                np.add.at(out[m], (u0 + du, n), wu * (1.0 - f) * w)
-                np.add.at(out[m], (u0 + du, n + 1), wu * f * w)
-    return out[:, :N]
+            out[m] += np.bincount(idx, weights=wts * np.tile(w, 4), minlength=(N + 1) * nez)
+    return out.reshape(M, N + 1, nez)[:, :N]
 
 
 # ----------------------------------------------------------------------------- A_z

@@ -66,7 +66,8 @@ class SolveReport(C.Structure):
 class Sizes(C.Structure):
     _fields_ = [("n_vox", C.c_int64), ("n_data", C.c_int64), ("n_proj", C.c_int64),
                 ("n_fine", C.c_int64), ("n_sig", C.c_int64), ("n_bins", C.c_int32),
-                ("fine_len", C.c_int32), ("line_len", C.c_int32), ("workspace_bytes", C.c_int64)]
+                ("fine_len", C.c_int32), ("line_len", C.c_int32), ("workspace_bytes", C.c_int64),
+                ("fine_len_z", C.c_int32)]
 
 
 class JobStatus(C.Structure):
@@ -91,6 +92,9 @@ PROTOTYPES = {
     "mpi_ffl_get_precision": (C.c_int, [H]),
     "mpi_ffl_set_host_overlap": (C.c_int, [H, C.c_int32]),
     "mpi_ffl_band_energy": (C.c_int, [H, FP, FP, FP, FP]),
+    "mpi_ffl_forward_zdrive": (C.c_int, [H, FP, FP, FP]),
+    "mpi_ffl_adjoint_zdrive": (C.c_int, [H, FP, FP, FP]),
+    "mpi_ffl_apply_stage_zdrive": (C.c_int, [H, C.c_int32, C.c_int32, FP, FP, FP]),
     "mpi_ffl_set_gain": (C.c_int, [H, C.POINTER(C.c_float)]),
     "mpi_ffl_set_psf_fwhm": (C.c_int, [H, C.c_double]),
     "mpi_ffl_sync_check": (C.c_int, [H, ST]),
@@ -119,7 +123,7 @@ PROTOTYPES = {
 }
 
 KERNEL_KINDS = ["transpose", "project", "backproject", "psf_fwd", "psf_adj", "resample_fwd", "resample_adj",
-                "dft_fwd", "dft_adj", "tc_fwd", "tc_adj", "solver", "gemm_fwd", "gemm_adj"]
+                "dft_fwd", "dft_adj", "tc_fwd", "tc_adj", "solver", "gemm_fwd", "gemm_adj", "zdrive"]
 
 _lib = None
 

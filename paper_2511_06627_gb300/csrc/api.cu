@@ -201,6 +201,7 @@ int compute_dims(const mpi_ffl_geometry *g, const mpi_ffl_trajectory *t, const m
     d.Q = t->upsample_q;
     d.D = (int)std::ceil(t->drive_amp_vox * d.Q - 1e-9);
     d.Ne = (d.N - 1) * d.Q + 2 * d.D + 1;
+    d.Nez = (d.Nz - 1) * d.Q + 2 * d.D + 1;
     d.K = hm->k_max - hm->k_min + 1;
     d.hw = hm->half_width;
     d.W = 2 * d.hw + 1;
@@ -217,7 +218,8 @@ int compute_dims(const mpi_ffl_geometry *g, const mpi_ffl_trajectory *t, const m
     d.nfine = (int64_t)d.nseg * d.Ne;
     d.nsig = (int64_t)d.nseg * d.L;
     d.ndata = (int64_t)2 * d.nseg * d.nb;
-    d.htab_off = (d.N - 1) * d.Q + d.D + d.Q * kPsfT;
+    // taps for the x-drive rows (N bins) and the z-drive columns (N_z slices)
+    d.htab_off = (std::max(d.N, d.Nz) - 1) * d.Q + d.D + d.Q * kPsfT;
     d.htab_len = 2 * d.htab_off + 1;
     d.n_par = t->zigzag ? 2 : 1;
     // shared memory of the staged kernels
@@ -367,6 +369,10 @@ void release(mpi_ffl_handle *h) {
     }
     for (auto e : h->ev_pool) cudaEventDestroy(e);
     for (float *p : {h->hs_in[0], h->hs_in[1], h->hs_out})
+        if (p) cudaFree(p);
+    for (void *p : {(void *)h->tz_ua, (void *)h->tz_n0, (void *)h->tz_plo, (void *)h->tz_phi, (void *)h->tz_tap_ptr,
+                    (void *)h->tz_f0, (void *)h->tz_v, (void *)h->tz_taps, (void *)h->w_fine_z,
+                    (void *)h->w_projT, (void *)h->w_tz})
         if (p) cudaFree(p);
     for (int k = 0; k < 2; ++k) {
         if (h->hs_ready[k]) cudaEventDestroy(h->hs_ready[k]);
@@ -751,6 +757,7 @@ extern "C" int mpi_ffl_get_sizes(const mpi_ffl_handle *h, mpi_ffl_sizes *o) {
     o->n_bins = h->d.nb;
     o->fine_len = h->d.Ne;
     o->line_len = h->d.L;
+    o->fine_len_z = h->d.Nez;
     o->workspace_bytes = h->bytes;
     return MPI_FFL_OK;
 }
@@ -898,6 +905,186 @@ extern "C" int mpi_ffl_adjoint(mpi_ffl_handle *h, const float *b, float *x, void
         with_host_buffers(h, b, h->d.ndata, x, h->d.nvox, st, [&](const float *db, float *dx) {
             adjoint_impl(h, db, dx, st);
         });
+        return MPI_FFL_OK;
+    });
+}
+
+// ------------------------------------------------------------ z-drive scan
+int float_bits(float f) {
+    int i;
+    std::memcpy(&i, &f, 4);
+    return i;
+}
+
+// Tables of the z-drive scan, in double precision on the host: the slow raster's
+// detector column and fraction per (parity, j), the drive's fine z offset, fraction
+// and velocity per phase r = j mod S, the periods reading each column, and the
+// transpose's taps grouped by residue of the fine index modulo Q.
+void z_init(mpi_ffl_handle *h) {
+    if (h->z_ready) return;
+    const Dims &d = h->d;
+    const int L = d.L, S = d.S, N = d.N, P = d.P, Q = d.Q, npar = d.n_par;
+    if ((size_t)(d.Nz + 1) * S * 4 > 200 * 1024) {
+        h->err = "the z-drive transpose keeps (N_z + 1) x S floats in shared memory (at most 200 KB)";
+        throw Fail{MPI_FFL_ERR_UNSUPPORTED};
+    }
+    const double slope = (double)(N - 1) / (double)(L - 1);
+    std::vector<int> u0((size_t)npar * L);
+    std::vector<float2> ua((size_t)npar * L);
+    for (int par = 0; par < npar; ++par)
+        for (int j = 0; j < L; ++j) {
+            const double c = par ? (N - 1) - slope * j : slope * j;
+            int k = (int)std::floor(c);
+            k = std::min(std::max(k, 0), N - 1);
+            u0[(size_t)par * L + j] = k;
+            float kb;
+            std::memcpy(&kb, &k, 4);
+            ua[(size_t)par * L + j] = make_float2(kb, (float)(c - k));
+        }
+    const double kPi = 3.14159265358979323846;
+    std::vector<int> n0(S);
+    std::vector<float> f0(S), v(S);
+    for (int r = 0; r < S; ++r) {
+        const double ph = 2.0 * kPi * r / S + h->phase;
+        const double t = Q * h->amp * std::sin(ph) + d.D;
+        n0[r] = (int)std::floor(t);
+        f0[r] = (float)(t - n0[r]);
+        v[r] = (float)(h->amp * (2.0 * kPi / S) * std::cos(ph));
+    }
+    std::vector<int> plo((size_t)npar * S * N, 0), phi((size_t)npar * S * N, -1);
+    for (int par = 0; par < npar; ++par)
+        for (int r = 0; r < S; ++r)
+            for (int p = 0; p < P; ++p) {
+                const int k = u0[(size_t)par * L + (size_t)p * S + r];
+                for (int u : {k, k + 1}) {
+                    if (u >= N) continue;
+                    const size_t i = ((size_t)par * S + r) * N + u;
+                    if (phi[i] < 0) plo[i] = p;
+                    phi[i] = p;
+                }
+            }
+    std::vector<int> ptr(Q + 1, 0);
+    std::vector<int4> taps;
+    for (int rho = 0; rho < Q; ++rho) {
+        ptr[rho] = (int)taps.size();
+        for (int r = 0; r < S; ++r) {
+            if (((n0[r] % Q) + Q) % Q == rho) taps.push_back(make_int4(r, n0[r], float_bits(1.f - f0[r]), 0));
+            if ((((n0[r] + 1) % Q) + Q) % Q == rho) taps.push_back(make_int4(r, n0[r] + 1, float_bits(f0[r]), 0));
+        }
+    }
+    ptr[Q] = (int)taps.size();
+    upload(h, &h->tz_ua, ua);
+    upload(h, &h->tz_n0, n0);
+    upload(h, &h->tz_f0, f0);
+    upload(h, &h->tz_v, v);
+    upload(h, &h->tz_plo, plo);
+    upload(h, &h->tz_phi, phi);
+    upload(h, &h->tz_tap_ptr, ptr);
+    upload(h, &h->tz_taps, taps);
+    ensure_sig(h);
+    dev_alloc(h, &h->w_fine_z, (size_t)d.M * N * d.Nez);
+    dev_alloc(h, &h->w_projT, (size_t)d.M * N * d.Nz);
+    dev_alloc(h, &h->w_tz, (size_t)d.M * d.Nz * N * S);
+    h->z_ready = 1;
+}
+
+ZTables z_tables(const mpi_ffl_handle *h) {
+    return ZTables{h->tz_ua, h->tz_n0, h->tz_f0, h->tz_v, h->tz_plo, h->tz_phi, h->tz_tap_ptr, h->tz_taps};
+}
+
+// the PSF kernels along z: lines are the M N detector columns, N_z slices long
+Dims z_dims(const Dims &d) {
+    Dims dz = d;
+    dz.N = d.Nz;
+    dz.Nz = d.N;
+    dz.nseg = d.M * d.N;
+    dz.Ne = d.Nez;
+    return dz;
+}
+
+void zstage_h(mpi_ffl_handle *h, const float *proj, float *cz, cudaStream_t st) {
+    const Dims &d = h->d;
+    TIMED(MPI_FFL_K_ZDRIVE, launch_transpose_2d(proj, h->w_projT, d.M, d.Nz, d.N, st));
+    TIMED(MPI_FFL_K_PSF_FWD, launch_psf_fwd(h->w_projT, h->t_htab, cz, z_dims(d), st));
+}
+
+void zstage_ht(mpi_ffl_handle *h, const float *cz, float *proj, cudaStream_t st) {
+    const Dims &d = h->d;
+    TIMED(MPI_FFL_K_PSF_ADJ, launch_psf_adj(cz, h->t_htab, h->w_projT, z_dims(d), st));
+    TIMED(MPI_FFL_K_ZDRIVE, launch_transpose_2d(h->w_projT, proj, d.M, d.N, d.Nz, st));
+}
+
+void zstage_ev(mpi_ffl_handle *h, const float *cz, float *sig, cudaStream_t st) {
+    TIMED(MPI_FFL_K_ZDRIVE, launch_resample_z_fwd(cz, z_tables(h), h->t_gain, sig, h->d, h->zigzag, st));
+}
+
+void zstage_evt(mpi_ffl_handle *h, const float *sig, float *cz, cudaStream_t st) {
+    TIMED(MPI_FFL_K_ZDRIVE, launch_resample_z_adj(sig, z_tables(h), h->t_gain, h->w_tz, cz, h->d, h->zigzag, st));
+}
+
+void forward_z_impl(mpi_ffl_handle *h, const float *x, float *b, cudaStream_t st) {
+    const Dims &d = h->d;
+    z_init(h);
+    stage_p(h, x, h->w_proj, st);
+    zstage_h(h, h->w_proj, h->w_fine_z, st);
+    zstage_ev(h, h->w_fine_z, h->w_sig, st);
+    TIMED(MPI_FFL_K_DFT_FWD, launch_dft_fwd(h->w_sig, h->t_tw1, h->t_tw2_ro, h->t_dgam, b, d, st));
+    check_launch(h, "z-drive forward");
+}
+
+void adjoint_z_impl(mpi_ffl_handle *h, const float *b, float *x, cudaStream_t st) {
+    const Dims &d = h->d;
+    z_init(h);
+    TIMED(MPI_FFL_K_DFT_ADJ, launch_dft_adj(b, h->t_tw1, h->t_tw2_qr, h->t_dgam, h->w_sig, d, st));
+    zstage_evt(h, h->w_sig, h->w_fine_z, st);
+    zstage_ht(h, h->w_fine_z, h->w_proj, st);
+    stage_pt(h, h->w_proj, x, st);
+    check_launch(h, "z-drive adjoint");
+}
+
+extern "C" int mpi_ffl_forward_zdrive(mpi_ffl_handle *h, const float *x, float *b, void *stream) {
+    return guarded(h, [&]() {
+        if (!x || !b) {
+            h->err = "NULL buffer";
+            return MPI_FFL_ERR_INVALID_ARG;
+        }
+        cudaStream_t st = S(stream);
+        with_host_buffers(h, x, h->d.nvox, b, h->d.ndata, st,
+                          [&](const float *dx, float *db) { forward_z_impl(h, dx, db, st); });
+        return MPI_FFL_OK;
+    });
+}
+
+extern "C" int mpi_ffl_adjoint_zdrive(mpi_ffl_handle *h, const float *b, float *x, void *stream) {
+    return guarded(h, [&]() {
+        if (!x || !b) {
+            h->err = "NULL buffer";
+            return MPI_FFL_ERR_INVALID_ARG;
+        }
+        cudaStream_t st = S(stream);
+        with_host_buffers(h, b, h->d.ndata, x, h->d.nvox, st,
+                          [&](const float *db, float *dx) { adjoint_z_impl(h, db, dx, st); });
+        return MPI_FFL_OK;
+    });
+}
+
+extern "C" int mpi_ffl_apply_stage_zdrive(mpi_ffl_handle *h, int32_t stage, int32_t transpose, const float *in,
+                                          float *out, void *stream) {
+    return guarded(h, [&]() {
+        if (!in || !out || (stage != 1 && stage != 2)) {
+            h->err = "bad z-drive stage or NULL buffer";
+            return MPI_FFL_ERR_INVALID_ARG;
+        }
+        z_init(h);
+        cudaStream_t st = S(stream);
+        if (stage == 1) {
+            if (transpose) zstage_ht(h, in, out, st);
+            else zstage_h(h, in, out, st);
+        } else {
+            if (transpose) zstage_evt(h, in, out, st);
+            else zstage_ev(h, in, out, st);
+        }
+        check_launch(h, "z-drive stage");
         return MPI_FFL_OK;
     });
 }

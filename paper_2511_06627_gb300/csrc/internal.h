@@ -45,6 +45,18 @@ struct CsrEntry {
     float w;
 };
 
+// Tables of the z-drive scan (k_zdrive.cu).
+struct ZTables {
+    const float2 *ua;         // [parity][j]: detector column u0 of the slow position c_j (int
+                              // bits) and its fraction c_j - u0
+    const int *n0;            // [r]: fine z cell offset floor(Q A sin(2 pi r / S + phi0) + D)
+    const float *f0;          // [r]: its fraction
+    const float *v;           // [r]: drive velocity along z, A (2 pi / S) cos(2 pi r / S + phi0)
+    const int *plo, *phi;     // [parity][r][u]: periods p whose sample pS + r reads column u
+    const int *tap_ptr;       // [Q + 1]: taps of each residue of e mod Q
+    const int4 *taps;         // (r, e_off, weight bits, 0)
+};
+
 // A group of raster lines of one angle that share a trajectory (same parity).
 struct SegGroup {
     int m;       // angle
@@ -56,6 +68,7 @@ struct SegGroup {
 
 struct Dims {
     int N, Nz, M, S, P, L, Q, D, Ne, K, W, nb, kmin, hw;
+    int Nez;                       // fine z grid of the z-drive scan: (N_z - 1) Q + 2 D + 1
     int nseg;                      // M * Nz
     int64_t nvox, nproj, nfine, nsig, ndata;
     int htab_off, htab_len;        // htab[d + htab_off] = h(d / Q), |d| <= htab_off + pad
@@ -141,6 +154,15 @@ struct mpi_ffl_handle {
     cudaEvent_t hs_ready[2] = {}, hs_free[2] = {};
     int hs_slot = 0;
     int host_overlap = 0;                   // mpi_ffl_set_host_overlap
+    // z-drive scan (k_zdrive.cu): tables and workspace, built on first use
+    int z_ready = 0;
+    int *tz_n0 = nullptr, *tz_plo = nullptr, *tz_phi = nullptr, *tz_tap_ptr = nullptr;
+    float *tz_f0 = nullptr, *tz_v = nullptr;
+    float2 *tz_ua = nullptr;
+    int4 *tz_taps = nullptr;
+    float *w_fine_z = nullptr;  // M N N_ez
+    float *w_projT = nullptr;   // M N N_z (projections by column)
+    float *w_tz = nullptr;      // M N_z N S (per-phase partials of the transpose)
 };
 
 namespace mpiffl {
@@ -255,6 +277,11 @@ void launch_update(const float *y, const float *g, float *xout, float tau, float
                    int N, int Nz, const int *done, cudaStream_t st, const float *xcur = nullptr);
 void launch_freeze(const int *stop, int *frozen, cudaStream_t st);
 void launch_bin_energy(const float *data, int nseg, int nb, double *out, cudaStream_t st);
+void launch_transpose_2d(const float *in, float *out, int batch, int rows, int cols, cudaStream_t st);
+void launch_resample_z_fwd(const float *cz, const ZTables &T, const float *gain, float *sig, const Dims &d,
+                           int zigzag, cudaStream_t st);
+void launch_resample_z_adj(const float *sig, const ZTables &T, const float *gain, float *tz, float *cz,
+                           const Dims &d, int zigzag, cudaStream_t st);
 void launch_ttt(const float *x, float *out, int N, int Nz, cudaStream_t st);
 void launch_splitmix_fill(float *v, int64_t n, uint64_t seed, cudaStream_t st);
 void launch_scale_by_rsqrt(const float *in, float *out, int64_t n, const double *n2, cudaStream_t st);

@@ -67,6 +67,7 @@ class FFLOperator:
         self.n_bins = sz.n_bins
         self.L = sz.line_len
         self.fine_len = sz.fine_len
+        self.fine_len_z = sz.fine_len_z
         self.S, self.P, self.Q = S, P, Q
         self.k_min, self.k_max, self.half_width = k_min, k_max, half_width
         self.fwhm = fwhm
@@ -124,6 +125,38 @@ class FFLOperator:
         out = self.new_volume() if out is None else out
         self._check(out, self.vol_shape, "out", host_ok=True)
         check(self._lib.mpi_ffl_adjoint(self._h, _ptr(b), _ptr(out), _stream()), self._h)
+        return out
+
+    # ---------------------------------------------------------------- z-drive scan
+    def forward_zdrive(self, x, out=None):
+        """b_z = A_z x: the z-drive scan of the dual-drive acquisition (same data layout
+        as forward). CUDA or host tensors."""
+        self._check(x, self.vol_shape, "x", host_ok=True)
+        out = self.new_data() if out is None else out
+        self._check(out, self.data_shape, "out", host_ok=True)
+        check(self._lib.mpi_ffl_forward_zdrive(self._h, _ptr(x), _ptr(out), _stream()), self._h)
+        return out
+
+    def adjoint_zdrive(self, b, out=None):
+        """x = A_z^T b_z; CUDA or host tensors."""
+        self._check(b, self.data_shape, "b", host_ok=True)
+        out = self.new_volume() if out is None else out
+        self._check(out, self.vol_shape, "out", host_ok=True)
+        check(self._lib.mpi_ffl_adjoint_zdrive(self._h, _ptr(b), _ptr(out), _stream()), self._h)
+        return out
+
+    def apply_stage_zdrive(self, stage, inp, transpose=False):
+        """z-drive stage 1 (H_z: proj [M, N_z, N] <-> fine_z [M, N, N_ez]) or 2
+        (E_z V_z B: fine_z <-> sig [M, N_z, L])."""
+        M, nz, n = self.n_angles, self.nz, self.nx
+        shapes = {1: ((M, nz, n), (M, n, self.fine_len_z)), 2: ((M, n, self.fine_len_z), (M, nz, self.L))}
+        if stage not in shapes:
+            raise ValueError("z-drive stages are 1 and 2")
+        sin, sout = shapes[stage][::-1] if transpose else shapes[stage]
+        self._check(inp, sin, "input")
+        out = torch.empty(sout, device=self.device, dtype=torch.float32)
+        check(self._lib.mpi_ffl_apply_stage_zdrive(self._h, int(stage), int(bool(transpose)), _ptr(inp), _ptr(out),
+                                                   _stream()), self._h)
         return out
 
     def stage_shapes(self):
