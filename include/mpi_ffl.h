@@ -210,18 +210,21 @@ int mpi_ffl_adjoint(mpi_ffl_handle *h, const float *b_ri, float *x, void *stream
  * (N_z - 1) Q + 2 D + 1 points from -D/Q), bilinearly at detector position c_j (the
  * slow raster) and height l + A sin(2 pi j / S + phi0), and is weighted by the drive
  * velocity along z and the gain. b_z has the layout of b (n_data floats). The
- * dual-drive operator is [A; A_z] with transpose A^T y + A_z^T y_z. Staged FP32
- * kernels; the first call builds the z tables and allocates the z workspace (time
- * signal n_sig floats, the transpose's per-phase partials M N_z N S floats, the fine
- * z grid M N N_ez floats) and returns MPI_FFL_ERR_UNSUPPORTED when (N_z + 1) S floats
- * exceed 200 KB. Host or device buffers, as mpi_ffl_forward. */
+ * dual-drive operator is [A; A_z] with transpose A^T y + A_z^T y_z. FP32 kernels
+ * that fuse E_z V_z B with S D_Gamma F (and their transposes), so no time signal is
+ * stored. The first call builds the z tables and allocates the z workspace (the fine
+ * z grid M N N_ez floats, the projections by column M N N_z floats, the transpose's
+ * synthesis coefficients M N_z (2w+1) S floats). It returns MPI_FFL_ERR_UNSUPPORTED
+ * when (N_z + 1) S floats exceed 200 KB or the fused kernels' shared-memory tiles
+ * exceed 227 KB. Host or device buffers, as mpi_ffl_forward. */
 int mpi_ffl_forward_zdrive(mpi_ffl_handle *h, const float *x, float *b_z_ri, void *stream);
 int mpi_ffl_adjoint_zdrive(mpi_ffl_handle *h, const float *b_z_ri, float *x, void *stream);
 
 /* Stages of the z-drive scan on caller device buffers (transpose = 1 for the
  * transpose): stage 1 = H_z: proj [M][N_z][N] <-> fine_z [M][N][N_ez];
  * stage 2 = E_z V_z B: fine_z <-> sig [M][N_z][L]. P and S D_Gamma F are the x-drive
- * stages 0 and 3 of mpi_ffl_apply_stage. */
+ * stages 0 and 3 of mpi_ffl_apply_stage. The first transpose of stage 2 allocates its
+ * per-phase partials (M N_z N S floats). */
 int mpi_ffl_apply_stage_zdrive(mpi_ffl_handle *h, int32_t stage, int32_t transpose, const float *d_in,
                                float *d_out, void *stream);
 
@@ -382,7 +385,7 @@ int mpi_ffl_dot_f64_noalloc(const float *d_a, const float *d_b, int64_t n, doubl
 #define MPI_FFL_K_SOLVER 11       /* momentum, residual, update and reductions      */
 #define MPI_FFL_K_GEMM_FWD 12     /* collapsed line operator, forward GEMM          */
 #define MPI_FFL_K_GEMM_ADJ 13     /* collapsed line operator, adjoint GEMM          */
-#define MPI_FFL_K_ZDRIVE 14       /* z-drive scan: column transposes, E_z V_z B and its transpose */
+#define MPI_FFL_K_ZDRIVE 14       /* z-drive scan: column transposes, E_z V_z B with S D F and their transposes */
 #define MPI_FFL_N_KERNEL_KINDS 15
 
 /* enable != 0: record a CUDA event pair around every kernel the handle launches (on

@@ -371,7 +371,8 @@ void release(mpi_ffl_handle *h) {
     for (float *p : {h->hs_in[0], h->hs_in[1], h->hs_out})
         if (p) cudaFree(p);
     for (void *p : {(void *)h->tz_ua, (void *)h->tz_n0, (void *)h->tz_plo, (void *)h->tz_phi, (void *)h->tz_tap_ptr,
-                    (void *)h->tz_f0, (void *)h->tz_v, (void *)h->tz_taps, (void *)h->w_fine_z,
+                    (void *)h->tz_f0, (void *)h->tz_v, (void *)h->tz_taps, (void *)h->tz_optr, (void *)h->tz_otap,
+                    (void *)h->w_zcoef, (void *)h->w_fine_z,
                     (void *)h->w_projT, (void *)h->w_tz})
         if (p) cudaFree(p);
     for (int k = 0; k < 2; ++k) {
@@ -973,6 +974,26 @@ void z_init(mpi_ffl_handle *h) {
         }
     }
     ptr[Q] = (int)taps.size();
+    // the same taps by offset o = e - Q l within a line's cells (the fused transpose)
+    int no = 0;
+    for (int r = 0; r < S; ++r) no = std::max(no, n0[r] + 2);
+    std::vector<int> optr(no + 1, 0);
+    std::vector<int2> otap;
+    for (int o = 0; o < no; ++o) {
+        optr[o] = (int)otap.size();
+        for (int r = 0; r < S; ++r) {
+            if (n0[r] == o) otap.push_back(make_int2(r, float_bits(1.f - f0[r])));
+            if (n0[r] + 1 == o) otap.push_back(make_int2(r, float_bits(f0[r])));
+        }
+    }
+    optr[no] = (int)otap.size();
+    h->tz_no = no;
+    if (zsyn_smem(d, no) > 227 * 1024 || zdft_fwd_smem(d) > 227 * 1024) {
+        h->err = "the fused z-drive kernels keep twiddles and tiles in shared memory (at most 227 KB)";
+        throw Fail{MPI_FFL_ERR_UNSUPPORTED};
+    }
+    upload(h, &h->tz_optr, optr);
+    upload(h, &h->tz_otap, otap);
     upload(h, &h->tz_ua, ua);
     upload(h, &h->tz_n0, n0);
     upload(h, &h->tz_f0, f0);
@@ -981,15 +1002,15 @@ void z_init(mpi_ffl_handle *h) {
     upload(h, &h->tz_phi, phi);
     upload(h, &h->tz_tap_ptr, ptr);
     upload(h, &h->tz_taps, taps);
-    ensure_sig(h);
     dev_alloc(h, &h->w_fine_z, (size_t)d.M * N * d.Nez);
     dev_alloc(h, &h->w_projT, (size_t)d.M * N * d.Nz);
-    dev_alloc(h, &h->w_tz, (size_t)d.M * d.Nz * N * S);
+    dev_alloc(h, &h->w_zcoef, (size_t)d.M * d.Nz * (2 * d.hw + 1) * S);
     h->z_ready = 1;
 }
 
 ZTables z_tables(const mpi_ffl_handle *h) {
-    return ZTables{h->tz_ua, h->tz_n0, h->tz_f0, h->tz_v, h->tz_plo, h->tz_phi, h->tz_tap_ptr, h->tz_taps};
+    return ZTables{h->tz_ua,  h->tz_n0,      h->tz_f0,   h->tz_v,    h->tz_plo, h->tz_phi,
+                   h->tz_tap_ptr, h->tz_taps, h->tz_optr, h->tz_otap, h->tz_no};
 }
 
 // the PSF kernels along z: lines are the M N detector columns, N_z slices long
@@ -1019,6 +1040,7 @@ void zstage_ev(mpi_ffl_handle *h, const float *cz, float *sig, cudaStream_t st) 
 }
 
 void zstage_evt(mpi_ffl_handle *h, const float *sig, float *cz, cudaStream_t st) {
+    if (!h->w_tz) dev_alloc(h, &h->w_tz, (size_t)h->d.M * h->d.Nz * h->d.N * h->d.S);
     TIMED(MPI_FFL_K_ZDRIVE, launch_resample_z_adj(sig, z_tables(h), h->t_gain, h->w_tz, cz, h->d, h->zigzag, st));
 }
 
@@ -1027,16 +1049,17 @@ void forward_z_impl(mpi_ffl_handle *h, const float *x, float *b, cudaStream_t st
     z_init(h);
     stage_p(h, x, h->w_proj, st);
     zstage_h(h, h->w_proj, h->w_fine_z, st);
-    zstage_ev(h, h->w_fine_z, h->w_sig, st);
-    TIMED(MPI_FFL_K_DFT_FWD, launch_dft_fwd(h->w_sig, h->t_tw1, h->t_tw2_ro, h->t_dgam, b, d, st));
+    // E_z V_z B fused with S D_Gamma F: the time signal is not stored
+    TIMED(MPI_FFL_K_ZDRIVE, launch_zdft_fwd(h->w_fine_z, z_tables(h), h->t_gain, h->t_tw1, h->t_tw2_ro, h->t_dgam, b,
+                                            d, h->zigzag, st));
     check_launch(h, "z-drive forward");
 }
 
 void adjoint_z_impl(mpi_ffl_handle *h, const float *b, float *x, cudaStream_t st) {
     const Dims &d = h->d;
     z_init(h);
-    TIMED(MPI_FFL_K_DFT_ADJ, launch_dft_adj(b, h->t_tw1, h->t_tw2_qr, h->t_dgam, h->w_sig, d, st));
-    zstage_evt(h, h->w_sig, h->w_fine_z, st);
+    TIMED(MPI_FFL_K_ZDRIVE, launch_zdft_adj(b, h->t_tw1, h->t_tw2_qr, h->t_dgam, z_tables(h), h->t_gain,
+                                            h->w_zcoef, h->w_fine_z, d, h->zigzag, st));
     zstage_ht(h, h->w_fine_z, h->w_proj, st);
     stage_pt(h, h->w_proj, x, st);
     check_launch(h, "z-drive adjoint");

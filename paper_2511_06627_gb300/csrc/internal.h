@@ -55,6 +55,9 @@ struct ZTables {
     const int *plo, *phi;     // [parity][r][u]: periods p whose sample pS + r reads column u
     const int *tap_ptr;       // [Q + 1]: taps of each residue of e mod Q
     const int4 *taps;         // (r, e_off, weight bits, 0)
+    const int *optr;          // [no + 1]: taps of each offset o = e - Q l of a line's cells
+    const int2 *otap;         // 2 S taps: (r, weight bits), n0_r with 1 - f0_r, n0_r + 1 with f0_r
+    int no;                   // offsets: max n0_r + 2
 };
 
 // A group of raster lines of one angle that share a trajectory (same parity).
@@ -160,9 +163,13 @@ struct mpi_ffl_handle {
     float *tz_f0 = nullptr, *tz_v = nullptr;
     float2 *tz_ua = nullptr;
     int4 *tz_taps = nullptr;
+    int *tz_optr = nullptr;
+    int2 *tz_otap = nullptr;
+    int tz_no = 0;
     float *w_fine_z = nullptr;  // M N N_ez
+    float *w_zcoef = nullptr;   // M N_z W S (synthesis coefficients of the z adjoint)
     float *w_projT = nullptr;   // M N N_z (projections by column)
-    float *w_tz = nullptr;      // M N_z N S (per-phase partials of the transpose)
+    float *w_tz = nullptr;      // M N_z N S (per-phase partials of the staged transpose)
 };
 
 namespace mpiffl {
@@ -282,6 +289,14 @@ void launch_resample_z_fwd(const float *cz, const ZTables &T, const float *gain,
                            int zigzag, cudaStream_t st);
 void launch_resample_z_adj(const float *sig, const ZTables &T, const float *gain, float *tz, float *cz,
                            const Dims &d, int zigzag, cudaStream_t st);
+void launch_zdft_fwd(const float *cz, const ZTables &T, const float *gain, const float *tw1, const float2 *tw2_ro,
+                     const float2 *dgam, float *data, const Dims &d, int zigzag, cudaStream_t st);
+void launch_zdft_adj(const float *data, const float *tw1, const float2 *tw2_qr, const float2 *dgam,
+                     const ZTables &T, const float *gain, float *coef, float *cz, const Dims &d, int zigzag,
+                     cudaStream_t st);
+size_t zdft_fwd_smem(const Dims &d);     // shared memory of the fused z forward
+int zsyn_ring(const Dims &d, int no);
+size_t zsyn_smem(const Dims &d, int no);
 void launch_ttt(const float *x, float *out, int N, int Nz, cudaStream_t st);
 void launch_splitmix_fill(float *v, int64_t n, uint64_t seed, cudaStream_t st);
 void launch_scale_by_rsqrt(const float *in, float *out, int64_t n, const double *n2, cudaStream_t st);
