@@ -655,6 +655,42 @@ def run_ours(args, cfg, rank, world, local_rank):
         result["dual_drive"] = {"pairs_per_s": 1e3 / dual_ms, "ms_per_pair": dual_ms, "z_drive_ms": z_ms,
                                 "x_drive_path": path, "z_drive_path": "FP32, E_z V_z B fused with S D F",
                                 "step": "[A; A_z] x then A^T b + A_z^T b_z"}
+        # tensor PSF (Appendix B, Eq. (31)): every line reads every slice of its projection;
+        # A and A^T run as per-line (per-slice) split-K GEMMs on the bf16 hi+lo operands
+        op.set_psf_model("tensor")
+        for _ in range(2):
+            op.forward(x, out=b)
+            op.adjoint(b, out=xa)
+        n_ten = max(3, args.steps // 2)
+        ten_ms = _timed_pairs(op, x, b, xa, n_ten, flush, stream) / n_ten
+        op.profile(True)
+        op.profile_read()
+        _timed_pairs(op, x, b, xa, n_ten, flush, stream)
+        tprof = op.profile_read()
+        op.profile(False)
+        t_ms, t_n = tprof["tensor"]
+        nz_ = dims["nvox"] // (dims["N"] * dims["N"])
+        R_ = dims["ndata"] // (dims["M"] * nz_)
+        flops = 2.0 * dims["M"] * nz_ * (nz_ * dims["N"]) * R_  # one direction, FP32 contraction
+        sec = t_ms / max(t_n, 1) / 1e3
+        peak, peak_src = bf16_peak_tflops()
+        # issued MMA work: J = 128 // M lines of one trajectory share a problem (rows M J in
+        # 128-row tiles) and its window spans N_z + step (J - 1) slices
+        step_ = 2 if cfg["zigzag"] else 1
+        J_ = max(1, min(128 // dims["M"], (nz_ + step_ - 1) // step_))
+        rows_ = dims["M"] * J_
+        issue_factor = 128 * ((rows_ + 127) // 128) / rows_ * (nz_ + step_ * (J_ - 1)) / nz_
+        result["tensor_psf"] = {
+            "pairs_per_s": 1e3 / ten_ms, "ms_per_pair": ten_ms,
+            "stage_ms_per_launch": round(t_ms / max(t_n, 1), 4),
+            "tensor_tflops": round(3 * flops / sec / 1e12, 2),
+            "tensor_frac": round(3 * flops / sec / 1e12 / peak, 4),
+            "issued_frac": round(3 * flops * issue_factor / sec / 1e12 / peak, 4),
+            "peak": f"{peak} TFLOP/s bf16 ({peak_src})",
+            "note": "stage = coil weighting + padding, per-line (per-slice) GEMMs over all slices (3 bf16 "
+                    "products of 2 M N_z (N_z N) 2n_b flops), sum of the K splits; issued counts the 128-row "
+                    "MMA tiles that hold J lines x M angles and the window's step (J - 1) extra slices"}
+        op.set_psf_model("collinear")
         # compression analysis (Appendix A, Eq. (30)) on the phantom's time signal
         Ks = [k for k in (1, 2, 4, 8, 16) if op.k_min <= k <= op.k_max]
         ws = [w for w in (0, 1, 2, 4) if w <= op.half_width]
@@ -735,6 +771,23 @@ def cpu_baseline_leg(cfg, x_np, op, args):
         xz = op.adjoint_zdrive(r["y_dev"]).cpu().numpy().astype(np.float64)
         eza = max(eza, float(np.linalg.norm(xz - ref_xz) / np.linalg.norm(ref_xz)))
     errs["z_drive"] = {"forward_rel_l2": ezf, "adjoint_rel_l2": eza}
+    # the tensor PSF (full-GEMM path, bf16 hi+lo) on the first sampled angle
+    from oracle import tensor_psf
+
+    use_path(op, "full_gemm")
+    op.set_psf_model("tensor")
+    bt_all = op.forward(x_dev).cpu().numpy().astype(np.float64)
+    m0 = sample[-1]
+    r = refs[m0]
+    ref_bt = tensor_psf.forward_stages(xo, st, None, angles=np.array([m0]))["data"][0]
+    etf = float(np.linalg.norm(bt_all[m0, ..., 0] + 1j * bt_all[m0, ..., 1] - ref_bt) / np.linalg.norm(ref_bt))
+    y_m = r["y_dev"][m0].cpu().numpy().astype(np.float64)
+    ref_xt = tensor_psf.adjoint_stages((y_m[..., 0] + 1j * y_m[..., 1])[None], st, None, angles=np.array([m0]))["vol"]
+    xt = op.adjoint(r["y_dev"]).cpu().numpy().astype(np.float64)
+    errs["tensor_psf"] = {"forward_rel_l2": etf, "adjoint_rel_l2": float(np.linalg.norm(xt - ref_xt) /
+                                                                             np.linalg.norm(ref_xt)),
+                          "angles": [int(m0)]}
+    op.set_psf_model("collinear")
     # per stage: the staged FP32 path's own intermediates against the oracle's
     op.set_path("staged")
     stages = {}

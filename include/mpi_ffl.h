@@ -185,6 +185,34 @@ int mpi_ffl_get_path(const mpi_ffl_handle *h);
 int mpi_ffl_set_gain(mpi_ffl_handle *h, const float *gain);
 int mpi_ffl_set_psf_fwhm(mpi_ffl_handle *h, double fwhm_vox);
 
+/* PSF models of the x-drive operator (forward, adjoint, solve, line stages). */
+#define MPI_FFL_PSF_COLLINEAR 0   /* 1D h(u) = 3 L'(u/a) along the drive axis, per line */
+#define MPI_FFL_PSF_TENSOR 1      /* in-plane tensor PSF: lines coupled across slices */
+
+/* Select the PSF model. TENSOR uses the (x, x) component of the tensor PSF of
+ * Appendix B, Eq. (31) in the FFL plane: h_uu(u, z) = 3 [L'(xi) u^2/rho^2 +
+ * (L(xi)/xi) z^2/rho^2], xi = rho / a, rho^2 = u^2 + z^2, a from the FWHM along the drive
+ * axis as for COLLINEAR (on z = 0 the two agree). Every line then reads every slice of
+ * its projection, c[l][e] = sum_{z', i} p[z'][i] h_uu(u_lo + e/Q - i, l - z'), with full
+ * support. It runs as one GEMM per line (forward) or per slice (adjoint) against
+ * per-offset folded line operators W H_d, built on the device in FP64 when the model is
+ * first selected (2 n_par (2 N_z - 1) 2 n_b N split operands, 4 bytes each, plus
+ * n_par N_z 2 n_b N doubles) and again after set_psf_fwhm or a precision change. It
+ * needs the collapsed line operator (the GEMM paths' tables) and applies whatever
+ * the handle's path; MPI_FFL_ERR_UNSUPPORTED otherwise. Gradients of mpi_ffl_param_grad
+ * and the batched jobs API use COLLINEAR only (MPI_FFL_ERR_UNSUPPORTED / the job runs
+ * alone). The call synchronises the device. */
+int mpi_ffl_set_psf_model(mpi_ffl_handle *h, int32_t model);
+int mpi_ffl_get_psf_model(const mpi_ffl_handle *h);
+
+/* Receive-coil sensitivity map (operator B of Eq. (13)): host array b[z][u] of N_z x N
+ * floats in scanner coordinates, the same for every angle (the object rotates, the
+ * scanner does not, Eq. (19)); NULL restores a uniform coil. The x-drive operator
+ * multiplies each projection by b before its PSF (both models) and its transpose
+ * multiplies after; the per-angle gains still apply. The z-drive scan is unaffected.
+ * The call synchronises the device. */
+int mpi_ffl_set_coil_map(mpi_ffl_handle *h, const float *b_zu);
+
 /* Waits for the stream, then reports whether a kernel of the handle gave up on a
  * bounded wait since the last check (MPI_FFL_ERR_TIMEOUT; the flag is cleared) or
  * the stream holds a CUDA error (MPI_FFL_ERR_CUDA). */
@@ -386,7 +414,9 @@ int mpi_ffl_dot_f64_noalloc(const float *d_a, const float *d_b, int64_t n, doubl
 #define MPI_FFL_K_GEMM_FWD 12     /* collapsed line operator, forward GEMM          */
 #define MPI_FFL_K_GEMM_ADJ 13     /* collapsed line operator, adjoint GEMM          */
 #define MPI_FFL_K_ZDRIVE 14       /* z-drive scan: column transposes, E_z V_z B with S D F and their transposes */
-#define MPI_FFL_N_KERNEL_KINDS 15
+#define MPI_FFL_K_TENSOR 15       /* tensor-PSF line stages: coil weighting, padding, per-line GEMMs */
+#define MPI_FFL_K_COIL 16         /* coil weighting of the collinear model */
+#define MPI_FFL_N_KERNEL_KINDS 17
 
 /* enable != 0: record a CUDA event pair around every kernel the handle launches (on
  * the launching stream) until disabled; enable == 0 stops recording. */

@@ -29,6 +29,8 @@ STAGE_P, STAGE_H, STAGE_EVB, STAGE_F = 0, 1, 2, 3
 
 PATH_STAGED, PATH_FUSED, PATH_LINE_GEMM, PATH_FULL_GEMM = 0, 1, 2, 3
 PATHS = {"staged": PATH_STAGED, "fused": PATH_FUSED, "line_gemm": PATH_LINE_GEMM, "full_gemm": PATH_FULL_GEMM}
+PSF_COLLINEAR, PSF_TENSOR = 0, 1
+PSF_MODELS = {"collinear": PSF_COLLINEAR, "tensor": PSF_TENSOR}
 
 
 class Geometry(C.Structure):
@@ -97,6 +99,9 @@ PROTOTYPES = {
     "mpi_ffl_apply_stage_zdrive": (C.c_int, [H, C.c_int32, C.c_int32, FP, FP, FP]),
     "mpi_ffl_set_gain": (C.c_int, [H, C.POINTER(C.c_float)]),
     "mpi_ffl_set_psf_fwhm": (C.c_int, [H, C.c_double]),
+    "mpi_ffl_set_psf_model": (C.c_int, [H, C.c_int32]),
+    "mpi_ffl_get_psf_model": (C.c_int, [H]),
+    "mpi_ffl_set_coil_map": (C.c_int, [H, FP]),
     "mpi_ffl_sync_check": (C.c_int, [H, ST]),
     "mpi_ffl_forward": (C.c_int, [H, FP, FP, ST]),
     "mpi_ffl_adjoint": (C.c_int, [H, FP, FP, ST]),
@@ -123,7 +128,8 @@ PROTOTYPES = {
 }
 
 KERNEL_KINDS = ["transpose", "project", "backproject", "psf_fwd", "psf_adj", "resample_fwd", "resample_adj",
-                "dft_fwd", "dft_adj", "tc_fwd", "tc_adj", "solver", "gemm_fwd", "gemm_adj", "zdrive"]
+                "dft_fwd", "dft_adj", "tc_fwd", "tc_adj", "solver", "gemm_fwd", "gemm_adj", "zdrive",
+                "tensor", "coil"]
 
 _lib = None
 

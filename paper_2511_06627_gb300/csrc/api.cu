@@ -360,7 +360,7 @@ void release(mpi_ffl_handle *h) {
                     h->t_csr, h->t_tw1, h->t_tw2_ro, h->t_tw2_qr, h->t_dgam, h->t_dgam_unit, h->t_groups, h->w_volT,
                     h->w_proj, h->w_fine, h->w_sig, h->w_data, h->w_vol2, h->w_red, h->w_scal,
                     h->s_xp, h->s_y, h->s_g, h->s_r, h->s_hist, h->s_flags, h->tc_twb, h->t_agroups,
-                    h->t_tnf, h->t_vr, h->w_err};
+                    h->t_tnf, h->t_vr, h->w_err, h->t_coil, h->w_projc};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (auto &r : h->prof_rec) {
@@ -476,6 +476,16 @@ void stage_pt(mpi_ffl_handle *h, const float *proj, float *x, cudaStream_t st) {
 void line_forward_impl(mpi_ffl_handle *h, const float *proj, float *b, const float *htab, const float *gain,
                        cudaStream_t st) {
     const Dims &d = h->d;
+    if (h->psf_model == MPI_FFL_PSF_TENSOR) {
+        // slices coupled by the tensor PSF; the coil map and the gains are applied inside
+        TIMED(MPI_FFL_K_TENSOR, ten_forward(h, proj, h->t_coil, b, st));
+        check_launch(h, "tensor forward");
+        return;
+    }
+    if (h->t_coil) {  // B: the coil map before the PSF
+        TIMED(MPI_FFL_K_COIL, launch_coil_pad(proj, h->t_coil, h->w_projc, (long long)d.M * d.Nz, d.Nz, d.N, d.N, st));
+        proj = h->w_projc;
+    }
     int path = h->path;
     if (path == MPI_FFL_PATH_FULL_GEMM && htab != h->t_htab) path = MPI_FFL_PATH_LINE_GEMM;  // other taps
     if (path == MPI_FFL_PATH_FULL_GEMM) {
@@ -508,8 +518,8 @@ void forward_impl(mpi_ffl_handle *h, const float *x, float *b, const float *htab
     line_forward_impl(h, h->w_proj, b, htab, gain, st);
 }
 
-// blockdiag(A_DC)^T: data -> projections
-void line_adjoint_impl(mpi_ffl_handle *h, const float *b, float *proj, cudaStream_t st) {
+// blockdiag(A_DC)^T without B's coil map: data -> projections
+void line_adjoint_body(mpi_ffl_handle *h, const float *b, float *proj, cudaStream_t st) {
     const Dims &d = h->d;
     if (h->path == MPI_FFL_PATH_FULL_GEMM) {
         TIMED(MPI_FFL_K_GEMM_ADJ, col_adjoint(h, b, true, h->t_gain, proj, st));
@@ -531,6 +541,21 @@ void line_adjoint_impl(mpi_ffl_handle *h, const float *b, float *proj, cudaStrea
     }
     TIMED(MPI_FFL_K_PSF_ADJ, launch_psf_adj(h->w_fine, h->t_htab, proj, d, st));
     check_launch(h, "psf_adj");
+}
+
+// blockdiag(A_DC)^T: data -> projections
+void line_adjoint_impl(mpi_ffl_handle *h, const float *b, float *proj, cudaStream_t st) {
+    const Dims &d = h->d;
+    if (h->psf_model == MPI_FFL_PSF_TENSOR) {
+        TIMED(MPI_FFL_K_TENSOR, ten_adjoint(h, b, h->t_coil, proj, st));
+        check_launch(h, "tensor adjoint");
+        return;
+    }
+    line_adjoint_body(h, b, proj, st);
+    if (h->t_coil) {  // B^T: the coil map after the PSF's transpose (in place)
+        TIMED(MPI_FFL_K_COIL, launch_coil_pad(proj, h->t_coil, proj, (long long)d.M * d.Nz, d.Nz, d.N, d.N, st));
+        check_launch(h, "coil");
+    }
 }
 
 void adjoint_impl(mpi_ffl_handle *h, const float *b, float *x, cudaStream_t st) {
@@ -763,7 +788,7 @@ extern "C" int mpi_ffl_get_sizes(const mpi_ffl_handle *h, mpi_ffl_sizes *o) {
     return MPI_FFL_OK;
 }
 
-extern "C" int mpi_ffl_set_precision(mpi_ffl_handle *h, int32_t precision) {
+static int set_precision_impl(mpi_ffl_handle *h, int32_t precision) {
     if (!h) return MPI_FFL_ERR_INVALID_ARG;
     if (precision < MPI_FFL_PREC_FP32 || precision > MPI_FFL_PREC_TF32) {
         h->err = "unknown precision";
@@ -793,7 +818,7 @@ extern "C" int mpi_ffl_set_precision(mpi_ffl_handle *h, int32_t precision) {
     return MPI_FFL_OK;
 }
 
-extern "C" int mpi_ffl_set_path(mpi_ffl_handle *h, int32_t path) {
+static int set_path_impl(mpi_ffl_handle *h, int32_t path) {
     if (!h) return MPI_FFL_ERR_INVALID_ARG;
     if (path < MPI_FFL_PATH_STAGED || path > MPI_FFL_PATH_FULL_GEMM) {
         h->err = "unknown path";
@@ -819,6 +844,68 @@ extern "C" int mpi_ffl_set_path(mpi_ffl_handle *h, int32_t path) {
                    : keep_tf32                 ? MPI_FFL_PREC_TF32
                                                : MPI_FFL_PREC_BF16X3;
     return MPI_FFL_OK;
+}
+
+// the tensor-PSF tables hold split operands of the handle's precision
+static int refresh_tensor(mpi_ffl_handle *h, int rc) {
+    if (rc != MPI_FFL_OK || h->psf_model != MPI_FFL_PSF_TENSOR) return rc;
+    return guarded(h, [&]() {
+        CK(cudaDeviceSynchronize());
+        const int r = ten_refresh(h, false);
+        if (r != MPI_FFL_OK) h->err = "rebuilding the tensor-PSF operands failed";
+        return r;
+    });
+}
+
+extern "C" int mpi_ffl_set_precision(mpi_ffl_handle *h, int32_t precision) {
+    return refresh_tensor(h, set_precision_impl(h, precision));
+}
+
+extern "C" int mpi_ffl_set_path(mpi_ffl_handle *h, int32_t path) { return refresh_tensor(h, set_path_impl(h, path)); }
+
+extern "C" int mpi_ffl_set_psf_model(mpi_ffl_handle *h, int32_t model) {
+    return guarded(h, [&]() {
+        if (model != MPI_FFL_PSF_COLLINEAR && model != MPI_FFL_PSF_TENSOR) {
+            h->err = "unknown PSF model";
+            return MPI_FFL_ERR_INVALID_ARG;
+        }
+        CK(cudaDeviceSynchronize());
+        if (model == MPI_FFL_PSF_TENSOR && !ten_ready(h)) {
+            if (!h->col_state) col_init(h);
+            const int rc = ten_init(h);
+            if (rc != MPI_FFL_OK) {
+                h->err = rc == MPI_FFL_ERR_UNSUPPORTED
+                             ? "the tensor PSF needs the collapsed line operator, which this shape does not support"
+                             : "building the tensor-PSF operator failed";
+                return rc;
+            }
+        }
+        h->psf_model = model;
+        return MPI_FFL_OK;
+    });
+}
+
+extern "C" int mpi_ffl_get_psf_model(const mpi_ffl_handle *h) { return h ? h->psf_model : MPI_FFL_ERR_INVALID_ARG; }
+
+extern "C" int mpi_ffl_set_coil_map(mpi_ffl_handle *h, const float *b_zu) {
+    return guarded(h, [&]() {
+        const Dims &d = h->d;
+        CK(cudaDeviceSynchronize());
+        if (!b_zu) {
+            if (h->t_coil) CK(cudaFree(h->t_coil));
+            h->t_coil = nullptr;
+            return MPI_FFL_OK;
+        }
+        for (int64_t k = 0; k < (int64_t)d.Nz * d.N; ++k)
+            if (!std::isfinite(b_zu[k])) {
+                h->err = "coil map holds a non-finite value";
+                return MPI_FFL_ERR_INVALID_ARG;
+            }
+        if (!h->t_coil) dev_alloc(h, &h->t_coil, (size_t)d.Nz * d.N);
+        if (!h->w_projc) dev_alloc(h, &h->w_projc, (size_t)d.M * d.Nz * d.N);
+        CK(cudaMemcpy(h->t_coil, b_zu, sizeof(float) * d.Nz * d.N, cudaMemcpyHostToDevice));
+        return MPI_FFL_OK;
+    });
 }
 
 extern "C" int mpi_ffl_get_path(const mpi_ffl_handle *h) { return h ? h->path : MPI_FFL_ERR_INVALID_ARG; }
@@ -861,7 +948,13 @@ extern "C" int mpi_ffl_set_psf_fwhm(mpi_ffl_handle *h, double fwhm) {
         if (had && !col_supported(h) && (h->path == MPI_FFL_PATH_LINE_GEMM || h->path == MPI_FFL_PATH_FULL_GEMM)) {
             h->path = MPI_FFL_PATH_STAGED;
             h->precision = MPI_FFL_PREC_FP32;
+            h->psf_model = MPI_FFL_PSF_COLLINEAR;
             h->err = "collapsed operator could not be rebuilt; fell back to the staged path";
+            return MPI_FFL_ERR_OOM;
+        }
+        if (h->psf_model == MPI_FFL_PSF_TENSOR && ten_init(h) != MPI_FFL_OK) {
+            h->psf_model = MPI_FFL_PSF_COLLINEAR;
+            h->err = "tensor-PSF operator could not be rebuilt; fell back to the collinear PSF";
             return MPI_FFL_ERR_OOM;
         }
         return MPI_FFL_OK;
@@ -1145,6 +1238,10 @@ extern "C" int mpi_ffl_apply_stage(mpi_ffl_handle *h, int32_t stage, int32_t tra
 extern "C" int mpi_ffl_param_grad(mpi_ffl_handle *h, const float *d_x, const float *d_gb, float *d_g_gain,
                                   float *d_g_fwhm, void *stream) {
     return guarded(h, [&]() {
+        if (h->psf_model == MPI_FFL_PSF_TENSOR) {
+            h->err = "parameter gradients are built for the collinear PSF only";
+            return MPI_FFL_ERR_UNSUPPORTED;
+        }
         if (!d_x || !d_gb) {
             h->err = "NULL buffer";
             return MPI_FFL_ERR_INVALID_ARG;
@@ -1159,6 +1256,10 @@ extern "C" int mpi_ffl_param_grad(mpi_ffl_handle *h, const float *d_x, const flo
 extern "C" int mpi_ffl_param_grad_proj(mpi_ffl_handle *h, const float *d_proj, const float *d_gb, float *d_g_gain,
                                        float *d_g_fwhm, void *stream) {
     return guarded(h, [&]() {
+        if (h->psf_model == MPI_FFL_PSF_TENSOR) {
+            h->err = "parameter gradients are built for the collinear PSF only";
+            return MPI_FFL_ERR_UNSUPPORTED;
+        }
         if (!d_proj || !d_gb) {
             h->err = "NULL buffer";
             return MPI_FFL_ERR_INVALID_ARG;

@@ -172,7 +172,8 @@ extern "C" int mpi_ffl_job_step(mpi_ffl_job *const *jobs, int32_t n, void *strea
         if (!j) return MPI_FFL_ERR_INVALID_ARG;
         if (j->k > j->iters) continue;  // iteration budget used up
         all.push_back(j);
-        if (j->h->path == MPI_FFL_PATH_FULL_GEMM && col_supported(j->h) && project_batch_ok(j->h->d.N))
+        if (j->h->path == MPI_FFL_PATH_FULL_GEMM && col_supported(j->h) && project_batch_ok(j->h->d.N) &&
+            j->h->psf_model == MPI_FFL_PSF_COLLINEAR && !j->h->t_coil)
             batch.push_back(j);
         else single.push_back(j);
     }

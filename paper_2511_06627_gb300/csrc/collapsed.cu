@@ -37,6 +37,7 @@ constexpr int kBM = 128;     // rows per tile (MMA M)
 constexpr int kBK = 64;      // K per pipeline stage
 constexpr int kProd = 128;   // producer threads (one per row)
 constexpr uint32_t kWait = 1u << 24;
+constexpr uint32_t kWaitSleep = 1u << 22;  // polls of mbar_wait_sleep_bounded: over a second
 
 struct GemmArgs {
     const float *A;
@@ -59,6 +60,7 @@ struct GemmArgs {
     int tf32;            // 1: tf32 hi + lo operands (32 K elements per stage), 0: bf16 (64)
     int nacc;            // accumulators in TMEM: K chunk kc adds into accumulator kc % nacc
     int acc_stride;      // TMEM columns between accumulators (a multiple of 32, >= BN)
+    int b_tstride;       // K chunks per N tile in B's storage (0: nkc); B may be a K window of a table
 };
 
 // The tensor-core accumulation into TMEM is not round-to-nearest FP32, so its error
@@ -193,8 +195,14 @@ __device__ __forceinline__ void gemm_body(const GemmArgs &g, int mt, int nt, uin
         // split and store chunk kc into its stage; false if the stage never came free
         auto produce = [&](int kc, const AChunk &c) -> bool {
             const int s = kc % g.stages;
-            if (kc >= g.stages && !ptx::mbar_wait_bounded(&bars[g.stages + s], ((kc / g.stages) - 1) & 1, kWait))
-                return false;
+            if (kc >= g.stages) {
+                // one lane per warp polls; __syncwarp orders the warp's stores after its acquire
+                int fr = 1;
+                if (lane == 0) fr = ptx::mbar_wait_bounded(&bars[g.stages + s], ((kc / g.stages) - 1) & 1, kWait);
+                fr = __shfl_sync(0xffffffffu, fr, 0);
+                __syncwarp();
+                if (!fr) return false;
+            }
             uint8_t *sa = sm + s * stage;
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
@@ -233,7 +241,11 @@ __device__ __forceinline__ void gemm_body(const GemmArgs &g, int mt, int nt, uin
         const int row = 32 * (warp & 3) + lane;
         const int gm = mt * kBM + row;
         const int ar = gm < g.M ? __ldg(g.arow + gm) : -1;
-        if (ok && ptx::mbar_wait_bounded(&bars[2 * g.stages], 0, kWait)) {
+        int done = 0;
+        if (ok && lane == 0) done = ptx::mbar_wait_sleep_bounded(&bars[2 * g.stages], 0, kWaitSleep);
+        done = __shfl_sync(0xffffffffu, done, 0);
+        __syncwarp();
+        if (ok && done) {
             ptx::tc_fence_after();
             const int cr = gm < g.M ? __ldg(g.crow + gm) : -1;
             const float sc = (cr >= 0 && g.rscale) ? __ldg(g.rscale + ar / g.rdiv) : 1.f;
@@ -309,7 +321,7 @@ __device__ __forceinline__ void gemm_body(const GemmArgs &g, int mt, int nt, uin
     } else {
         // ------------------------------------------------------------ B loader
         if (lane == 0) {
-            const uint8_t *bt = g.B + (size_t)nt * g.nkc * 2 * bytesB;
+            const uint8_t *bt = g.B + (size_t)nt * (g.b_tstride ? g.b_tstride : g.nkc) * 2 * bytesB;
             for (int kc = 0; kc < g.nkc; ++kc) {
                 const int s = kc % g.stages;
                 if (kc >= g.stages && !ptx::mbar_wait_bounded(&bars[g.stages + s], ((kc / g.stages) - 1) & 1, kWait)) {
@@ -429,6 +441,8 @@ struct ColState {
     // per operand format (0 bf16, 1 tf32) and trajectory: forward / adjoint operands of
     // W (line) and W H (full)
     Packed evf_f[2][2], evf_a[2][2], full_f[2][2], full_a[2][2];
+    std::vector<double> W[2];           // S D_Gamma F V E per trajectory (2 n_b x N_e, double)
+    struct TensorState *ten = nullptr;  // slice-coupled operator of the tensor PSF
     int *rows[2] = {nullptr, nullptr};  // line indices of each trajectory
     int nrows[2] = {0, 0};
     int *err = nullptr;
@@ -647,6 +661,7 @@ void col_init(mpi_ffl_handle *h) {
         if (!mk(s->evf_f, Wr, R, d.Ne, pick_bn(R)) || !mk(s->evf_a, Wt, d.Ne, R, pick_bn(d.Ne)) ||
             !mk(s->full_f, WH, R, d.N, pick_bn(R)) || !mk(s->full_a, WHt, d.N, R, pick_bn(d.N)))
             return;
+        s->W[par] = std::move(Wr);
         // lines of this trajectory
         std::vector<int> rows;
         for (int m = 0; m < d.M; ++m)
@@ -665,9 +680,12 @@ void col_init(mpi_ffl_handle *h) {
     s->ok = true;
 }
 
+void ten_release(ColState *s);
+
 void col_release(mpi_ffl_handle *h) {
     ColState *s = cs(h);
     if (!s) return;
+    ten_release(s);
     for (int p = 0; p < 2; ++p) {
         for (int f = 0; f < 2; ++f)
             for (Packed *pk : {&s->evf_f[f][p], &s->evf_a[f][p], &s->full_f[f][p], &s->full_a[f][p]})
@@ -753,6 +771,456 @@ void col_batch_launch(const void *dargs, const int4 *ditems, int n_items, size_t
 
 void col_batch_init() {
     cudaFuncSetAttribute(k_gemm_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+}
+
+// ============================================================ tensor PSF (slices coupled)
+// With the in-plane tensor PSF (Appendix B, Eq. (31): an x drive read by a collinear
+// coil takes h_uu(u, z) = 3 [L'(xi) u^2/rho^2 + (L(xi)/xi) z^2/rho^2], xi = rho / a) the
+// PSF-convolved projection of line l mixes every slice z': c_l = sum_z' H_{l-z'} b.p_z',
+// with H_d[e][i] = h_uu(u_lo + e/Q - i, d). Folded with the line operator W_par of the
+// line's trajectory, line l's data are
+//     data[m][l] = g_m sum_z' W_{par(l), l-z'} (b . p)[m][z'],    W_{par,d} = W_par H_d,
+// one 2 n_b x N matrix per trajectory and slice offset (H_d is even in d). Stacked by
+// offset, T_par[t] = W_{par, Nz-1-t} (t = 0 .. 2 Nz - 2), line l is one GEMM whose K
+// runs over all slices (z', i) and whose B is the window t = Nz-1-l .. 2Nz-2-l of
+// T_par; its rows are the angles. The transpose is one GEMM per slice z' whose K runs
+// over all lines (l, o): B is the window t = Nz-1-z' .. 2Nz-2-z' of Tadj_s[t] =
+// W_{par(l), t-(Nz-1)}^T, where line l = z' + t - (Nz-1) has parity (s + t - Nz + 1) & 1
+// for slices of parity s.
+//
+// The rows of one such GEMM are the M angles only, so J = 128 / M lines of one
+// trajectory share a problem: line l + step j (step = 2 with zig-zag, else 1) reads the
+// window of line l shifted by step j slices, which is the same window applied to the
+// projection shifted by step j slices. Row (j, m) of the problem whose last line is
+// l_J reads the coil-weighted projection, padded with step (J - 1) zero slices in
+// front, from slice step (j + J - J_g) on; the window starts at t = Nz - 1 - l_J and
+// spans Nz + step (J - 1) slices. The tables carry step (J - 1) zero slices at both
+// ends so that a partial group keeps the same extent (its missing rows write
+// nothing). The transpose groups slices the same way.
+namespace {
+
+constexpr int kTenSplitK = 4096; // K per problem at most (64 bf16 chunks: 32 per accumulator)
+
+// N tile: the fewest tiles of at most 128 columns (two TMEM accumulators per block),
+// rounded up to 32 columns
+int ten_bn(int Nv) {
+    const int tiles = (Nv + 127) / 128;
+    return std::min(128, ((Nv + tiles - 1) / tiles + 31) / 32 * 32);
+}
+
+struct TensorState {
+    int fmt = -1;              // operand format of the packed tables (0 bf16, 1 tf32)
+    Packed fwd[2], adj[2];     // T per trajectory (forward), Tadj per slice parity (adjoint)
+    int Np = 0, Op = 0;        // K per slice (forward) and per line (adjoint), multiples of 64
+    int step = 1, J = 1;       // line step of one trajectory; lines per problem
+    int Zp = 0, P0 = 0;        // padded slices per angle (a multiple of step), leading zeros
+    int Tpre = 0;              // zero offsets in front of and behind each table (step (J - 1))
+    double *Wd = nullptr;      // [n_par][Nz][2 n_b][N], offsets d >= 0
+    float *a_in = nullptr;     // [M][Zp][Np] coil-weighted projections, padded
+    float *a_data = nullptr;   // [M][Zp][Op] data rows, padded
+    int nsplit[2] = {1, 1};    // K splits of the forward and adjoint problems
+    int ksplit[2] = {0, 0};    // K per split (a multiple of 64)
+    float *c_fwd = nullptr;    // [nsplit][M][Nz][2 n_b] partial sums
+    float *c_adj = nullptr;    // [nsplit][M][Nz][N] partial sums
+    int *idx = nullptr;        // per problem group: M J A rows, then M J C rows
+    GemmArgs *dargs = nullptr; // forward problems, then adjoint problems
+    int n_prob_f = 0;
+    int4 *ditems = nullptr;    // forward items, then adjoint items
+    int n_items_f = 0, n_items_a = 0;
+    size_t smem[2] = {0, 0};   // dynamic shared memory of the forward and adjoint launches
+};
+
+// W_{par,d}[o][i] = sum_e W_par[o][e] g_d[e - D - Q i - kmin] in FP64 (g_d[k - kmin] =
+// h_uu(k / Q, d)). A block takes 8 rows o, 128 columns i, one offset and trajectory;
+// e runs in tiles of 256 staged in shared memory with the g values they meet.
+constexpr int kWdRows = 8, kWdCols = 128, kWdTile = 256;
+
+__global__ void __launch_bounds__(kWdCols) k_tensor_wd(const double *__restrict__ W, const double *__restrict__ g,
+                                                       double *__restrict__ Wd, int R, int Ne, int N, int Nz, int D,
+                                                       int Q, int kmin, int Lk) {
+    __shared__ double sw[kWdRows][kWdTile];
+    extern __shared__ double sg[];  // kWdTile + Q (kWdCols - 1) values of g_d
+    const int ncb = (N + kWdCols - 1) / kWdCols;
+    const int o0 = (blockIdx.x / ncb) * kWdRows, i0 = (blockIdx.x % ncb) * kWdCols;
+    const int d = blockIdx.y, par = blockIdx.z;
+    const int il = threadIdx.x, i = i0 + il;
+    const double *Wp = W + (size_t)par * R * Ne;
+    const double *gd = g + (size_t)d * Lk;
+    const int span = kWdTile + Q * (kWdCols - 1);
+    double acc[kWdRows];
+#pragma unroll
+    for (int r = 0; r < kWdRows; ++r) acc[r] = 0.0;
+    for (int e0 = 0; e0 < Ne; e0 += kWdTile) {
+        __syncthreads();
+        for (int t = threadIdx.x; t < kWdRows * kWdTile; t += blockDim.x) {
+            const int r = t / kWdTile, e = e0 + t % kWdTile;
+            sw[r][t % kWdTile] = (o0 + r < R && e < Ne) ? Wp[(size_t)(o0 + r) * Ne + e] : 0.0;
+        }
+        // k = e - D - Q i runs from kb (e = e0, i = i0 + kWdCols - 1) upwards
+        const int kb = e0 - D - Q * (i0 + kWdCols - 1) - kmin;
+        for (int t = threadIdx.x; t < span; t += blockDim.x) {
+            const int k = kb + t;
+            sg[t] = (k >= 0 && k < Lk) ? gd[k] : 0.0;
+        }
+        __syncthreads();
+        const double *gl = sg + Q * (kWdCols - 1 - il);
+        for (int e = 0; e < kWdTile; ++e) {
+            const double gv = gl[e];
+#pragma unroll
+            for (int r = 0; r < kWdRows; ++r) acc[r] = fma(sw[r][e], gv, acc[r]);
+        }
+    }
+    if (i < N)
+        for (int r = 0; r < kWdRows; ++r)
+            if (o0 + r < R) Wd[(((size_t)par * Nz + d) * R + o0 + r) * N + i] = acc[r];
+}
+
+// Forward table value T_par[n = o][k = (t + Tpre) Np + i] and adjoint table value
+// Tadj_s[n = i][k = (t + Tpre) Op + o], read from W_{par,|d|} (zero past |d| = Nz - 1).
+struct TenFwdSrc {
+    const double *Wd;
+    int par, Nz, R, N, Np, Tpre;
+    __device__ double operator()(int n, long long k) const {
+        const int ts = (int)(k / Np), i = (int)(k - (long long)ts * Np);
+        const int d = abs(Nz - 1 - (ts - Tpre));
+        if (i >= N || d > Nz - 1) return 0.0;
+        return Wd[(((size_t)par * Nz + d) * R + n) * N + i];
+    }
+};
+struct TenAdjSrc {
+    const double *Wd;
+    int s, n_par, Nz, R, N, Op, Tpre;
+    __device__ double operator()(int n, long long k) const {
+        const int ts = (int)(k / Op), o = (int)(k - (long long)ts * Op);
+        const int dd = ts - Tpre - (Nz - 1);
+        if (o >= R || abs(dd) > Nz - 1) return 0.0;
+        const int par = n_par == 1 ? 0 : ((dd + s) & 1);
+        return Wd[(((size_t)par * Nz + abs(dd)) * R + o) * N + n];
+    }
+};
+
+__device__ __forceinline__ uint16_t bf16_bits_dev(double x) {
+    const uint32_t u = __float_as_uint((float)x);
+    return (uint16_t)((u + 0x7FFFu + ((u >> 16) & 1u)) >> 16);
+}
+__device__ __forceinline__ uint32_t tf32_bits_dev(double x) {
+    return (__float_as_uint((float)x) + 0x1000u) & 0xFFFFE000u;
+}
+
+// pack_b on the device: one thread per (tile, chunk, row, K element) of the canonical
+// layout; hi = round(v), lo = round(v - hi), in bf16 or tf32.
+template <class Src>
+__global__ void k_pack_b(Src src, int Nv, long long Kv, int BN, int ntile, int nkc, int tf32, uint8_t *out) {
+    const int kpc = tf32 ? kBK / 2 : kBK;
+    const size_t blk = (size_t)BN * kBK * 2;
+    const size_t total = (size_t)ntile * nkc * BN * kpc;
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const int kl = (int)(idx % kpc);
+        size_t r = idx / kpc;
+        const int nl = (int)(r % BN);
+        r /= BN;
+        const int kc = (int)(r % nkc), t = (int)(r / nkc);
+        const int n = t * BN + nl;
+        const long long k = (long long)kc * kpc + kl;
+        const double v = (n < Nv && k < Kv) ? src(n, k) : 0.0;
+        uint8_t *hi = out + ((size_t)t * nkc + kc) * 2 * blk;
+        uint8_t *lo = hi + blk;
+        if (tf32) {
+            const uint32_t hb = tf32_bits_dev(v);
+            const uint32_t lb = tf32_bits_dev(v - (double)__uint_as_float(hb));
+            const size_t off = (size_t)(nl / 8) * 1024 + (kl / 4) * 128 + (nl % 8) * 16 + (kl % 4) * 4;
+            *reinterpret_cast<uint32_t *>(hi + off) = hb;
+            *reinterpret_cast<uint32_t *>(lo + off) = lb;
+        } else {
+            const uint16_t hb = bf16_bits_dev(v);
+            const uint16_t lb = bf16_bits_dev(v - (double)__uint_as_float((uint32_t)hb << 16));
+            const size_t off = (size_t)(nl / 8) * 1024 + (kl / 8) * 128 + (nl % 8) * 16 + (kl % 8) * 2;
+            *reinterpret_cast<uint16_t *>(hi + off) = hb;
+            *reinterpret_cast<uint16_t *>(lo + off) = lb;
+        }
+    }
+}
+
+template <class Src>
+bool pack_dev(Packed &p, Src src, int Nv, long long Kv, int BN, int tf32) {
+    const int kpc = tf32 ? kBK / 2 : kBK;
+    p.BN = BN;
+    p.ntile = (Nv + BN - 1) / BN;
+    p.nkc = (int)((Kv + kpc - 1) / kpc);
+    const size_t bytes = (size_t)p.ntile * p.nkc * 2 * BN * kBK * 2;
+    if (p.dev) cudaFree(p.dev);
+    p.dev = nullptr;
+    if (cudaMalloc((void **)&p.dev, bytes) != cudaSuccess) {
+        p.dev = nullptr;
+        cudaGetLastError();
+        return false;
+    }
+    k_pack_b<Src><<<4 * 152 * 8, 256>>>(src, Nv, Kv, BN, p.ntile, p.nkc, tf32, p.dev);
+    return cudaGetLastError() == cudaSuccess;
+}
+
+// h_uu at in-plane offset (u, z) voxels; a = FWHM / (2 x_h)
+double h_uu_host(double u, double z, double a) {
+    const double rho2 = u * u + z * z;
+    if (rho2 == 0.0) return 1.0;
+    const double xi = std::sqrt(rho2) / a;
+    double lx;  // L(xi) / xi
+    if (xi < 0.05) {
+        const double x2 = xi * xi;
+        lx = 1.0 / 3.0 - x2 / 45.0 + 2.0 * x2 * x2 / 945.0 - x2 * x2 * x2 / 4725.0;
+    } else {
+        lx = (1.0 / std::tanh(xi) - 1.0 / xi) / xi;
+    }
+    return 3.0 * (langevin_d1_host(xi) * u * u / rho2 + lx * z * z / rho2);
+}
+
+template <class T>
+bool talloc(T **p, size_t n) {
+    if (cudaMalloc((void **)p, std::max<size_t>(1, n) * sizeof(T)) != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return false;
+    }
+    return true;
+}
+
+// W_{par,d} for d = 0 .. Nz-1 from W_par and the tensor PSF (FP64, on the device).
+bool ten_build_wd(const mpi_ffl_handle *h, ColState *s, TensorState *t) {
+    const Dims &d = h->d;
+    const int R = 2 * d.nb;
+    const int kmin = -d.D - d.Q * (d.N - 1), Lk = d.Ne + d.Q * (d.N - 1);
+    const double a = h->fwhm / (2.0 * langevin_half_point_host());
+    std::vector<double> g((size_t)d.Nz * Lk);
+    for (int dz = 0; dz < d.Nz; ++dz)
+        for (int k = 0; k < Lk; ++k) g[(size_t)dz * Lk + k] = h_uu_host((double)(k + kmin) / d.Q, dz, a);
+    double *dW = nullptr, *dg = nullptr;
+    bool ok = talloc(&dW, (size_t)s->n_par * R * d.Ne) && talloc(&dg, g.size());
+    if (ok && !t->Wd) ok = talloc(&t->Wd, (size_t)s->n_par * d.Nz * R * d.N);
+    if (ok) {
+        for (int par = 0; par < s->n_par; ++par)
+            cudaMemcpy(dW + (size_t)par * R * d.Ne, s->W[par].data(), (size_t)R * d.Ne * sizeof(double),
+                       cudaMemcpyHostToDevice);
+        cudaMemcpy(dg, g.data(), g.size() * sizeof(double), cudaMemcpyHostToDevice);
+        const int ncb = (d.N + kWdCols - 1) / kWdCols;
+        const size_t smem = sizeof(double) * (kWdTile + d.Q * (kWdCols - 1));
+        if (smem > 48 * 1024) cudaFuncSetAttribute(k_tensor_wd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_tensor_wd<<<dim3(((R + kWdRows - 1) / kWdRows) * ncb, d.Nz, s->n_par), kWdCols, smem>>>(
+            dW, dg, t->Wd, R, d.Ne, d.N, d.Nz, d.D, d.Q, kmin, Lk);
+        ok = cudaDeviceSynchronize() == cudaSuccess;
+    }
+    if (dW) cudaFree(dW);
+    if (dg) cudaFree(dg);
+    cudaGetLastError();
+    return ok;
+}
+
+// Line (slice) groups of one trajectory (slice parity): first line and count.
+std::vector<int2> ten_groups(const Dims &d, int step, int J) {
+    std::vector<int2> g;
+    for (int p = 0; p < step; ++p)
+        for (int l = p; l < d.Nz; l += step * J) g.push_back(make_int2(l, std::min(J, (d.Nz - 1 - l) / step + 1)));
+    return g;
+}
+
+// Packed tables, problems and items for operand format fmt.
+bool ten_prepare(const mpi_ffl_handle *h, ColState *s, TensorState *t, int fmt) {
+    const Dims &d = h->d;
+    const int R = 2 * d.nb;
+    const int kpc = fmt ? kBK / 2 : kBK;
+    const long long tslices = 2LL * d.Nz - 1 + 2LL * t->Tpre;  // zero offsets at both ends
+    for (int par = 0; par < s->n_par; ++par)
+        if (!pack_dev(t->fwd[par], TenFwdSrc{t->Wd, par, d.Nz, R, d.N, t->Np, t->Tpre}, R, tslices * t->Np,
+                      ten_bn(R), fmt))
+            return false;
+    for (int sp = 0; sp < s->n_par; ++sp)
+        if (!pack_dev(t->adj[sp], TenAdjSrc{t->Wd, sp, s->n_par, d.Nz, R, d.N, t->Op, t->Tpre}, d.N,
+                      tslices * t->Op, ten_bn(d.N), fmt))
+            return false;
+    if (cudaDeviceSynchronize() != cudaSuccess) return false;
+    const std::vector<int2> groups = ten_groups(d, t->step, t->J);
+    const int rows = d.M * t->J;
+    std::vector<int> idx(groups.size() * 2 * 2 * rows);
+    std::vector<GemmArgs> args;
+    std::vector<int4> items[2];
+    const int mtiles = (rows + kBM - 1) / kBM;
+    const int span = d.Nz + t->step * (t->J - 1);  // window slices (lines)
+    // both launches with the larger footprint: one block per SM measured faster than two
+    // for these long-K problems, whose producers are bound by the latency of their A loads
+    {
+        int st0 = 0, st1 = 0;
+        t->smem[0] = t->smem[1] = std::max(smem_for(t->fwd[0].BN, st0), smem_for(t->adj[0].BN, st1));
+    }
+    for (int dir = 0; dir < 2; ++dir) {
+        const int per = dir ? t->Op : t->Np;  // K per line (adjoint) or per slice (forward)
+        const int BN = dir ? t->adj[0].BN : t->fwd[0].BN;
+        const size_t blk = (size_t)BN * kBK * 2;
+        int stages = 0;
+        smem_for(BN, stages);
+        const int base = (int)args.size();
+        for (size_t gi = 0; gi < groups.size(); ++gi) {
+            const int l0 = groups[gi].x, Jg = groups[gi].y;
+            const int llast = l0 + t->step * (Jg - 1);
+            int *ar = idx.data() + ((size_t)dir * groups.size() + gi) * 2 * rows;
+            int *cr = ar + rows;
+            for (int j = 0; j < t->J; ++j)
+                for (int m = 0; m < d.M; ++m) {
+                    // row (j, m): the padded block of angle m from slice step (j + J - Jg)
+                    const int jj = std::min(j, Jg - 1);
+                    ar[j * d.M + m] = m * (t->Zp / t->step) + jj + t->J - Jg;
+                    cr[j * d.M + m] = j < Jg ? m * d.Nz + l0 + t->step * j : -1;
+                }
+            const int *dar = t->idx + (ar - idx.data());
+            const int *dcr = t->idx + (cr - idx.data());
+            // the window starts at t = Nz - 1 - llast (table slice + Tpre)
+            const long long kwin = (long long)(d.Nz - 1 - llast + t->Tpre) * per;
+            const Packed &B = dir ? t->adj[s->n_par == 1 ? 0 : (l0 & 1)] : t->fwd[s->n_par == 1 ? 0 : (l0 & 1)];
+            for (int ks = 0; ks < t->nsplit[dir]; ++ks) {
+                const int k0 = ks * t->ksplit[dir];
+                const int kn = std::min(t->ksplit[dir], span * per - k0);
+                GemmArgs g{};
+                g.A = (dir ? t->a_data : t->a_in) + k0;
+                g.lda = (int64_t)t->step * per;
+                g.Ka = kn;
+                g.arow = dar;
+                g.M = rows;
+                g.B = B.dev + (size_t)((kwin + k0) / kpc) * 2 * blk;
+                g.BN = BN;
+                g.nkc = kn / kpc;
+                g.b_tstride = B.nkc;
+                g.C = (dir ? t->c_adj : t->c_fwd) + (size_t)ks * d.M * d.Nz * (dir ? d.N : R);
+                g.ldc = dir ? d.N : R;
+                g.crow = dcr;
+                g.Nc = dir ? d.N : R;
+                g.rscale = h->t_gain;
+                g.rdiv = t->Zp / t->step;  // A row / rdiv = angle
+                g.prec = h->precision;
+                g.tf32 = fmt;
+                g.stages = stages;
+                set_accumulators(g);
+                g.err = s->err;
+                g.done = nullptr;
+                const int pi = (int)args.size() - base;
+                args.push_back(g);
+                for (int mt = 0; mt < mtiles; ++mt)
+                    for (int nt = 0; nt < B.ntile; ++nt) items[dir].push_back(make_int4(pi, mt, nt, 0));
+            }
+        }
+        if (dir == 0) t->n_prob_f = (int)args.size();
+    }
+    if (cudaMemcpy(t->idx, idx.data(), idx.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess) return false;
+    // the adjoint items index their problems from the adjoint part of the arguments
+    t->n_items_f = (int)items[0].size();
+    t->n_items_a = (int)items[1].size();
+    items[0].insert(items[0].end(), items[1].begin(), items[1].end());
+    if (t->dargs) cudaFree(t->dargs);
+    if (t->ditems) cudaFree(t->ditems);
+    t->dargs = nullptr;
+    t->ditems = nullptr;
+    if (!talloc(&t->dargs, args.size()) || !talloc(&t->ditems, items[0].size())) return false;
+    cudaMemcpy(t->dargs, args.data(), args.size() * sizeof(GemmArgs), cudaMemcpyHostToDevice);
+    cudaMemcpy(t->ditems, items[0].data(), items[0].size() * sizeof(int4), cudaMemcpyHostToDevice);
+    t->fmt = fmt;
+    return cudaGetLastError() == cudaSuccess;
+}
+
+}  // namespace
+
+void ten_release(ColState *s) {
+    TensorState *t = s->ten;
+    if (!t) return;
+    for (int p = 0; p < 2; ++p)
+        for (Packed *pk : {&t->fwd[p], &t->adj[p]})
+            if (pk->dev) cudaFree(pk->dev);
+    for (void *p : {(void *)t->Wd, (void *)t->a_in, (void *)t->a_data, (void *)t->c_fwd, (void *)t->c_adj,
+                    (void *)t->idx, (void *)t->dargs, (void *)t->ditems})
+        if (p) cudaFree(p);
+    delete t;
+    s->ten = nullptr;
+}
+
+int ten_init(mpi_ffl_handle *h) {
+    ColState *s = cs(h);
+    if (!s || !s->ok || s->W[0].empty()) return MPI_FFL_ERR_UNSUPPORTED;
+    const Dims &d = h->d;
+    const int R = 2 * d.nb;
+    ten_release(s);
+    TensorState *t = new TensorState();
+    s->ten = t;
+    t->Np = (d.N + kBK - 1) / kBK * kBK;
+    t->Op = (R + kBK - 1) / kBK * kBK;
+    t->step = s->n_par;
+    t->J = std::max(1, std::min(kBM / d.M, (d.Nz + t->step - 1) / t->step));
+    t->P0 = t->step * (t->J - 1);
+    t->Tpre = t->step * (t->J - 1);
+    t->Zp = (d.Nz + 2 * t->P0 + t->step - 1) / t->step * t->step;
+    // the accumulation in TMEM is not round-to-nearest, so its error grows with the MMAs
+    // chained into one accumulator: K is split into parts of at most kTenSplitK, summed
+    // in FP32 afterwards (in a fixed order)
+    const int span = d.Nz + t->step * (t->J - 1);
+    for (int dir = 0; dir < 2; ++dir) {
+        const int K = span * (dir ? t->Op : t->Np);
+        t->nsplit[dir] = (K + kTenSplitK - 1) / kTenSplitK;
+        t->ksplit[dir] = ((K + t->nsplit[dir] - 1) / t->nsplit[dir] + kBK - 1) / kBK * kBK;
+        t->nsplit[dir] = (K + t->ksplit[dir] - 1) / t->ksplit[dir];
+    }
+    const size_t ng = ten_groups(d, t->step, t->J).size();
+    bool ok = talloc(&t->a_in, (size_t)d.M * t->Zp * t->Np) && talloc(&t->a_data, (size_t)d.M * t->Zp * t->Op) &&
+              talloc(&t->c_fwd, (size_t)t->nsplit[0] * d.M * d.Nz * R) &&
+              talloc(&t->c_adj, (size_t)t->nsplit[1] * d.M * d.Nz * d.N) &&
+              talloc(&t->idx, ng * 2 * 2 * (size_t)d.M * t->J);
+    if (ok) {  // the padding slices stay zero: only the interior is ever written
+        ok = cudaMemset(t->a_in, 0, (size_t)d.M * t->Zp * t->Np * sizeof(float)) == cudaSuccess &&
+             cudaMemset(t->a_data, 0, (size_t)d.M * t->Zp * t->Op * sizeof(float)) == cudaSuccess;
+    }
+    ok = ok && ten_build_wd(h, s, t) && ten_prepare(h, s, t, h->precision == MPI_FFL_PREC_TF32 ? 1 : 0);
+    if (!ok) {
+        ten_release(s);
+        cudaGetLastError();
+        return MPI_FFL_ERR_OOM;
+    }
+    cudaFuncSetAttribute(k_gemm_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    return MPI_FFL_OK;
+}
+
+bool ten_ready(const mpi_ffl_handle *h) {
+    const ColState *s = cs(h);
+    return s && s->ten;
+}
+
+int ten_refresh(mpi_ffl_handle *h, bool psf_changed) {
+    ColState *s = cs(h);
+    if (!s || !s->ten) return MPI_FFL_OK;
+    TensorState *t = s->ten;
+    const int fmt = h->precision == MPI_FFL_PREC_TF32 ? 1 : 0;
+    if (psf_changed) {
+        if (!ten_build_wd(h, s, t)) return MPI_FFL_ERR_CUDA;
+        t->fmt = -1;
+    }
+    if (t->fmt != fmt && !ten_prepare(h, s, t, fmt)) return MPI_FFL_ERR_OOM;
+    return MPI_FFL_OK;
+}
+
+// proj -> data: coil-weighted, padded A rows; the GEMM problems; sum of the K splits
+void ten_forward(mpi_ffl_handle *h, const float *proj, const float *coil, float *data, cudaStream_t st) {
+    ColState *s = cs(h);
+    TensorState *t = s->ten;
+    const Dims &d = h->d;
+    const long long rows = (long long)d.M * d.Nz;
+    launch_coil_pad(proj, coil, t->a_in, rows, d.Nz, d.N, t->Np, st, 1, 0, t->Zp, t->P0);
+    k_gemm_batch<<<t->n_items_f, kGemmThreads, t->smem[0], st>>>(t->dargs, t->ditems);
+    launch_coil_pad(t->c_fwd, nullptr, data, rows, d.Nz, 2 * d.nb, 2 * d.nb, st, t->nsplit[0], rows * 2 * d.nb);
+}
+
+// data -> proj: padded data rows; the GEMM problems; sum of the K splits, coil weighting
+void ten_adjoint(mpi_ffl_handle *h, const float *data, const float *coil, float *proj, cudaStream_t st) {
+    ColState *s = cs(h);
+    TensorState *t = s->ten;
+    const Dims &d = h->d;
+    const long long rows = (long long)d.M * d.Nz;
+    launch_coil_pad(data, nullptr, t->a_data, rows, d.Nz, 2 * d.nb, t->Op, st, 1, 0, t->Zp, t->P0);
+    k_gemm_batch<<<t->n_items_a, kGemmThreads, t->smem[1], st>>>(t->dargs + t->n_prob_f, t->ditems + t->n_items_f);
+    launch_coil_pad(t->c_adj, coil, proj, rows, d.Nz, d.N, d.N, st, t->nsplit[1], rows * d.N);
 }
 
 }  // namespace mpiffl

@@ -25,6 +25,16 @@ int col_batch_prepare(mpi_ffl_handle *const *hs, const float *const *in, float *
 void col_batch_launch(const void *dargs, const int4 *ditems, int n_items, size_t smem, cudaStream_t st);
 void col_batch_init();
 
+// Slice-coupled operator of the tensor PSF (Appendix B, Eq. (31)): per-offset folded
+// line operators W_par H_d stacked by offset, one GEMM per line (forward) or per slice
+// (adjoint). ten_init builds the tables (FP64 fold, then split operands for the
+// handle's precision); ten_refresh rebuilds them after a PSF or precision change.
+int ten_init(mpi_ffl_handle *h);
+bool ten_ready(const mpi_ffl_handle *h);
+int ten_refresh(mpi_ffl_handle *h, bool psf_changed);
+void ten_forward(mpi_ffl_handle *h, const float *proj, const float *coil, float *data, cudaStream_t st);
+void ten_adjoint(mpi_ffl_handle *h, const float *data, const float *coil, float *proj, cudaStream_t st);
+
 // host-side model pieces shared with the table builders (api.cu)
 double langevin_d1_host(double x);
 double langevin_half_point_host();

@@ -157,6 +157,10 @@ struct mpi_ffl_handle {
     cudaEvent_t hs_ready[2] = {}, hs_free[2] = {};
     int hs_slot = 0;
     int host_overlap = 0;                   // mpi_ffl_set_host_overlap
+    // PSF model (MPI_FFL_PSF_*) and receive-coil map b[z][u] (NULL: uniform coil)
+    int psf_model = 0;
+    float *t_coil = nullptr;    // N_z N
+    float *w_projc = nullptr;   // M N_z N: coil-weighted projections (collinear model)
     // z-drive scan (k_zdrive.cu): tables and workspace, built on first use
     int z_ready = 0;
     int *tz_n0 = nullptr, *tz_plo = nullptr, *tz_phi = nullptr, *tz_tap_ptr = nullptr;
@@ -294,6 +298,11 @@ void launch_zdft_fwd(const float *cz, const ZTables &T, const float *gain, const
 void launch_zdft_adj(const float *data, const float *tw1, const float2 *tw2_qr, const float2 *dgam,
                      const ZTables &T, const float *gain, float *coef, float *cz, const Dims &d, int zigzag,
                      cudaStream_t st);
+// coil weighting and row padding (k_coil.cu): out[r'][c] = b[r mod Nz][c] sum_p in[p][r][c],
+// c < ncols (nparts partial sums part_stride floats apart); zero up to stride. Output row
+// r' = (r / Nz) zp + p0 + r mod Nz (zp 0: Nz)
+void launch_coil_pad(const float *in, const float *coil, float *out, long long rows, int Nz, int ncols, int stride,
+                     cudaStream_t st, int nparts = 1, long long part_stride = 0, int zp = 0, int p0 = 0);
 size_t zdft_fwd_smem(const Dims &d);     // shared memory of the fused z forward
 int zsyn_ring(const Dims &d, int no);
 size_t zsyn_smem(const Dims &d, int no);

@@ -72,6 +72,16 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     return false;
 }
 
+// As mbar_wait_bounded, sleeping about 256 ns between polls: for long waits of many
+// threads, whose polling would otherwise crowd the load/store pipe.
+__device__ __forceinline__ bool mbar_wait_sleep_bounded(uint64_t *bar, uint32_t parity, uint32_t max_iter) {
+    for (uint32_t it = 0; it < max_iter; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        __nanosleep(256);
+    }
+    return false;
+}
+
 // ------------------------------------------------------------------ fences
 __device__ __forceinline__ void fence_proxy_async_smem() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");

@@ -332,6 +332,29 @@ class FFLOperator:
         check(self._lib.mpi_ffl_set_psf_fwhm(self._h, float(fwhm)), self._h)
         self.fwhm = float(fwhm)
 
+    def set_psf_model(self, model):
+        """PSF model of the x-drive operator: 'collinear' (1D L' along the drive axis, per
+        line) or 'tensor' (the in-plane tensor PSF of Appendix B, Eq. (31): every line reads
+        every slice). Selecting 'tensor' builds its per-offset operator on the device."""
+        if isinstance(model, str):
+            model = _lib.PSF_MODELS[model]
+        check(self._lib.mpi_ffl_set_psf_model(self._h, int(model)), self._h)
+
+    @property
+    def psf_model(self):
+        return int(self._lib.mpi_ffl_get_psf_model(self._h))
+
+    def set_coil_map(self, b):
+        """Receive-coil sensitivity b[z][u] (N_z x N, scanner coordinates, the same for every
+        angle) applied to each projection before the PSF; None restores a uniform coil."""
+        if b is None:
+            check(self._lib.mpi_ffl_set_coil_map(self._h, None), self._h)
+            return
+        arr = np.ascontiguousarray(np.asarray(b.cpu() if isinstance(b, torch.Tensor) else b, dtype=np.float32))
+        if arr.shape != (self.nz, self.nx):
+            raise ValueError(f"coil map must be {(self.nz, self.nx)}, got {arr.shape}")
+        check(self._lib.mpi_ffl_set_coil_map(self._h, arr.ctypes.data), self._h)
+
     def close(self):
         if getattr(self, "_h", None):
             self._lib.mpi_ffl_destroy(self._h)
