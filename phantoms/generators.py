@@ -161,3 +161,39 @@ def random_volume(nz, n, seed, dtype=np.float64):
 def random_data(shape, seed, dtype=np.float64):
     """Standard-normal real array of the given shape (e.g. interleaved complex data)."""
     return np.random.default_rng(seed).standard_normal(shape).astype(dtype)
+
+
+def sensitivity_series(nx, nz, amounts, seed=0, sigma=1.2):
+    """A stand-in for the paper's sensitivity phantom (Sec. 4.2, Figs. 4-5): point-like
+    samples of known iron amounts on one slice, plus void regions for the background.
+
+    Each sample is a Gaussian blob whose integral equals its amount. Samples sit on a
+    line through the middle slice, spaced evenly inside the inscribed cylinder.
+    Returns (volume float32 [nz][nx][nx], sample_boxes, void_boxes). Boxes are
+    (z0, z1, y0, y1, x0, x1), half-open. Each sample box is a cube of half-width 2
+    sigma around its sample. The five void boxes lie on slices a quarter of the
+    height away from the samples.
+    """
+    rng = np.random.default_rng(seed)
+    vol = np.zeros((nz, nx, nx), dtype=np.float64)
+    zc = nz // 2
+    yc = (nx - 1) / 2.0
+    k = len(amounts)
+    span = 0.55 * (nx / 2.0)
+    xs = np.linspace((nx - 1) / 2.0 - span, (nx - 1) / 2.0 + span, k)
+    h = max(1, int(np.ceil(2 * sigma)))
+    sample_boxes = []
+    for amt, xc in zip(amounts, xs):
+        c = (zc + rng.uniform(-0.3, 0.3), yc + rng.uniform(-0.3, 0.3), xc)
+        add_gaussian(vol, c, sigma, float(amt) / (2.0 * np.pi * sigma * sigma) ** 1.5)
+        iz, iy, ix = (int(round(v)) for v in c)
+        sample_boxes.append((iz - h, iz + h + 1, iy - h, iy + h + 1, ix - h, ix + h + 1))
+    w = max(2, nx // 16)
+    void_boxes = []
+    for j, zq in enumerate((nz // 4, nz // 4, 3 * nz // 4, 3 * nz // 4, nz // 4)):
+        ang = 2 * np.pi * j / 5
+        cy = int(round(yc + 0.3 * nx * np.sin(ang)))
+        cx = int(round((nx - 1) / 2.0 + 0.3 * nx * np.cos(ang)))
+        dz = max(1, nz // 16)
+        void_boxes.append((zq - dz, zq + dz, cy - w, cy + w, cx - w, cx + w))
+    return vol.astype(np.float32), sample_boxes, void_boxes
