@@ -256,6 +256,26 @@ int mpi_ffl_adjoint_zdrive(mpi_ffl_handle *h, const float *b_z_ri, float *x, voi
 int mpi_ffl_apply_stage_zdrive(mpi_ffl_handle *h, int32_t stage, int32_t transpose, const float *d_in,
                                float *d_out, void *stream);
 
+/* Detection-limit analysis (Sec. 4.2, Fig. 5), handle-free.
+ *
+ * mpi_ffl_box_stats: FP64 statistics of boxes of a volume d_vol (device, nz x ny x nx
+ * floats, x fastest). boxes: host array of n_boxes x 6 int32 (z0, z1, y0, y1, x0, x1),
+ * half-open and inside the volume. pooled = 0: out (host, n_boxes x 4 doubles) gets,
+ * per box, (voxel count, mean, mean absolute deviation about the mean, max); pooled = 1:
+ * one such row for all boxes taken together (the noise of Fig. 5 over void regions).
+ * Synchronous: waits for `stream`, which it uses for its two kernels and copies. It
+ * allocates a few bytes of device memory per call. The sums are in a fixed order:
+ * repeated calls give the same bits. MPI_FFL_ERR_INVALID_ARG for an empty box or one
+ * leaving the volume.
+ *
+ * mpi_ffl_detection_limit (host only): least-squares line values = a + s * amounts over
+ * n >= 2 samples; out (3 doubles) = (limit, s, a), limit = (k * noise - a) / s, NaN
+ * unless s > 0 (k = 3 in Fig. 5). MPI_FFL_ERR_INVALID_ARG when all amounts are equal. */
+int mpi_ffl_box_stats(const float *d_vol, int32_t nz, int32_t ny, int32_t nx, const int32_t *boxes, int32_t n_boxes,
+                      int32_t pooled, double *out, void *stream);
+int mpi_ffl_detection_limit(const double *amounts, const double *values, int32_t n, double noise, double k,
+                            double *out);
+
 /* on != 0: host inputs of forward/adjoint are copied on a stream of the handle that
  * waits only for the previous use of its (double-buffered) staging slot, so the copy
  * for the next call overlaps the work already queued on `stream`. The caller must

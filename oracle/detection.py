@@ -9,7 +9,9 @@ against its iron amount. Take the background noise as the mean absolute deviatio
 three times the noise.
 
 Readings (the paper describes the procedure in words):
-  - The image value of a sample is the largest reconstructed value in a box around it.
+  - The image value of a sample is the mean reconstructed value over a box around it
+    (an ROI mean, which stays linear in the amount when the reconstruction spreads a
+    sample over several voxels).
   - The noise is the mean absolute deviation about their mean of all voxels of the
     void boxes taken together.
   - The fit is ordinary least squares v = a + s * amount over the samples given.
@@ -49,7 +51,7 @@ def detection_limit(amounts, values, noise, k=3.0):
 
 def analyse(vol, sample_boxes, amounts, void_boxes, k=3.0):
     """Sample values, noise and the detection limit of one reconstruction."""
-    values = box_stats(vol, sample_boxes)[:, 3]
+    values = box_stats(vol, sample_boxes)[:, 1]
     noise = box_stats(vol, void_boxes, pooled=True)[0, 2]
     limit, s, a = detection_limit(amounts, values, noise, k)
     return dict(values=values, noise=noise, limit=limit, slope=s, intercept=a)

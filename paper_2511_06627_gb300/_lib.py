@@ -102,6 +102,9 @@ PROTOTYPES = {
     "mpi_ffl_set_psf_model": (C.c_int, [H, C.c_int32]),
     "mpi_ffl_get_psf_model": (C.c_int, [H]),
     "mpi_ffl_set_coil_map": (C.c_int, [H, FP]),
+    "mpi_ffl_box_stats": (C.c_int, [FP, C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_int32, C.c_int32,
+                                    C.c_void_p, ST]),
+    "mpi_ffl_detection_limit": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_double, C.c_double, C.c_void_p]),
     "mpi_ffl_sync_check": (C.c_int, [H, ST]),
     "mpi_ffl_forward": (C.c_int, [H, FP, FP, ST]),
     "mpi_ffl_adjoint": (C.c_int, [H, FP, FP, ST]),

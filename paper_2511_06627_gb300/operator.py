@@ -371,3 +371,36 @@ class FFLOperator:
 
     def __exit__(self, *a):
         self.close()
+
+
+def box_stats(vol, boxes, pooled=False):
+    """FP64 (count, mean, mean absolute deviation, max) of each box of a float32 CUDA volume
+    [nz][ny][nx] (or of all boxes together when pooled), as an [n][4] numpy array. Boxes
+    are (z0, z1, y0, y1, x0, x1), half-open (Sec. 4.2: sample values and background
+    noise of a reconstruction)."""
+    import numpy as np
+
+    if not (isinstance(vol, torch.Tensor) and vol.is_cuda and vol.dtype == torch.float32 and vol.is_contiguous()
+            and vol.dim() == 3):
+        raise TypeError("vol must be a contiguous float32 CUDA tensor [nz][ny][nx]")
+    b = np.ascontiguousarray(np.asarray(boxes, dtype=np.int32).reshape(-1, 6))
+    out = np.empty((1 if pooled else len(b), 4), dtype=np.float64)
+    nz, ny, nx = vol.shape
+    check(_lib.load().mpi_ffl_box_stats(_ptr(vol), nz, ny, nx, b.ctypes.data, len(b), int(bool(pooled)),
+                                        out.ctypes.data, _stream()))
+    return out
+
+
+def detection_limit(amounts, values, noise, k=3.0):
+    """Least-squares line values ~ a + s * amounts and the amount at which it reaches
+    k * noise (Sec. 4.2, Fig. 5): dict(limit, slope, intercept); limit NaN unless s > 0."""
+    import numpy as np
+
+    a = np.ascontiguousarray(np.asarray(amounts, dtype=np.float64))
+    v = np.ascontiguousarray(np.asarray(values, dtype=np.float64))
+    if a.shape != v.shape:
+        raise ValueError("amounts and values differ in length")
+    out = np.empty(3, dtype=np.float64)
+    check(_lib.load().mpi_ffl_detection_limit(a.ctypes.data, v.ctypes.data, len(a), float(noise), float(k),
+                                              out.ctypes.data))
+    return dict(limit=float(out[0]), slope=float(out[1]), intercept=float(out[2]))

@@ -167,11 +167,12 @@ def sensitivity_series(nx, nz, amounts, seed=0, sigma=1.2):
     """A stand-in for the paper's sensitivity phantom (Sec. 4.2, Figs. 4-5): point-like
     samples of known iron amounts on one slice, plus void regions for the background.
 
-    Each sample is a Gaussian blob whose integral equals its amount. Samples sit on a
-    line through the middle slice, spaced evenly inside the inscribed cylinder.
+    Each sample is a Gaussian blob whose integral equals its amount. Samples sit on the
+    middle slice, evenly spaced on a circle about the rotation axis (radius 0.45 N/2),
+    so that the rotating acquisition treats them alike.
     Returns (volume float32 [nz][nx][nx], sample_boxes, void_boxes). Boxes are
-    (z0, z1, y0, y1, x0, x1), half-open. Each sample box is a cube of half-width 2
-    sigma around its sample. The five void boxes lie on slices a quarter of the
+    (z0, z1, y0, y1, x0, x1), half-open. Each sample box is a cube of half-width
+    3 sigma + 1 around its sample. The five void boxes lie on slices a quarter of the
     height away from the samples.
     """
     rng = np.random.default_rng(seed)
@@ -179,12 +180,13 @@ def sensitivity_series(nx, nz, amounts, seed=0, sigma=1.2):
     zc = nz // 2
     yc = (nx - 1) / 2.0
     k = len(amounts)
-    span = 0.55 * (nx / 2.0)
-    xs = np.linspace((nx - 1) / 2.0 - span, (nx - 1) / 2.0 + span, k)
-    h = max(1, int(np.ceil(2 * sigma)))
+    rad = 0.45 * (nx / 2.0)
+    h = max(1, int(np.ceil(3 * sigma)) + 1)
     sample_boxes = []
-    for amt, xc in zip(amounts, xs):
-        c = (zc + rng.uniform(-0.3, 0.3), yc + rng.uniform(-0.3, 0.3), xc)
+    for s_, amt in enumerate(amounts):
+        phi = 2 * np.pi * s_ / k + 0.3
+        c = (zc + rng.uniform(-0.3, 0.3), yc + rad * np.sin(phi) + rng.uniform(-0.3, 0.3),
+             (nx - 1) / 2.0 + rad * np.cos(phi))
         add_gaussian(vol, c, sigma, float(amt) / (2.0 * np.pi * sigma * sigma) ** 1.5)
         iz, iy, ix = (int(round(v)) for v in c)
         sample_boxes.append((iz - h, iz + h + 1, iy - h, iy + h + 1, ix - h, ix + h + 1))
