@@ -696,7 +696,21 @@ def run_ours(args, cfg, rank, world, local_rank):
             z1.record(stream)
             torch.cuda.synchronize()
             z_ms[name] = z0.elapsed_time(z1)
+        # reconstruction from both scans: Eq. (26) on [A; A_z] (mpi_ffl_set_scans)
+        op.set_scans("xz")
+        b_xz = torch.cat([b, bz]).contiguous()
+        op.solve(b_xz, iters=2)
+        r0 = torch.cuda.Event(enable_timing=True)
+        r1 = torch.cuda.Event(enable_timing=True)
+        flush.zero_()
+        r0.record(stream)
+        op.solve(b_xz, iters=100, report=False)
+        r1.record(stream)
+        torch.cuda.synchronize()
+        recon_xz_s = r0.elapsed_time(r1) / 1e3
+        op.set_scans("x")
         result["dual_drive"] = {"pairs_per_s": 1e3 / dual_ms, "ms_per_pair": dual_ms, "z_drive_ms": z_ms,
+                                "recon_both_scans_s_per_100_iters": recon_xz_s,
                                 "x_drive_path": path, "z_drive_path": "FP32, E_z V_z B fused with S D F",
                                 "step": "[A; A_z] x then A^T b + A_z^T b_z"}
         # tensor PSF (Appendix B, Eq. (31)): every line reads every slice of its projection;

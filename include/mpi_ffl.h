@@ -248,6 +248,20 @@ int mpi_ffl_adjoint(mpi_ffl_handle *h, const float *b_ri, float *x, void *stream
 int mpi_ffl_forward_zdrive(mpi_ffl_handle *h, const float *x, float *b_z_ri, void *stream);
 int mpi_ffl_adjoint_zdrive(mpi_ffl_handle *h, const float *b_z_ri, float *x, void *stream);
 
+/* Scans of mpi_ffl_solve and mpi_ffl_power_norm (Sec. 3.1: an x-drive and a z-drive scan
+ * at every angle). MPI_FFL_SCAN_X (the default) is A alone; MPI_FFL_SCAN_Z is A_z alone;
+ * both reconstruct from the stacked operator [A; A_z], whose data d_b are the two scans'
+ * data one after the other (x first), 2 n_data floats, and whose transpose is
+ * A^T r + A_z^T r_z. ||A^T A|| of the power iteration and the default lambda and tau
+ * then refer to that operator. mpi_ffl_forward/adjoint stay the x-drive scan;
+ * param_grad and jobs refuse other scan sets (MPI_FFL_ERR_UNSUPPORTED). Selecting the
+ * z scan builds its tables (as mpi_ffl_forward_zdrive); both scans add 2 n_data +
+ * 2 n_vox floats of workspace. The call synchronises the device. */
+#define MPI_FFL_SCAN_X 1
+#define MPI_FFL_SCAN_Z 2
+int mpi_ffl_set_scans(mpi_ffl_handle *h, int32_t scans);
+int mpi_ffl_get_scans(const mpi_ffl_handle *h);
+
 /* Stages of the z-drive scan on caller device buffers (transpose = 1 for the
  * transpose): stage 1 = H_z: proj [M][N_z][N] <-> fine_z [M][N][N_ez];
  * stage 2 = E_z V_z B: fine_z <-> sig [M][N_z][L]. P and S D_Gamma F are the x-drive

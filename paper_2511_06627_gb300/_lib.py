@@ -30,6 +30,8 @@ STAGE_P, STAGE_H, STAGE_EVB, STAGE_F = 0, 1, 2, 3
 PATH_STAGED, PATH_FUSED, PATH_LINE_GEMM, PATH_FULL_GEMM = 0, 1, 2, 3
 PATHS = {"staged": PATH_STAGED, "fused": PATH_FUSED, "line_gemm": PATH_LINE_GEMM, "full_gemm": PATH_FULL_GEMM}
 PSF_COLLINEAR, PSF_TENSOR = 0, 1
+SCAN_X, SCAN_Z = 1, 2
+SCANS = {"x": SCAN_X, "z": SCAN_Z, "xz": SCAN_X | SCAN_Z}
 PSF_MODELS = {"collinear": PSF_COLLINEAR, "tensor": PSF_TENSOR}
 
 
@@ -102,6 +104,8 @@ PROTOTYPES = {
     "mpi_ffl_set_psf_model": (C.c_int, [H, C.c_int32]),
     "mpi_ffl_get_psf_model": (C.c_int, [H]),
     "mpi_ffl_set_coil_map": (C.c_int, [H, FP]),
+    "mpi_ffl_set_scans": (C.c_int, [H, C.c_int32]),
+    "mpi_ffl_get_scans": (C.c_int, [H]),
     "mpi_ffl_box_stats": (C.c_int, [FP, C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_int32, C.c_int32,
                                     C.c_void_p, ST]),
     "mpi_ffl_detection_limit": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_double, C.c_double, C.c_void_p]),

@@ -13,6 +13,11 @@
 
 using namespace mpiffl;
 
+// the z-drive scan (defined with its entry points below)
+void z_init(mpi_ffl_handle *h);
+void forward_z_impl(mpi_ffl_handle *h, const float *x, float *b, cudaStream_t st);
+void adjoint_z_impl(mpi_ffl_handle *h, const float *b, float *x, cudaStream_t st);
+
 namespace {
 
 thread_local std::string g_create_error;
@@ -360,7 +365,7 @@ void release(mpi_ffl_handle *h) {
                     h->t_csr, h->t_tw1, h->t_tw2_ro, h->t_tw2_qr, h->t_dgam, h->t_dgam_unit, h->t_groups, h->w_volT,
                     h->w_proj, h->w_fine, h->w_sig, h->w_data, h->w_vol2, h->w_red, h->w_scal,
                     h->s_xp, h->s_y, h->s_g, h->s_r, h->s_hist, h->s_flags, h->tc_twb, h->t_agroups,
-                    h->t_tnf, h->t_vr, h->w_err, h->t_coil, h->w_projc};
+                    h->t_tnf, h->t_vr, h->w_err, h->t_coil, h->w_projc, h->w_scanvol};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (auto &r : h->prof_rec) {
@@ -596,6 +601,36 @@ double dot_sync(mpi_ffl_handle *h, const float *a, const float *b, int64_t n, cu
     return v;
 }
 
+// The operator of the selected scans (Sec. 3.1: an x-drive and a z-drive scan per
+// angle): r = [A x; A_z x] in that order, and its transpose A^T r + A_z^T r_z (the
+// two volumes summed in a fixed order).
+int64_t scan_data_len(const mpi_ffl_handle *h) {
+    return (int64_t)(((h->scans & MPI_FFL_SCAN_X) ? 1 : 0) + ((h->scans & MPI_FFL_SCAN_Z) ? 1 : 0)) * h->d.ndata;
+}
+
+void scans_forward(mpi_ffl_handle *h, const float *x, float *r, cudaStream_t st) {
+    if (h->scans & MPI_FFL_SCAN_X) {
+        forward_impl(h, x, r, h->t_htab, h->t_gain, st);
+        r += h->d.ndata;
+    }
+    if (h->scans & MPI_FFL_SCAN_Z) forward_z_impl(h, x, r, st);
+}
+
+void scans_adjoint(mpi_ffl_handle *h, const float *r, float *g, cudaStream_t st) {
+    const Dims &d = h->d;
+    if (h->scans == (MPI_FFL_SCAN_X | MPI_FFL_SCAN_Z)) {
+        adjoint_impl(h, r, h->w_scanvol, st);
+        adjoint_z_impl(h, r + d.ndata, h->w_scanvol + d.nvox, st);
+        TIMED(MPI_FFL_K_SOLVER, launch_coil_pad(h->w_scanvol, nullptr, g, (long long)d.Nz * d.N, d.Nz, d.N, d.N, st, 2,
+                                                d.nvox));
+        check_launch(h, "scan sum");
+    } else if (h->scans & MPI_FFL_SCAN_X) {
+        adjoint_impl(h, r, g, st);
+    } else {
+        adjoint_z_impl(h, r, g, st);
+    }
+}
+
 double power_norm_impl(mpi_ffl_handle *h, int n_iter, uint64_t seed, cudaStream_t st) {
     const Dims &d = h->d;
     float *v = h->w_vol2, *w = h->s_g;
@@ -606,8 +641,8 @@ double power_norm_impl(mpi_ffl_handle *h, int n_iter, uint64_t seed, cudaStream_
     TIMED(MPI_FFL_K_SOLVER, launch_scale_by_rsqrt(v, v, d.nvox, h->w_scal + 0, st));
     check_launch(h, "power init");
     for (int it = 0; it < n_iter; ++it) {
-        forward_impl(h, v, h->w_data, h->t_htab, h->t_gain, st);
-        adjoint_impl(h, h->w_data, w, st);
+        scans_forward(h, v, h->w_data, st);
+        scans_adjoint(h, h->w_data, w, st);
         TIMED(MPI_FFL_K_SOLVER, launch_dot(v, w, d.nvox, h->w_red, nbv, st));
         TIMED(MPI_FFL_K_SOLVER, launch_finalize(h->w_red, nbv, h->w_scal + 1, st));
         TIMED(MPI_FFL_K_SOLVER, launch_dot(w, w, d.nvox, h->w_red, nbv, st));
@@ -907,6 +942,35 @@ extern "C" int mpi_ffl_set_coil_map(mpi_ffl_handle *h, const float *b_zu) {
         return MPI_FFL_OK;
     });
 }
+
+extern "C" int mpi_ffl_set_scans(mpi_ffl_handle *h, int32_t scans) {
+    return guarded(h, [&]() {
+        if (scans < MPI_FFL_SCAN_X || scans > (MPI_FFL_SCAN_X | MPI_FFL_SCAN_Z)) {
+            h->err = "scans must be MPI_FFL_SCAN_X, MPI_FFL_SCAN_Z or both";
+            return MPI_FFL_ERR_INVALID_ARG;
+        }
+        const Dims &d = h->d;
+        CK(cudaDeviceSynchronize());
+        if (scans & MPI_FFL_SCAN_Z) z_init(h);
+        const int n = ((scans & MPI_FFL_SCAN_X) ? 1 : 0) + ((scans & MPI_FFL_SCAN_Z) ? 1 : 0);
+        if (n == 2 && !h->w_scanvol) {
+            // residual and power-iteration data of both scans, and the two transposes
+            float *r = nullptr, *w = nullptr;
+            dev_alloc(h, &r, (size_t)2 * d.ndata);
+            dev_alloc(h, &w, (size_t)2 * d.ndata);
+            dev_alloc(h, &h->w_scanvol, (size_t)2 * d.nvox);
+            CK(cudaFree(h->s_r));
+            CK(cudaFree(h->w_data));
+            h->bytes -= (int64_t)(2 * d.ndata * sizeof(float));
+            h->s_r = r;
+            h->w_data = w;
+        }
+        h->scans = scans;
+        return MPI_FFL_OK;
+    });
+}
+
+extern "C" int mpi_ffl_get_scans(const mpi_ffl_handle *h) { return h ? h->scans : MPI_FFL_ERR_INVALID_ARG; }
 
 extern "C" int mpi_ffl_get_path(const mpi_ffl_handle *h) { return h ? h->path : MPI_FFL_ERR_INVALID_ARG; }
 extern "C" int mpi_ffl_get_precision(const mpi_ffl_handle *h) {
@@ -1238,8 +1302,8 @@ extern "C" int mpi_ffl_apply_stage(mpi_ffl_handle *h, int32_t stage, int32_t tra
 extern "C" int mpi_ffl_param_grad(mpi_ffl_handle *h, const float *d_x, const float *d_gb, float *d_g_gain,
                                   float *d_g_fwhm, void *stream) {
     return guarded(h, [&]() {
-        if (h->psf_model == MPI_FFL_PSF_TENSOR) {
-            h->err = "parameter gradients are built for the collinear PSF only";
+        if (h->psf_model == MPI_FFL_PSF_TENSOR || h->scans != MPI_FFL_SCAN_X) {
+            h->err = "parameter gradients are built for the collinear PSF of the x-drive scan only";
             return MPI_FFL_ERR_UNSUPPORTED;
         }
         if (!d_x || !d_gb) {
@@ -1256,8 +1320,8 @@ extern "C" int mpi_ffl_param_grad(mpi_ffl_handle *h, const float *d_x, const flo
 extern "C" int mpi_ffl_param_grad_proj(mpi_ffl_handle *h, const float *d_proj, const float *d_gb, float *d_g_gain,
                                        float *d_g_fwhm, void *stream) {
     return guarded(h, [&]() {
-        if (h->psf_model == MPI_FFL_PSF_TENSOR) {
-            h->err = "parameter gradients are built for the collinear PSF only";
+        if (h->psf_model == MPI_FFL_PSF_TENSOR || h->scans != MPI_FFL_SCAN_X) {
+            h->err = "parameter gradients are built for the collinear PSF of the x-drive scan only";
             return MPI_FFL_ERR_UNSUPPORTED;
         }
         if (!d_proj || !d_gb) {
@@ -1389,16 +1453,17 @@ extern "C" int mpi_ffl_solve(mpi_ffl_handle *h, const float *d_b, float *d_x, co
         const int *frozen = p->stop_rel > 0.0 ? flags + 2 : nullptr;
         CK(cudaMemcpyAsync(h->s_xp, d_x, sizeof(float) * d.nvox, cudaMemcpyDeviceToDevice, st));
         float *xc = d_x, *xp = h->s_xp;
-        const int nbd = reduce_blocks(d.ndata);
+        const int64_t nd = scan_data_len(h);  // data of the selected scans
+        const int nbd = reduce_blocks(nd);
         int done_host = 0, k_run = 0;
         for (int k = 1; k <= p->iters; ++k) {
             const double beta = (k - 1.0) / (k + 2.0);
             TIMED(MPI_FFL_K_SOLVER, launch_momentum(xc, xp, h->s_y, beta, k, d.nvox, frozen, st));
-            forward_impl(h, h->s_y, h->s_r, h->t_htab, h->t_gain, st);
-            TIMED(MPI_FFL_K_SOLVER, launch_sub_norm(h->s_r, d_b, d.ndata, h->w_red, nbd, frozen, st));
+            scans_forward(h, h->s_y, h->s_r, st);
+            TIMED(MPI_FFL_K_SOLVER, launch_sub_norm(h->s_r, d_b, nd, h->w_red, nbd, frozen, st));
             TIMED(MPI_FFL_K_SOLVER, launch_finalize(h->w_red, nbd, h->s_hist + (k - 1), st));
             TIMED(MPI_FFL_K_SOLVER, launch_stop_check(h->s_hist, k - 1, p->stop_rel, flags, flags + 1, st));
-            adjoint_impl(h, h->s_r, h->s_g, st);
+            scans_adjoint(h, h->s_r, h->s_g, st);
             TIMED(MPI_FFL_K_SOLVER, launch_update(h->s_y, h->s_g, xp, (float)tau, (float)lam, p->nonneg ? 1 : 0,
                                                   d.N, d.Nz, frozen, st, xc));
             if (frozen) TIMED(MPI_FFL_K_SOLVER, launch_freeze(flags, flags + 2, st));
@@ -1422,7 +1487,7 @@ extern "C" int mpi_ffl_solve(mpi_ffl_handle *h, const float *d_b, float *d_x, co
                 CK(cudaMemcpyAsync(&first, h->s_hist, sizeof(double), cudaMemcpyDeviceToHost, st));
                 CK(cudaMemcpyAsync(&last, h->s_hist + (k_run - 1), sizeof(double), cudaMemcpyDeviceToHost, st));
             }
-            const double bn = std::sqrt(dot_sync(h, d_b, d_b, d.ndata, st));
+            const double bn = std::sqrt(dot_sync(h, d_b, d_b, nd, st));
             if (rep) {
                 rep->iters_done = k_run;
                 rep->tau = tau;

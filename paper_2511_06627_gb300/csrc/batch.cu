@@ -106,6 +106,10 @@ extern "C" int mpi_ffl_job_create(mpi_ffl_handle *h, const float *d_b, const flo
                                   const mpi_ffl_solve_params *p, mpi_ffl_job **out, void *stream) {
     if (!h || !d_b || !p || !out || p->iters < 1) return MPI_FFL_ERR_INVALID_ARG;
     *out = nullptr;
+    if (h->scans != MPI_FFL_SCAN_X) {  // jobs reconstruct from the x-drive scan
+        h->err = "jobs use the x-drive scan only (mpi_ffl_set_scans)";
+        return MPI_FFL_ERR_UNSUPPORTED;
+    }
     mpi_ffl_job *j = new (std::nothrow) mpi_ffl_job();
     if (!j) return MPI_FFL_ERR_OOM;
     const Dims &d = h->d;

@@ -157,6 +157,9 @@ struct mpi_ffl_handle {
     cudaEvent_t hs_ready[2] = {}, hs_free[2] = {};
     int hs_slot = 0;
     int host_overlap = 0;                   // mpi_ffl_set_host_overlap
+    // scans of the solve and power iteration (MPI_FFL_SCAN_* bits): [A; A_z] when both
+    int scans = 1;
+    float *w_scanvol = nullptr;  // 2 n_vox: A^T r and A_z^T r_z before their sum
     // PSF model (MPI_FFL_PSF_*) and receive-coil map b[z][u] (NULL: uniform coil)
     int psf_model = 0;
     float *t_coil = nullptr;    // N_z N

@@ -265,10 +265,28 @@ class FFLOperator:
         check(self._lib.mpi_ffl_power_norm(self._h, int(n_iter), C.c_uint64(seed), C.byref(out), _stream()), self._h)
         return out.value
 
+    def set_scans(self, scans):
+        """Scans the solve and power iteration reconstruct from (Sec. 3.1): 'x' (the default,
+        A), 'z' (the z-drive scan A_z) or 'xz' (the stacked [A; A_z]); or SCAN_* bits."""
+        if isinstance(scans, str):
+            scans = _lib.SCANS[scans]
+        check(self._lib.mpi_ffl_set_scans(self._h, int(scans)), self._h)
+
+    @property
+    def scans(self):
+        return int(self._lib.mpi_ffl_get_scans(self._h))
+
+    @property
+    def solve_data_shape(self):
+        """Shape of the solve's data: the selected scans' data along the angle axis (x first)."""
+        n = bin(self.scans).count("1")
+        return (n * self.n_angles,) + self.data_shape[1:]
+
     def solve(self, b, x0=None, iters=50, lam=-1.0, tau=0.0, n_power=50, seed=1234, nonneg=True,
               stop_rel=0.0, ata_norm=0.0, report=True):
-        """Run Eq. (26); returns (x, report dict or None)."""
-        self._check(b, self.data_shape, "b")
+        """Run Eq. (26) on the selected scans (set_scans); returns (x, report dict or None).
+        b has solve_data_shape: with both scans, torch.cat([b_x, b_z])."""
+        self._check(b, self.solve_data_shape, "b")
         x = torch.zeros(self.vol_shape, device=self.device, dtype=torch.float32) if x0 is None else x0.clone()
         self._check(x, self.vol_shape, "x0")
         p = _lib.SolveParams(int(iters), float(lam), float(tau), int(n_power), C.c_uint64(seed), int(bool(nonneg)),
