@@ -117,6 +117,7 @@ struct mpi_ffl_handle {
     mpiffl::SegGroup *t_groups = nullptr;
     int n_groups = 0;
     int *t_agroups = nullptr;  // projector angle groups: kProjAnglesPerBlock indices, -1 = empty
+    float *w_volI = nullptr, *w_volTI = nullptr;  // slice-interleaved volume copies (il_len floats each)
     int n_agroups = 0;
 
     // workspace
@@ -259,6 +260,12 @@ void set_thread_error(const std::string &msg);
 // ---------------------------------------------------------------- launchers
 // Projector (k_projector.cu)
 void launch_transpose_xy(const float *vol, float *volT, int N, int Nz, cudaStream_t st);
+// slice-interleaved volume copies and the projector that reads them (k_projector.cu)
+bool project_il_ok(int N);
+size_t il_len(int N, int Nz);
+void launch_interleave(const float *vol, float *volI, float *volTI, int N, int Nz, cudaStream_t st);
+void launch_project_il(const float *volI, const float *volTI, const AngleParam *ang, const int *agroups,
+                       int n_agroups, float *proj, int N, int Nz, cudaStream_t st, int *err);
 void launch_project(const float *vol, const float *volT, const AngleParam *ang, const int *agroups,
                     int n_agroups, float *proj, int N, int Nz, cudaStream_t st, int *err);
 constexpr int kProjAnglesPerBlock = 2;  // angle slots per projector block (k_projector.cu)

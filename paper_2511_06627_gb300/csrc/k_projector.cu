@@ -313,6 +313,191 @@ void launch_project(const float *vol, const float *volT, const AngleParam *ang, 
     k_project<<<grid, threads, smem, st>>>(vol, volT, ang, agroups, proj, N, Nz, rays);
 }
 
+// Interleaved variant (same shapes as the pipelined one). The volume is copied with each
+// line's kZc slices innermost, [z block][s][c][kZc], once for row-marched angles (s = y,
+// c = x) and once transposed for column-marched ones (s = x, c = y). The two 16-byte
+// halves of position c are swapped when bit 2 of c + kPad is set. A march step is then
+// one bulk copy of N kZc floats. A ray reads its two taps for all kZc slices with four
+// 16-byte loads. Eight rays whose positions differ mod 8 read eight distinct 16-byte
+// bank groups: position p puts slices 0-3 in group 2p + ((p >> 2) & 1) mod 8. The sums
+// are those of the pipelined variant, slice by slice.
+__host__ __device__ __forceinline__ int il_swap(int cs) { return (cs >> 2) & 1; }
+
+size_t il_len(int N, int Nz) { return (size_t)((Nz + kZc - 1) / kZc) * kZc * N * N; }
+
+// volI[zb][y][x][e] and volTI[zb][x][y][e] = vol[kZc zb + e][y][x] (zero past Nz), halves
+// swapped as above. A block of 8 x 32 threads moves a 32 x 32 tile of one slice block
+// through shared memory: thread (tx, ty) loads 4 consecutive x of row ty of every slice
+// (16-byte loads; N % 4 == 0) and stores 4 consecutive positions (128 contiguous bytes)
+// of each copy. The transposed reads tile[e][4 tx + q][ty] hit 32 distinct banks.
+__global__ void __launch_bounds__(256) k_interleave(const float *__restrict__ vol, float *__restrict__ volI,
+                                                    float *__restrict__ volTI, int N, int Nz) {
+    __shared__ float tile[kZc][32][33];
+    const int tx = threadIdx.x, ty = threadIdx.y;  // 8 x 32
+    const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 32, zb = blockIdx.z;
+    {
+        const int y = y0 + ty, x = x0 + 4 * tx;
+#pragma unroll
+        for (int e = 0; e < kZc; ++e) {
+            const int z = zb * kZc + e;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (z < Nz && y < N && x < N) v = __ldg(reinterpret_cast<const float4 *>(vol + ((size_t)z * N + y) * N + x));
+            tile[e][ty][4 * tx] = v.x;
+            tile[e][ty][4 * tx + 1] = v.y;
+            tile[e][ty][4 * tx + 2] = v.z;
+            tile[e][ty][4 * tx + 3] = v.w;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int c = 4 * tx + q;
+        {  // volI: row y0 + ty, position x0 + c
+            const int y = y0 + ty, x = x0 + c;
+            if (y < N && x < N) {
+                const int sw = il_swap(x + kPad);
+                float4 *o = reinterpret_cast<float4 *>(volI + (((size_t)zb * N + y) * N + x) * kZc);
+                o[sw] = make_float4(tile[0][ty][c], tile[1][ty][c], tile[2][ty][c], tile[3][ty][c]);
+                o[1 - sw] = make_float4(tile[4][ty][c], tile[5][ty][c], tile[6][ty][c], tile[7][ty][c]);
+            }
+        }
+        {  // volTI: row x0 + ty, position y0 + c
+            const int x = x0 + ty, y = y0 + c;
+            if (y < N && x < N) {
+                const int sw = il_swap(y + kPad);
+                float4 *o = reinterpret_cast<float4 *>(volTI + (((size_t)zb * N + x) * N + y) * kZc);
+                o[sw] = make_float4(tile[0][c][ty], tile[1][c][ty], tile[2][c][ty], tile[3][c][ty]);
+                o[1 - sw] = make_float4(tile[4][c][ty], tile[5][c][ty], tile[6][c][ty], tile[7][c][ty]);
+            }
+        }
+    }
+}
+
+void launch_interleave(const float *vol, float *volI, float *volTI, int N, int Nz, cudaStream_t st) {
+    dim3 grid((N + 31) / 32, (N + 31) / 32, (Nz + kZc - 1) / kZc), block(8, 32);
+    k_interleave<<<grid, block, 0, st>>>(vol, volI, volTI, N, Nz);
+}
+
+template <int LDC>
+__global__ void __launch_bounds__(1024 + 32) k_project_il(const float *__restrict__ volI,
+                                                          const float *__restrict__ volTI,
+                                                          const AngleParam *__restrict__ ang,
+                                                          const int *__restrict__ agroups, float *__restrict__ proj,
+                                                          int N, int Nz, int rays_per_angle, int *err) {
+    extern __shared__ __align__(128) float psm[];  // kPStages x LDC positions x kZc
+    uint64_t *bars = reinterpret_cast<uint64_t *>(psm + kPStages * LDC * kZc);  // full[K], empty[K]
+    const int bx = blockIdx.x, zb = blockIdx.y;
+    const int nthreads_c = rays_per_angle * kProjAnglesPerBlock;  // consumers
+    const int ncw = nthreads_c / 32;
+    const int z0 = zb * kZc;
+    const int nz = min(kZc, Nz - z0);
+    const int tid = threadIdx.x;
+    // zero the pad positions [0, kPad) and [kPad + N, LDC) of every stage
+    const int padp = LDC - N;
+    for (int t = tid; t < kPStages * padp * kZc; t += nthreads_c + 32) {
+        const int stg = t / (padp * kZc), r = t - stg * padp * kZc;
+        const int pp = r / kZc, e = r - pp * kZc;
+        psm[((size_t)stg * LDC + (pp < kPad ? pp : N + pp)) * kZc + e] = 0.f;
+    }
+    if (tid == 0) {
+        for (int k = 0; k < kPStages; ++k) {
+            ptx::mbar_init(&bars[k], 1);
+            ptx::mbar_init(&bars[kPStages + k], ncw);
+        }
+        ptx::fence_mbar_init();
+    }
+    __syncthreads();
+    const AngleParam a0 = ang[agroups[bx * kProjAnglesPerBlock]];
+    const float *src = (a0.row_major ? volI : volTI) + (size_t)zb * N * N * kZc;  // one orientation per block
+    const uint32_t step_bytes = (uint32_t)N * kZc * 4u;
+    if (tid >= nthreads_c) {
+        // ---------------------------------------------------------------- producer
+        if (tid == nthreads_c) {
+            for (int s = 0; s < N; ++s) {
+                const int k = s % kPStages;
+                if (s >= kPStages && !ptx::mbar_wait_bounded(&bars[kPStages + k], ((s / kPStages) - 1) & 1, 1u << 24)) {
+                    atomicExch(err, 1);
+                    break;
+                }
+                ptx::mbar_arrive_expect_tx(&bars[k], step_bytes);
+                ptx::bulk_g2s(psm + ((size_t)k * LDC + kPad) * kZc, src + (size_t)s * N * kZc, step_bytes, &bars[k]);
+            }
+        }
+        return;
+    }
+    // -------------------------------------------------------------------- consumers
+    // Threads of an inactive slot or beyond the last ray run the loop on clamped,
+    // in-bounds taps and store nothing; slices past nz hold zeros, never stored.
+    const int slot = tid / rays_per_angle;
+    const int i = tid % rays_per_angle;
+    const int m = agroups[bx * kProjAnglesPerBlock + slot];
+    const bool active = (m >= 0) && (i < N);
+    const AngleParam ap = ang[m >= 0 ? m : agroups[bx * kProjAnglesPerBlock]];
+    long long fs = ap.fx_a + (long long)i * ap.fx_d;  // position of ray i at march step s
+    float acc[kZc];
+#pragma unroll
+    for (int zz = 0; zz < kZc; ++zz) acc[zz] = 0.f;
+    bool good = true;
+    for (int s = 0; s < N; ++s, fs += ap.fx_b) {
+        const int k = s % kPStages;
+        if (!ptx::mbar_wait_bounded(&bars[k], (s / kPStages) & 1, 1u << 24)) {
+            good = false;
+            break;
+        }
+        int cell;
+        float t;
+        fx_split(fs, cell, t);
+        const int cs = min(max(cell, -2), N) + kPad;  // staged position of the left tap
+        const float *b0 = psm + ((size_t)k * LDC + cs) * kZc;
+        const int w0 = 4 * il_swap(cs), w1 = 4 * il_swap(cs + 1);
+        const float4 l0 = *reinterpret_cast<const float4 *>(b0 + w0);
+        const float4 l1 = *reinterpret_cast<const float4 *>(b0 + 4 - w0);
+        const float4 r0 = *reinterpret_cast<const float4 *>(b0 + kZc + w1);
+        const float4 r1 = *reinterpret_cast<const float4 *>(b0 + kZc + 4 - w1);
+        const float v0[kZc] = {l0.x, l0.y, l0.z, l0.w, l1.x, l1.y, l1.z, l1.w};
+        const float v1[kZc] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+#pragma unroll
+        for (int zz = 0; zz < kZc; ++zz) acc[zz] = fmaf(1.f - t, v0[zz], fmaf(t, v1[zz], acc[zz]));
+        __syncwarp();
+        if ((tid & 31) == 0) ptx::mbar_arrive(&bars[kPStages + k]);
+    }
+    if (!good) {
+        if ((tid & 31) == 0) atomicExch(err, 1);
+        return;
+    }
+    if (active) {
+#pragma unroll
+        for (int zz = 0; zz < kZc; ++zz)
+            if (zz < nz) proj[((size_t)m * Nz + z0 + zz) * N + i] = acc[zz] * ap.scale;
+    }
+}
+
+template <int LDC>
+void launch_il(dim3 grid, int threads, cudaStream_t st, const float *volI, const float *volTI, const AngleParam *ang,
+               const int *agroups, float *proj, int N, int Nz, int rays, int *err) {
+    const size_t smem = pipe_smem(LDC);  // kPStages x kZc x LDC floats, as the pipelined variant
+    cudaFuncSetAttribute(k_project_il<LDC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    k_project_il<LDC><<<grid, threads, smem, st>>>(volI, volTI, ang, agroups, proj, N, Nz, rays, err);
+}
+
+bool project_il_ok(int N) { return N % 4 == 0 && pipe_ld(N) > 0; }
+
+void launch_project_il(const float *volI, const float *volTI, const AngleParam *ang, const int *agroups,
+                       int n_agroups, float *proj, int N, int Nz, cudaStream_t st, int *err) {
+    const int rays = (N + 31) / 32 * 32;
+    dim3 grid(n_agroups, (Nz + kZc - 1) / kZc);
+    const int threads = rays * kProjAnglesPerBlock + 32;
+    switch (pipe_ld(N)) {
+    case 40: launch_il<40>(grid, threads, st, volI, volTI, ang, agroups, proj, N, Nz, rays, err); break;
+    case 72: launch_il<72>(grid, threads, st, volI, volTI, ang, agroups, proj, N, Nz, rays, err); break;
+    case 136: launch_il<136>(grid, threads, st, volI, volTI, ang, agroups, proj, N, Nz, rays, err); break;
+    case 200: launch_il<200>(grid, threads, st, volI, volTI, ang, agroups, proj, N, Nz, rays, err); break;
+    case 264: launch_il<264>(grid, threads, st, volI, volTI, ang, agroups, proj, N, Nz, rays, err); break;
+    case 392: launch_il<392>(grid, threads, st, volI, volTI, ang, agroups, proj, N, Nz, rays, err); break;
+    default: launch_il<520>(grid, threads, st, volI, volTI, ang, agroups, proj, N, Nz, rays, err); break;
+    }
+}
+
 // Transpose: a block owns a tile of kBpTX x kBpTY voxel columns and kBpZ slices; a
 // thread owns one column (x, y) and its kBpZ slices. For every angle the rays whose
 // interpolation touches the voxel are among i1-1, i1, i1+1 (i1 the nearest ray); ray
