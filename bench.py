@@ -197,7 +197,8 @@ ALGO_BYTES = {
     "dft_adj": lambda d: 4 * (d["nsig"] + d["ndata"]),
     "tc_fwd": lambda d: 4 * (d["nfine"] + d["ndata"]),
     "tc_adj": lambda d: 4 * (d["nfine"] + d["ndata"]),
-    "transpose": lambda d: 8 * d["nvox"],
+    # the slice-interleaving pass: reads the volume, writes its two interleaved copies
+    "transpose": lambda d: 12 * d["nvox"],
     # the full-GEMM path applies W H to projections, the line-GEMM path W to fine rows
     "gemm_fwd": lambda d: 4 * ((d["nproj"] if d["path"].startswith("full_gemm") else d["nfine"]) + d["ndata"]),
     "gemm_adj": lambda d: 4 * ((d["nproj"] if d["path"].startswith("full_gemm") else d["nfine"]) + d["ndata"]),
@@ -214,11 +215,12 @@ SMEM_BYTES = {
 SMEM_BYTES_PER_CLK_SM = 128
 
 # DRAM bytes (read + write) per launch from the ncu capture summarised in
-# profiles/full_gemm_invivo_kernels.md (cold caches, 256^2x128, 36 angles). Reported
-# only for that workload and only while the kernel is the one that was captured.
+# profiles/projector_il_invivo.md (cold caches, 256^2x128, 36 angles). Reported only
+# for that workload and only while the kernel is the one that was captured.
 DRAM_TRAFFIC = {
-    "project": 67_126_016 + 1_203_456,   # reads the volume and its transposed copy
-    "backproject": 4_736_000 + 512,      # reads the projections; the volume it writes stays in L2
+    "project": 67_128_064 + 1_369_088,    # reads both interleaved copies of the volume
+    "backproject": 4_732_160 + 1_024,     # reads the projections; the volume it writes stays in L2
+    "transpose": 33_926_912 + 13_372_928,  # interleave pass: most of its writes stay in L2
 }
 
 

@@ -510,9 +510,16 @@ void launch_project_il(const float *volI, const float *volTI, const AngleParam *
 // the chunk's windows of proj x scale (zero outside the detector) are staged in
 // shared memory, then every thread gathers its two rays per slice from there.
 constexpr int kBpTX = 32, kBpTY = 16, kBpZ = 16, kBpSeg = 40, kBpChunk = 12;
+// A staged ray holds its kBpZ slices innermost in a row of kBpRow floats: a voxel reads
+// its two rays' taps for all slices with eight 16-byte loads. kBpRow = 20 is an odd
+// number of 16-byte groups, so eight consecutive rays start in distinct bank groups.
+// (32 slices per thread, sharing each angle's weights over more samples, measured
+// slower: 186 against 125 us at 256^2 x 128, 36 angles.)
+constexpr int kBpRow = 20;
+static_assert(kBpRow >= kBpZ && kBpRow % 4 == 0 && (kBpRow / 4) % 2 == 1, "row of 16-byte groups, odd count");
 
-struct BpShared {
-    float seg[kBpChunk][kBpZ][kBpSeg];
+struct __align__(16) BpShared {
+    float seg[kBpChunk][kBpSeg][kBpRow];
     AngleParam ang[kBpChunk];
     int ilo[kBpChunk];
 };
@@ -559,7 +566,7 @@ __device__ __forceinline__ void backproject_body(const float *__restrict__ proj,
             const int i = S.ilo[a] + j, z = z0 + zz;
             float v = 0.f;
             if (i >= 0 && i < N && z < Nz) v = __ldg(proj + ((size_t)(m0 + a) * Nz + z) * N + i) * S.ang[a].scale;
-            S.seg[a][zz][j] = v;
+            S.seg[a][j][zz] = v;
         }
         __syncthreads();
         for (int a = 0; a < na; ++a) {
@@ -584,10 +591,16 @@ __device__ __forceinline__ void backproject_body(const float *__restrict__ proj,
             const bool lo = w0 != 0.f;
             const float wA = lo ? w0 : w1, wB = lo ? w1 : w2;
             const int j = min(max(i1 - (lo ? 1 : 0) - S.ilo[a], 0), kBpSeg - 2);
-            const float *p = &S.seg[a][0][j];
+            const float4 *pa = reinterpret_cast<const float4 *>(&S.seg[a][j][0]);
+            const float4 *pb = reinterpret_cast<const float4 *>(&S.seg[a][j + 1][0]);
 #pragma unroll
-            for (int zz = 0; zz < kBpZ; ++zz)
-                acc[zz] = fmaf(wA, p[zz * kBpSeg], fmaf(wB, p[zz * kBpSeg + 1], acc[zz]));
+            for (int g4 = 0; g4 < kBpZ / 4; ++g4) {
+                const float4 va = pa[g4], vb = pb[g4];
+                acc[4 * g4] = fmaf(wA, va.x, fmaf(wB, vb.x, acc[4 * g4]));
+                acc[4 * g4 + 1] = fmaf(wA, va.y, fmaf(wB, vb.y, acc[4 * g4 + 1]));
+                acc[4 * g4 + 2] = fmaf(wA, va.z, fmaf(wB, vb.z, acc[4 * g4 + 2]));
+                acc[4 * g4 + 3] = fmaf(wA, va.w, fmaf(wB, vb.w, acc[4 * g4 + 3]));
+            }
         }
     }
     if (x < N && y < N) {
