@@ -613,9 +613,19 @@ def run_ours(args, cfg, rank, world, local_rank):
         "config": {"workload": workload_desc(cfg), "path": path,
                    "l2": "flushed (256 MB write) between timed steps",
                    "step": "b = A x then x' = A^T b, inputs resident in HBM"},
-        "roofline": {"kernel": top, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": traffic, "peak_source": src,
-                     "algorithmic_bytes_per_launch": algo, "avg_launch_ms": per_launch_ms, "onchip": onchip},
+        # the projector pair is bound by shared-memory bandwidth, not HBM: its roofline is
+        # the shared-memory one (peak from the SM count, 128 B/clk/SM and the measured
+        # clock); the HBM figures are kept beside it, with the DRAM traffic of the capture
+        "roofline": ({"kernel": top, "bound": "smem", "achieved": onchip["achieved"], "peak": onchip["peak"],
+                      "unit": "GB/s", "frac": onchip["frac"], "traffic": traffic,
+                      "peak_source": "derived: " + onchip["peak_basis"],
+                      "algorithmic_bytes_per_launch": onchip["bytes_per_launch"], "avg_launch_ms": per_launch_ms,
+                      "hbm": {"achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                              "peak_source": src, "algorithmic_bytes_per_launch": algo}}
+                     if onchip else
+                     {"kernel": top, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                      "frac": achieved / hbm, "traffic": traffic, "peak_source": src,
+                      "algorithmic_bytes_per_launch": algo, "avg_launch_ms": per_launch_ms}),
         "kernel_time_share": kernel_share,
         "profiled_ms_per_step": ms_prof / args.steps,
         "kernel_ms_per_launch": kernel_ms,

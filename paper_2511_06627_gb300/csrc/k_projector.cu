@@ -326,49 +326,62 @@ __host__ __device__ __forceinline__ int il_swap(int cs) { return (cs >> 2) & 1; 
 size_t il_len(int N, int Nz) { return (size_t)((Nz + kZc - 1) / kZc) * kZc * N * N; }
 
 // volI[zb][y][x][e] and volTI[zb][x][y][e] = vol[kZc zb + e][y][x] (zero past Nz), halves
-// swapped as above. A block of 8 x 32 threads moves a 32 x 32 tile of one slice block
-// through shared memory: thread (tx, ty) loads 4 consecutive x of row ty of every slice
-// (16-byte loads; N % 4 == 0) and stores 4 consecutive positions (128 contiguous bytes)
-// of each copy. The transposed reads tile[e][4 tx + q][ty] hit 32 distinct banks.
+// swapped as above. A block of 8 x 32 threads moves a 32 x 32 tile of one slice block:
+// thread (tx, ty) loads 4 consecutive x of row ty of every slice (eight 16-byte loads;
+// N % 4 == 0), forms each position's 8 slices in registers and writes them to volI
+// directly. For volTI the tile goes through shared memory as 16-byte halves: half h of
+// tile row r, column c sits at 16-byte slot 64 r + 8 (c >> 2) + ((2 (c & 3) + h) ^ sw),
+// sw = ((c >> 2) ^ (r >> 2)) & 7. The row's stores (c = 4 tx + q) and the transposed
+// loads (r = 4 tx + q) then take 8 distinct bank groups per 8 lanes.
+__device__ __forceinline__ int il_tile_slot(int r, int c, int h) {
+    return 64 * r + 8 * (c >> 2) + ((2 * (c & 3) + h) ^ (((c >> 2) ^ (r >> 2)) & 7));
+}
+
 __global__ void __launch_bounds__(256) k_interleave(const float *__restrict__ vol, float *__restrict__ volI,
                                                     float *__restrict__ volTI, int N, int Nz) {
-    __shared__ float tile[kZc][32][33];
+    __shared__ float4 tile[32 * 64];  // 32 rows x 32 columns x 2 halves
     const int tx = threadIdx.x, ty = threadIdx.y;  // 8 x 32
     const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 32, zb = blockIdx.z;
-    {
-        const int y = y0 + ty, x = x0 + 4 * tx;
+    const int y = y0 + ty, xs = x0 + 4 * tx;
+    float4 v[kZc];
 #pragma unroll
-        for (int e = 0; e < kZc; ++e) {
-            const int z = zb * kZc + e;
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (z < Nz && y < N && x < N) v = __ldg(reinterpret_cast<const float4 *>(vol + ((size_t)z * N + y) * N + x));
-            tile[e][ty][4 * tx] = v.x;
-            tile[e][ty][4 * tx + 1] = v.y;
-            tile[e][ty][4 * tx + 2] = v.z;
-            tile[e][ty][4 * tx + 3] = v.w;
+    for (int e = 0; e < kZc; ++e) {
+        const int z = zb * kZc + e;
+        v[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (z < Nz && y < N && xs < N) v[e] = __ldg(reinterpret_cast<const float4 *>(vol + ((size_t)z * N + y) * N + xs));
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const float f0 = q == 0 ? v[0].x : q == 1 ? v[0].y : q == 2 ? v[0].z : v[0].w;
+        const float f1 = q == 0 ? v[1].x : q == 1 ? v[1].y : q == 2 ? v[1].z : v[1].w;
+        const float f2 = q == 0 ? v[2].x : q == 1 ? v[2].y : q == 2 ? v[2].z : v[2].w;
+        const float f3 = q == 0 ? v[3].x : q == 1 ? v[3].y : q == 2 ? v[3].z : v[3].w;
+        const float f4 = q == 0 ? v[4].x : q == 1 ? v[4].y : q == 2 ? v[4].z : v[4].w;
+        const float f5 = q == 0 ? v[5].x : q == 1 ? v[5].y : q == 2 ? v[5].z : v[5].w;
+        const float f6 = q == 0 ? v[6].x : q == 1 ? v[6].y : q == 2 ? v[6].z : v[6].w;
+        const float f7 = q == 0 ? v[7].x : q == 1 ? v[7].y : q == 2 ? v[7].z : v[7].w;
+        const float4 lo = make_float4(f0, f1, f2, f3), hi = make_float4(f4, f5, f6, f7);
+        const int c = 4 * tx + q, x = x0 + c;
+        tile[il_tile_slot(ty, c, 0)] = lo;
+        tile[il_tile_slot(ty, c, 1)] = hi;
+        if (y < N && x < N) {  // volI: row y, position x
+            const int sw = il_swap(x + kPad);
+            float4 *o = reinterpret_cast<float4 *>(volI + (((size_t)zb * N + y) * N + x) * kZc);
+            o[sw] = lo;
+            o[1 - sw] = hi;
         }
     }
     __syncthreads();
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int c = 4 * tx + q;
-        {  // volI: row y0 + ty, position x0 + c
-            const int y = y0 + ty, x = x0 + c;
-            if (y < N && x < N) {
-                const int sw = il_swap(x + kPad);
-                float4 *o = reinterpret_cast<float4 *>(volI + (((size_t)zb * N + y) * N + x) * kZc);
-                o[sw] = make_float4(tile[0][ty][c], tile[1][ty][c], tile[2][ty][c], tile[3][ty][c]);
-                o[1 - sw] = make_float4(tile[4][ty][c], tile[5][ty][c], tile[6][ty][c], tile[7][ty][c]);
-            }
-        }
-        {  // volTI: row x0 + ty, position y0 + c
-            const int x = x0 + ty, y = y0 + c;
-            if (y < N && x < N) {
-                const int sw = il_swap(y + kPad);
-                float4 *o = reinterpret_cast<float4 *>(volTI + (((size_t)zb * N + x) * N + y) * kZc);
-                o[sw] = make_float4(tile[0][c][ty], tile[1][c][ty], tile[2][c][ty], tile[3][c][ty]);
-                o[1 - sw] = make_float4(tile[4][c][ty], tile[5][c][ty], tile[6][c][ty], tile[7][c][ty]);
-            }
+    for (int q = 0; q < 4; ++q) {  // volTI: row x0 + ty, position y0 + 4 tx + q
+        const int r = 4 * tx + q;
+        const int x = x0 + ty, yy = y0 + r;
+        const float4 lo = tile[il_tile_slot(r, ty, 0)], hi = tile[il_tile_slot(r, ty, 1)];
+        if (yy < N && x < N) {
+            const int sw = il_swap(yy + kPad);
+            float4 *o = reinterpret_cast<float4 *>(volTI + (((size_t)zb * N + x) * N + yy) * kZc);
+            o[sw] = lo;
+            o[1 - sw] = hi;
         }
     }
 }
