@@ -744,12 +744,13 @@ def run_ours(args, cfg, rank, world, local_rank):
         flops = 2.0 * dims["M"] * nz_ * (nz_ * dims["N"]) * R_  # one direction, FP32 contraction
         sec = t_ms / max(t_n, 1) / 1e3
         peak, peak_src = bf16_peak_tflops()
-        # issued MMA work: J = 128 // M lines of one trajectory share a problem (rows M J in
-        # 128-row tiles) and its window spans N_z + step (J - 1) slices
+        # issued MMA work: J = 128 // M8 lines of one trajectory share a problem (rows M8 J,
+        # M8 = M rounded up to 8, in 128-row tiles) and its window spans N_z + step (J - 1)
+        # slices
         step_ = 2 if cfg["zigzag"] else 1
-        J_ = max(1, min(128 // dims["M"], (nz_ + step_ - 1) // step_))
-        rows_ = dims["M"] * J_
-        issue_factor = 128 * ((rows_ + 127) // 128) / rows_ * (nz_ + step_ * (J_ - 1)) / nz_
+        M8_ = (dims["M"] + 7) // 8 * 8
+        J_ = max(1, min(128 // M8_, (nz_ + step_ - 1) // step_))
+        issue_factor = (128 * ((M8_ * J_ + 127) // 128) / (dims["M"] * J_)) * (nz_ + step_ * (J_ - 1)) / nz_
         result["tensor_psf"] = {
             "pairs_per_s": 1e3 / ten_ms, "ms_per_pair": ten_ms,
             "stage_ms_per_launch": round(t_ms / max(t_n, 1), 4),
@@ -759,7 +760,7 @@ def run_ours(args, cfg, rank, world, local_rank):
             "peak": f"{peak} TFLOP/s bf16 ({peak_src})",
             "note": "stage = coil weighting + padding, per-line (per-slice) GEMMs over all slices (3 bf16 "
                     "products of 2 M N_z (N_z N) 2n_b flops), sum of the K splits; issued counts the 128-row "
-                    "MMA tiles that hold J lines x M angles and the window's step (J - 1) extra slices"}
+                    "MMA tiles that hold J lines x M8 angles and the window's step (J - 1) extra slices"}
         op.set_psf_model("collinear")
         # detection limit (Sec. 4.2, Fig. 5) of a synthetic sensitivity series at the
         # phantom scale: reconstruction with Eq. (26), box statistics on the GPU, line fit

@@ -61,6 +61,12 @@ struct GemmArgs {
     int nacc;            // accumulators in TMEM: K chunk kc adds into accumulator kc % nacc
     int acc_stride;      // TMEM columns between accumulators (a multiple of 32, >= BN)
     int b_tstride;       // K chunks per N tile in B's storage (0: nkc); B may be a K window of a table
+    // A pre-split in its canonical layout (NULL: the producer warps split g.A). 1 KB blocks
+    // (group of 8 rows, K chunk) ordered [chunk][hi, lo][group]; tile row group
+    // j * apk_gper + g (g < apk_gper, j < apk_jg) takes the blocks of group g at chunk
+    // apk_cbase + j * apk_cstep + kc, so each j is one contiguous copy per half.
+    const uint8_t *apk;
+    int apk_jg, apk_gper, apk_cbase, apk_cstep;
 };
 
 // The tensor-core accumulation into TMEM is not round-to-nearest FP32, so its error
@@ -129,7 +135,8 @@ __device__ __forceinline__ void gemm_body(const GemmArgs &g, int mt, int nt, uin
 
     if (tid == 0) {
         for (int s = 0; s < g.stages; ++s) {
-            ptx::mbar_init(&bars[s], kProdWarps + 1);  // producer warps + the B copy
+            // producer warps + the B copy, or the loader alone when A comes pre-split
+            ptx::mbar_init(&bars[s], g.apk ? 1 : kProdWarps + 1);
             ptx::mbar_init(&bars[g.stages + s], 1);
         }
         ptx::mbar_init(&bars[2 * g.stages], 1);
@@ -227,8 +234,8 @@ __device__ __forceinline__ void gemm_body(const GemmArgs &g, int mt, int nt, uin
         };
         bool ok = true;
         AChunk ca, cb;
-        load(0, ca);
-        for (int kc = 0; kc < g.nkc && ok; kc += 2) {
+        if (!g.apk) load(0, ca);
+        for (int kc = 0; kc < g.nkc && ok && !g.apk; kc += 2) {
             if (kc + 1 < g.nkc) load(kc + 1, cb);
             ok = produce(kc, ca);
             if (!ok || kc + 1 >= g.nkc) break;
@@ -322,15 +329,29 @@ __device__ __forceinline__ void gemm_body(const GemmArgs &g, int mt, int nt, uin
         // ------------------------------------------------------------ B loader
         if (lane == 0) {
             const uint8_t *bt = g.B + (size_t)nt * (g.b_tstride ? g.b_tstride : g.nkc) * 2 * bytesB;
+            // pre-split A: the row groups of this m tile that hold rows
+            const int rg0 = mt * (kBM / 8);
+            const int nrg = g.apk ? max(0, min(kBM / 8, g.apk_jg * g.apk_gper - rg0)) : 0;
             for (int kc = 0; kc < g.nkc; ++kc) {
                 const int s = kc % g.stages;
                 if (kc >= g.stages && !ptx::mbar_wait_bounded(&bars[g.stages + s], ((kc / g.stages) - 1) & 1, kWait)) {
                     atomicExch(flag, 1);
                     break;
                 }
-                uint8_t *sb = sm + s * stage + 2 * bytesA;
-                ptx::mbar_arrive_expect_tx(&bars[s], 2 * bytesB);
+                uint8_t *sa = sm + s * stage;
+                uint8_t *sb = sa + 2 * bytesA;
+                ptx::mbar_arrive_expect_tx(&bars[s], 2 * bytesB + 2048u * (uint32_t)nrg);
                 ptx::bulk_g2s(sb, bt + (size_t)kc * 2 * bytesB, 2 * bytesB, &bars[s]);
+                for (int r = 0; r < nrg;) {  // one copy per half for each run of one j
+                    const int rg = rg0 + r, j = rg / g.apk_gper, gg = rg - j * g.apk_gper;
+                    const int len = min(g.apk_gper - gg, nrg - r);
+                    const size_t c2 = 2 * (size_t)(g.apk_cbase + j * g.apk_cstep + kc);
+                    const uint8_t *hi = g.apk + (c2 * g.apk_gper + gg) * 1024u;
+                    const uint8_t *lo = g.apk + ((c2 + 1) * g.apk_gper + gg) * 1024u;
+                    ptx::bulk_g2s(sa + r * 1024u, hi, 1024u * len, &bars[s]);
+                    ptx::bulk_g2s(sa + bytesA + r * 1024u, lo, 1024u * len, &bars[s]);
+                    r += len;
+                }
             }
         }
         __syncwarp();
@@ -801,11 +822,12 @@ namespace {
 
 constexpr int kTenSplitK = 4096; // K per problem at most (64 bf16 chunks: 32 per accumulator)
 
-// N tile: the fewest tiles of at most 128 columns (two TMEM accumulators per block),
-// rounded up to 32 columns
+// N tile: the fewest tiles of at most 256 columns (one MMA), rounded up to 16. Fewer
+// tiles fetch the A rows fewer times; one block per SM holds up to 512 TMEM columns, two
+// accumulators of 256 or three of 160.
 int ten_bn(int Nv) {
-    const int tiles = (Nv + 127) / 128;
-    return std::min(128, ((Nv + tiles - 1) / tiles + 31) / 32 * 32);
+    const int tiles = (Nv + 255) / 256;
+    return std::min(256, ((Nv + tiles - 1) / tiles + 15) / 16 * 16);
 }
 
 struct TensorState {
@@ -816,13 +838,15 @@ struct TensorState {
     int Zp = 0, P0 = 0;        // padded slices per angle (a multiple of step), leading zeros
     int Tpre = 0;              // zero offsets in front of and behind each table (step (J - 1))
     double *Wd = nullptr;      // [n_par][Nz][2 n_b][N], offsets d >= 0
-    float *a_in = nullptr;     // [M][Zp][Np] coil-weighted projections, padded
-    float *a_data = nullptr;   // [M][Zp][Op] data rows, padded
+    int M8 = 0;                // angles rounded up to a multiple of 8 (rows of a shift j)
+    uint8_t *apk_f = nullptr;  // split A of the forward: coil-weighted projections, padded
+    uint8_t *apk_a = nullptr;  // split A of the adjoint: data rows, padded
+    int cm[2] = {0, 0};        // K chunks per angle row of apk_f / apk_a (current format)
     int nsplit[2] = {1, 1};    // K splits of the forward and adjoint problems
     int ksplit[2] = {0, 0};    // K per split (a multiple of 64)
     float *c_fwd = nullptr;    // [nsplit][M][Nz][2 n_b] partial sums
     float *c_adj = nullptr;    // [nsplit][M][Nz][N] partial sums
-    int *idx = nullptr;        // per problem group: M J A rows, then M J C rows
+    int *idx = nullptr;        // per problem group: M8 J A rows, then M8 J C rows
     GemmArgs *dargs = nullptr; // forward problems, then adjoint problems
     int n_prob_f = 0;
     int4 *ditems = nullptr;    // forward items, then adjoint items
@@ -942,6 +966,52 @@ __global__ void k_pack_b(Src src, int Nv, long long Kv, int BN, int ntile, int n
     }
 }
 
+// A operand of the tensor-PSF GEMMs, split once per call: row m (angle) of the padded
+// block holds K = Zp * per values, value (zp, c) = b[z][c] in[(m Nz + z) ncols + c] for
+// z = zp - P0 in [0, Nz) and c < ncols, else 0 (b NULL: 1). 1 KB blocks per (group of 8
+// angles, K chunk, half), ordered [chunk][hi, lo][group], each in the canonical layout
+// the producer warps write: core-matrix column kg at kg * 128, row r7 at r7 * 16. One
+// thread per 16-byte row of a block (8 bf16 or 4 tf32 values), split as the producers
+// split.
+__global__ void __launch_bounds__(256) k_pack_rows(const float *__restrict__ in, const float *__restrict__ coil,
+                                                   int M, int Nz, int ncols, int per, int P0, int Zp, int cm,
+                                                   int tf32, uint8_t *__restrict__ out) {
+    const int kpc = tf32 ? kBK / 2 : kBK, epk = tf32 ? 4 : 8;
+    const long long total = (long long)((M + 7) / 8) * cm * 64;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int kg = (int)(t & 7), r7 = (int)((t >> 3) & 7);
+        const long long gc = t >> 6;  // block: (angle group, chunk)
+        const int c = (int)(gc % cm), gq = (int)(gc / cm);
+        const int m = 8 * gq + r7;
+        float v[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            v[e] = 0.f;
+            if (e < epk && m < M) {
+                const long long k = (long long)c * kpc + kg * epk + e;
+                const int zp = (int)(k / per), col = (int)(k - (long long)zp * per);
+                const int z = zp - P0;
+                if (z >= 0 && z < Nz && col < ncols) {
+                    v[e] = __ldg(in + ((size_t)m * Nz + z) * ncols + col);
+                    if (coil) v[e] *= __ldg(coil + (size_t)z * ncols + col);
+                }
+            }
+        }
+        uint4 hi, lo;
+        if (tf32) {
+            const float f[4] = {v[0], v[1], v[2], v[3]};
+            split4_tf32(f, hi, lo);
+        } else {
+            split8(v, hi, lo);
+        }
+        const int G = (M + 7) / 8;
+        const uint32_t off = (uint32_t)kg * 128u + (uint32_t)r7 * 16u;
+        *reinterpret_cast<uint4 *>(out + ((2 * (size_t)c) * G + gq) * 1024u + off) = hi;
+        *reinterpret_cast<uint4 *>(out + ((2 * (size_t)c + 1) * G + gq) * 1024u + off) = lo;
+    }
+}
+
 template <class Src>
 bool pack_dev(Packed &p, Src src, int Nv, long long Kv, int BN, int tf32) {
     const int kpc = tf32 ? kBK / 2 : kBK;
@@ -1039,24 +1109,28 @@ bool ten_prepare(const mpi_ffl_handle *h, ColState *s, TensorState *t, int fmt) 
             return false;
     if (cudaDeviceSynchronize() != cudaSuccess) return false;
     const std::vector<int2> groups = ten_groups(d, t->step, t->J);
-    const int rows = d.M * t->J;
+    const int rows = t->M8 * t->J;  // tile rows (j, m), m padded to M8
+    t->cm[0] = t->Zp * t->Np / kpc;
+    t->cm[1] = t->Zp * t->Op / kpc;
     std::vector<int> idx(groups.size() * 2 * 2 * rows);
     std::vector<GemmArgs> args;
     std::vector<int4> items[2];
     const int mtiles = (rows + kBM - 1) / kBM;
     const int span = d.Nz + t->step * (t->J - 1);  // window slices (lines)
-    // both launches with the larger footprint: one block per SM measured faster than two
-    // for these long-K problems, whose producers are bound by the latency of their A loads
-    {
-        int st0 = 0, st1 = 0;
-        t->smem[0] = t->smem[1] = std::max(smem_for(t->fwd[0].BN, st0), smem_for(t->adj[0].BN, st1));
-    }
+    // one block per SM (it measured faster than two for these long-K problems), so the
+    // pipeline takes as many stages as fit: A and B both arrive by bulk copies
+    auto deep = [](int BN, int &stages) {
+        const size_t stage = 2u * kBM * kBK * 2 + 2u * BN * kBK * 2;
+        stages = (int)std::max<size_t>(2, std::min<size_t>(4, (220u * 1024u - 256u) / stage));
+        return stages * stage + 256;
+    };
+    int st_dir[2] = {0, 0};
+    t->smem[0] = t->smem[1] = std::max(deep(t->fwd[0].BN, st_dir[0]), deep(t->adj[0].BN, st_dir[1]));
     for (int dir = 0; dir < 2; ++dir) {
         const int per = dir ? t->Op : t->Np;  // K per line (adjoint) or per slice (forward)
         const int BN = dir ? t->adj[0].BN : t->fwd[0].BN;
         const size_t blk = (size_t)BN * kBK * 2;
-        int stages = 0;
-        smem_for(BN, stages);
+        const int stages = st_dir[dir];
         const int base = (int)args.size();
         for (size_t gi = 0; gi < groups.size(); ++gi) {
             const int l0 = groups[gi].x, Jg = groups[gi].y;
@@ -1064,11 +1138,11 @@ bool ten_prepare(const mpi_ffl_handle *h, ColState *s, TensorState *t, int fmt) 
             int *ar = idx.data() + ((size_t)dir * groups.size() + gi) * 2 * rows;
             int *cr = ar + rows;
             for (int j = 0; j < t->J; ++j)
-                for (int m = 0; m < d.M; ++m) {
-                    // row (j, m): the padded block of angle m from slice step (j + J - Jg)
-                    const int jj = std::min(j, Jg - 1);
-                    ar[j * d.M + m] = m * (t->Zp / t->step) + jj + t->J - Jg;
-                    cr[j * d.M + m] = j < Jg ? m * d.Nz + l0 + t->step * j : -1;
+                for (int m = 0; m < t->M8; ++m) {
+                    // row (j, m): angle m's padded block from slice step (j + J - Jg); the
+                    // A row list only gives the gain (A comes pre-split)
+                    ar[j * t->M8 + m] = m < d.M ? m : 0;
+                    cr[j * t->M8 + m] = (j < Jg && m < d.M) ? m * d.Nz + l0 + t->step * j : -1;
                 }
             const int *dar = t->idx + (ar - idx.data());
             const int *dcr = t->idx + (cr - idx.data());
@@ -1079,11 +1153,16 @@ bool ten_prepare(const mpi_ffl_handle *h, ColState *s, TensorState *t, int fmt) 
                 const int k0 = ks * t->ksplit[dir];
                 const int kn = std::min(t->ksplit[dir], span * per - k0);
                 GemmArgs g{};
-                g.A = (dir ? t->a_data : t->a_in) + k0;
-                g.lda = (int64_t)t->step * per;
+                g.A = nullptr;
+                g.lda = 0;
                 g.Ka = kn;
                 g.arow = dar;
                 g.M = rows;
+                g.apk = dir ? t->apk_a : t->apk_f;
+                g.apk_jg = Jg;
+                g.apk_gper = t->M8 / 8;
+                g.apk_cbase = (t->step * (t->J - Jg) * per + k0) / kpc;
+                g.apk_cstep = t->step * per / kpc;
                 g.B = B.dev + (size_t)((kwin + k0) / kpc) * 2 * blk;
                 g.BN = BN;
                 g.nkc = kn / kpc;
@@ -1093,11 +1172,17 @@ bool ten_prepare(const mpi_ffl_handle *h, ColState *s, TensorState *t, int fmt) 
                 g.crow = dcr;
                 g.Nc = dir ? d.N : R;
                 g.rscale = h->t_gain;
-                g.rdiv = t->Zp / t->step;  // A row / rdiv = angle
+                g.rdiv = 1;  // A row list = angle
                 g.prec = h->precision;
                 g.tf32 = fmt;
                 g.stages = stages;
-                set_accumulators(g);
+                // one block per SM: up to 512 TMEM columns, at most 4 accumulators
+                g.acc_stride = (g.BN + 31) / 32 * 32;
+                g.nacc = std::max(1, std::min({4, 512 / g.acc_stride, g.nkc}));
+                {
+                    const int cols = g.nacc * g.acc_stride;
+                    g.tmem_cols = cols <= 32 ? 32 : cols <= 64 ? 64 : cols <= 128 ? 128 : cols <= 256 ? 256 : 512;
+                }
                 g.err = s->err;
                 g.done = nullptr;
                 const int pi = (int)args.size() - base;
@@ -1132,7 +1217,7 @@ void ten_release(ColState *s) {
     for (int p = 0; p < 2; ++p)
         for (Packed *pk : {&t->fwd[p], &t->adj[p]})
             if (pk->dev) cudaFree(pk->dev);
-    for (void *p : {(void *)t->Wd, (void *)t->a_in, (void *)t->a_data, (void *)t->c_fwd, (void *)t->c_adj,
+    for (void *p : {(void *)t->Wd, (void *)t->apk_f, (void *)t->apk_a, (void *)t->c_fwd, (void *)t->c_adj,
                     (void *)t->idx, (void *)t->dargs, (void *)t->ditems})
         if (p) cudaFree(p);
     delete t;
@@ -1150,7 +1235,8 @@ int ten_init(mpi_ffl_handle *h) {
     t->Np = (d.N + kBK - 1) / kBK * kBK;
     t->Op = (R + kBK - 1) / kBK * kBK;
     t->step = s->n_par;
-    t->J = std::max(1, std::min(kBM / d.M, (d.Nz + t->step - 1) / t->step));
+    t->M8 = (d.M + 7) / 8 * 8;
+    t->J = std::max(1, std::min(kBM / t->M8, (d.Nz + t->step - 1) / t->step));
     t->P0 = t->step * (t->J - 1);
     t->Tpre = t->step * (t->J - 1);
     t->Zp = (d.Nz + 2 * t->P0 + t->step - 1) / t->step * t->step;
@@ -1165,14 +1251,13 @@ int ten_init(mpi_ffl_handle *h) {
         t->nsplit[dir] = (K + t->ksplit[dir] - 1) / t->ksplit[dir];
     }
     const size_t ng = ten_groups(d, t->step, t->J).size();
-    bool ok = talloc(&t->a_in, (size_t)d.M * t->Zp * t->Np) && talloc(&t->a_data, (size_t)d.M * t->Zp * t->Op) &&
+    // split A: 2 KB per (8 angles, K chunk); a tf32 chunk holds 32 values, a bf16 one 64
+    const size_t blocks_f = (size_t)(t->M8 / 8) * (t->Zp * t->Np / (kBK / 2));
+    const size_t blocks_a = (size_t)(t->M8 / 8) * (t->Zp * t->Op / (kBK / 2));
+    bool ok = talloc(&t->apk_f, blocks_f * 2048) && talloc(&t->apk_a, blocks_a * 2048) &&
               talloc(&t->c_fwd, (size_t)t->nsplit[0] * d.M * d.Nz * R) &&
               talloc(&t->c_adj, (size_t)t->nsplit[1] * d.M * d.Nz * d.N) &&
-              talloc(&t->idx, ng * 2 * 2 * (size_t)d.M * t->J);
-    if (ok) {  // the padding slices stay zero: only the interior is ever written
-        ok = cudaMemset(t->a_in, 0, (size_t)d.M * t->Zp * t->Np * sizeof(float)) == cudaSuccess &&
-             cudaMemset(t->a_data, 0, (size_t)d.M * t->Zp * t->Op * sizeof(float)) == cudaSuccess;
-    }
+              talloc(&t->idx, ng * 2 * 2 * (size_t)t->M8 * t->J);
     ok = ok && ten_build_wd(h, s, t) && ten_prepare(h, s, t, h->precision == MPI_FFL_PREC_TF32 ? 1 : 0);
     if (!ok) {
         ten_release(s);
@@ -1201,13 +1286,21 @@ int ten_refresh(mpi_ffl_handle *h, bool psf_changed) {
     return MPI_FFL_OK;
 }
 
-// proj -> data: coil-weighted, padded A rows; the GEMM problems; sum of the K splits
+void ten_pack(TensorState *t, const float *in, const float *coil, int M, int Nz, int ncols, int per, int dir,
+              cudaStream_t st) {
+    const long long total = (long long)(t->M8 / 8) * t->cm[dir] * 64;
+    const int blocks = (int)std::min<long long>((total + 255) / 256, 152LL * 16);
+    k_pack_rows<<<std::max(1, blocks), 256, 0, st>>>(in, coil, M, Nz, ncols, per, t->P0, t->Zp, t->cm[dir], t->fmt,
+                                                    dir ? t->apk_a : t->apk_f);
+}
+
+// proj -> data: coil-weighted, padded A rows split once; the GEMM problems; sum of the K splits
 void ten_forward(mpi_ffl_handle *h, const float *proj, const float *coil, float *data, cudaStream_t st) {
     ColState *s = cs(h);
     TensorState *t = s->ten;
     const Dims &d = h->d;
     const long long rows = (long long)d.M * d.Nz;
-    launch_coil_pad(proj, coil, t->a_in, rows, d.Nz, d.N, t->Np, st, 1, 0, t->Zp, t->P0);
+    ten_pack(t, proj, coil, d.M, d.Nz, d.N, t->Np, 0, st);
     k_gemm_batch<<<t->n_items_f, kGemmThreads, t->smem[0], st>>>(t->dargs, t->ditems);
     launch_coil_pad(t->c_fwd, nullptr, data, rows, d.Nz, 2 * d.nb, 2 * d.nb, st, t->nsplit[0], rows * 2 * d.nb);
 }
@@ -1218,7 +1311,7 @@ void ten_adjoint(mpi_ffl_handle *h, const float *data, const float *coil, float 
     TensorState *t = s->ten;
     const Dims &d = h->d;
     const long long rows = (long long)d.M * d.Nz;
-    launch_coil_pad(data, nullptr, t->a_data, rows, d.Nz, 2 * d.nb, t->Op, st, 1, 0, t->Zp, t->P0);
+    ten_pack(t, data, nullptr, d.M, d.Nz, 2 * d.nb, t->Op, 1, st);
     k_gemm_batch<<<t->n_items_a, kGemmThreads, t->smem[1], st>>>(t->dargs + t->n_prob_f, t->ditems + t->n_items_f);
     launch_coil_pad(t->c_adj, coil, proj, rows, d.Nz, d.N, d.N, st, t->nsplit[1], rows * d.N);
 }
