@@ -76,6 +76,28 @@ def test_tensor_operator_and_transpose(name, precision):
     assert rel_l2(xa, tensor_psf.adjoint(y, st, coil.astype(np.float64))) < OP_TOL
 
 
+def test_tensor_with_more_angles_than_a_tile():
+    """130 angles: one line per problem and A rows over two 128-row tiles."""
+    from paper_2511_06627_gb300 import FFLOperator
+
+    kw = dict(nx=16, nz=5, n_angles=130, S=24, P=10, A=3.0, phi0=0.2, zigzag=1, Q=4, fwhm=2.0,
+              k_min=1, k_max=3, half_width=1)
+    gains = np.linspace(0.9, 1.1, 130).astype(np.float32)
+    st = Setup(**kw, gains=gains.astype(np.float64))
+    op = FFLOperator(**kw, gains=gains)
+    op.set_path("full_gemm")
+    op.set_psf_model("tensor")
+    coil = _coil(st, 31)
+    op.set_coil_map(coil)
+    x = random_volume(st.nz, st.nx, seed=32).astype(np.float32)
+    y = _data(st, 33).astype(np.complex64)
+    b = op.forward(_t(x)).cpu().numpy()
+    xa = op.adjoint(_t(to_interleaved(y))).cpu().numpy()
+    op.sync_check()
+    assert rel_l2(b, to_interleaved(tensor_psf.forward(x, st, coil.astype(np.float64)))) < OP_TOL
+    assert rel_l2(xa, tensor_psf.adjoint(y, st, coil.astype(np.float64))) < OP_TOL
+
+
 def test_tensor_adjoint_identity_and_model_switch():
     st, op = _make("ragged")
     x = _t(random_volume(st.nz, st.nx, seed=24))
