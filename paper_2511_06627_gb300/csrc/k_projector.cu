@@ -211,8 +211,13 @@ __device__ __forceinline__ void project_pipe_body(const float *__restrict__ vol,
             float *dst = psm + k * kZc * LD + kPad;
             if (lane == 0) ptx::mbar_arrive_expect_tx(&bars[k], row_bytes * nz);
             __syncwarp();
-            if (lane < nz)
+            if (lane < nz) {
+                // the consumers read the stage with ordinary loads (generic proxy) and
+                // the bulk copy writes it through the async proxy: the empty barrier
+                // orders the two only with this fence between them
+                ptx::fence_proxy_async_smem();
                 ptx::bulk_g2s(dst + lane * LD, src + ((size_t)(z0 + lane) * N + s) * N, row_bytes, &bars[k]);
+            }
         }
         return;
     }
@@ -328,13 +333,15 @@ size_t il_len(int N, int Nz) { return (size_t)((Nz + kZc - 1) / kZc) * kZc * N *
 // volI[zb][y][x][e] and volTI[zb][x][y][e] = vol[kZc zb + e][y][x] (zero past Nz), halves
 // swapped as above. A block of 8 x 32 threads moves a 32 x 32 tile of one slice block:
 // thread (tx, ty) loads 4 consecutive x of row ty of every slice (eight 16-byte loads;
-// N % 4 == 0), forms each position's 8 slices in registers and writes them to volI
-// directly. For volTI the tile goes through shared memory as 16-byte halves: half h of
-// tile row r, column c sits at 16-byte slot 64 r + 8 (c >> 2) + ((2 (c & 3) + h) ^ sw),
-// sw = ((c >> 2) ^ (r >> 2)) & 7. The row's stores (c = 4 tx + q) and the transposed
-// loads (r = 4 tx + q) then take 8 distinct bank groups per 8 lanes.
+// N % 4 == 0) and forms each position's two halves in registers. The tile goes through
+// shared memory as 16-byte halves: half h of tile row r, column c sits at 16-byte slot
+// 64 r + 8 (c >> 2) + ((2 (c & 3) + h) ^ sw), sw = (c >> 2) ^ 2 (r & 3). Both copies are
+// then written from the tile, 32 consecutive 16-byte units of one output row per warp
+// (full 128-byte lines). Every 8-lane phase takes 8 distinct bank groups: the row stores
+// (c = 4 tx + q, tx over the lanes), the row reads (four aligned positions, both halves)
+// and the column reads (four aligned rows of one column, both halves).
 __device__ __forceinline__ int il_tile_slot(int r, int c, int h) {
-    return 64 * r + 8 * (c >> 2) + ((2 * (c & 3) + h) ^ (((c >> 2) ^ (r >> 2)) & 7));
+    return 64 * r + 8 * (c >> 2) + ((2 * (c & 3) + h) ^ (((c >> 2) ^ (2 * (r & 3))) & 7));
 }
 
 __global__ void __launch_bounds__(256) k_interleave(const float *__restrict__ vol, float *__restrict__ volI,
@@ -360,29 +367,29 @@ __global__ void __launch_bounds__(256) k_interleave(const float *__restrict__ vo
         const float f5 = q == 0 ? v[5].x : q == 1 ? v[5].y : q == 2 ? v[5].z : v[5].w;
         const float f6 = q == 0 ? v[6].x : q == 1 ? v[6].y : q == 2 ? v[6].z : v[6].w;
         const float f7 = q == 0 ? v[7].x : q == 1 ? v[7].y : q == 2 ? v[7].z : v[7].w;
-        const float4 lo = make_float4(f0, f1, f2, f3), hi = make_float4(f4, f5, f6, f7);
-        const int c = 4 * tx + q, x = x0 + c;
-        tile[il_tile_slot(ty, c, 0)] = lo;
-        tile[il_tile_slot(ty, c, 1)] = hi;
-        if (y < N && x < N) {  // volI: row y, position x
-            const int sw = il_swap(x + kPad);
-            float4 *o = reinterpret_cast<float4 *>(volI + (((size_t)zb * N + y) * N + x) * kZc);
-            o[sw] = lo;
-            o[1 - sw] = hi;
-        }
+        const int c = 4 * tx + q;
+        tile[il_tile_slot(ty, c, 0)] = make_float4(f0, f1, f2, f3);
+        tile[il_tile_slot(ty, c, 1)] = make_float4(f4, f5, f6, f7);
     }
     __syncthreads();
+    // thread t writes 16-byte unit j = t mod 64 (position j / 2, stored half j mod 2) of
+    // tile rows (volI) or tile columns (volTI) 4 i + t / 64
+    const int t = ty * 8 + tx, j = t & 63, c = j >> 1, m = j & 1;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {  // volTI: row x0 + ty, position y0 + 4 tx + q
-        const int r = 4 * tx + q;
-        const int x = x0 + ty, yy = y0 + r;
-        const float4 lo = tile[il_tile_slot(r, ty, 0)], hi = tile[il_tile_slot(r, ty, 1)];
-        if (yy < N && x < N) {
-            const int sw = il_swap(yy + kPad);
-            float4 *o = reinterpret_cast<float4 *>(volTI + (((size_t)zb * N + x) * N + yy) * kZc);
-            o[sw] = lo;
-            o[1 - sw] = hi;
-        }
+    for (int i = 0; i < 8; ++i) {
+        const int r = 4 * i + (t >> 6);
+        const int yy = y0 + r, x = x0 + c;  // volI: row yy, position x
+        if (yy < N && x < N)
+            reinterpret_cast<float4 *>(volI + (((size_t)zb * N + yy) * N + x) * kZc)[m] =
+                tile[il_tile_slot(r, c, m ^ il_swap(x + kPad))];
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int r = 4 * i + (t >> 6);
+        const int xr = x0 + r, yp = y0 + c;  // volTI: row xr, position yp (tile row c, column r)
+        if (xr < N && yp < N)
+            reinterpret_cast<float4 *>(volTI + (((size_t)zb * N + xr) * N + yp) * kZc)[m] =
+                tile[il_tile_slot(c, r, m ^ il_swap(yp + kPad))];
     }
 }
 
@@ -432,6 +439,10 @@ __global__ void __launch_bounds__(1024 + 32) k_project_il(const float *__restric
                     atomicExch(err, 1);
                     break;
                 }
+                // generic-proxy reads of the stage, then its async-proxy refill: without
+                // this fence some consumers read the next step's data (the sums then
+                // changed from run to run)
+                ptx::fence_proxy_async_smem();
                 ptx::mbar_arrive_expect_tx(&bars[k], step_bytes);
                 ptx::bulk_g2s(psm + ((size_t)k * LDC + kPad) * kZc, src + (size_t)s * N * kZc, step_bytes, &bars[k]);
             }
