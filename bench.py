@@ -16,6 +16,9 @@ precomputed per trajectory, on tensor cores in split bf16 with FP32 accuracy);
 reconstruction, `serving` the continuous-batching run of the serving workload
 against one-at-a-time plain FP32.
 
+K defaults to 3000 pairs, about a second of device time, so that the 200 ms clock
+samples fall inside the timed region; the other paths take at most 20 steps each.
+
 --impl reference times the FP64 CPU oracle on the host cores on a bounded
 sample of the same workload (a subset of angles), scaled to pairs/s.
 """
@@ -79,8 +82,12 @@ class ClockSampler:
                  "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
+            t0 = time.perf_counter()  # nvidia-smi takes a moment to start: wait for its first line
+            while not self.lines and self.proc.poll() is None and time.perf_counter() - t0 < 5.0:
+                time.sleep(0.01)
         except Exception:
             self.proc = None
+        self.first = len(self.lines)  # samples taken before the timed region are not counted
         return self
 
     def _read(self):
@@ -99,7 +106,7 @@ class ClockSampler:
     def summary(self):
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ln in self.lines[getattr(self, "first", 0):]:
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 7:
                 continue
@@ -152,6 +159,11 @@ def over_ranks(values_ms, dist, device="cuda"):
     t = torch.tensor([float(v) for v in values_ms], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return [float(v) for v in t.tolist()]
+
+
+def aux_steps(args):
+    """Steps for the secondary measurements (other paths, dual drive, tensor PSF)."""
+    return max(3, min(args.steps, 40) // 2)
 
 
 def whole_job_rate(units_per_rank, world, max_ms):
@@ -218,9 +230,9 @@ SMEM_BYTES_PER_CLK_SM = 128
 # profiles/projector_il_invivo.md (cold caches, 256^2x128, 36 angles). Reported only
 # for that workload and only while the kernel is the one that was captured.
 DRAM_TRAFFIC = {
-    "project": 67_128_064 + 1_369_088,    # reads both interleaved copies of the volume
+    "project": 67_126_528 + 1_161_472,    # reads both interleaved copies of the volume
     "backproject": 4_732_160 + 1_024,     # reads the projections; the volume it writes stays in L2
-    "transpose": 33_926_912 + 13_372_928,  # interleave pass: most of its writes stay in L2
+    "transpose": 33_571_072 + 7_517_952,  # interleave pass: most of its writes stay in L2
 }
 
 
@@ -596,8 +608,8 @@ def run_ours(args, cfg, rank, world, local_rank):
                 continue
             for _ in range(2):
                 step()
-            pm = _timed_pairs(op, x, b, xa, max(3, args.steps // 2), flush, stream)
-            n = max(3, args.steps // 2)
+            pm = _timed_pairs(op, x, b, xa, aux_steps(args), flush, stream)
+            n = aux_steps(args)
             paths[key] = {"pairs_per_s": n / (pm / 1e3), "ms_per_pair": pm / n}
         use_path(op, path)
     plain = paths.get("staged", {}).get("pairs_per_s")
@@ -687,7 +699,7 @@ def run_ours(args, cfg, rank, world, local_rank):
 
         for _ in range(2):
             dual_step()
-        n_dual = max(3, args.steps // 2)
+        n_dual = aux_steps(args)
         d_starts = [torch.cuda.Event(enable_timing=True) for _ in range(n_dual)]
         d_ends = [torch.cuda.Event(enable_timing=True) for _ in range(n_dual)]
         for k in range(n_dual):
@@ -731,7 +743,7 @@ def run_ours(args, cfg, rank, world, local_rank):
         for _ in range(2):
             op.forward(x, out=b)
             op.adjoint(b, out=xa)
-        n_ten = max(3, args.steps // 2)
+        n_ten = aux_steps(args)
         ten_ms = _timed_pairs(op, x, b, xa, n_ten, flush, stream) / n_ten
         op.profile(True)
         op.profile_read()
@@ -887,7 +899,9 @@ def cpu_baseline_leg(cfg, x_np, op, args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: 3000 A+A^T pairs, about a second, so that the clock "
+                         "sampler sees the load; 20 oracle samples with --impl reference)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--path", default=None,
@@ -905,6 +919,8 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     cfg = config(args.workload)
+    if args.steps is None:
+        args.steps = 20 if args.impl == "reference" else 3000
     if args.impl == "reference":
         run_reference(args, cfg, rank)
         return
