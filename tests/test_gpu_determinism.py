@@ -1,7 +1,8 @@
 """Run-to-run determinism on the GPU: every kernel of A, A^T and the solve sums in a
 fixed order (no atomics), so repeating a call on the same input must give the same
 bits. Checked at the full 256^2 x 128, 36-angle size on the staged and full-GEMM
-paths, stage by stage, and for a short solve."""
+paths, stage by stage, for a short solve, for the tensor-PSF operator and for the
+z-drive scan."""
 
 import pytest
 
@@ -64,3 +65,22 @@ def test_solve_repeats_bit_for_bit(op_x):
     bad = _repeat(lambda: op.solve(b, iters=30, ata_norm=norms[0], report=False)[0], n=2)
     op.sync_check()
     assert not bad, f"solve changed between calls: {bad}"
+
+
+def test_tensor_psf_and_zdrive_repeat_bit_for_bit(op_x):
+    """The slice-coupled tensor-PSF GEMMs (pre-split A staged by bulk copies, fixed-order
+    sum of the K splits) and the fused z-drive kernels at the same size."""
+    op, x = op_x
+    op.set_path("full_gemm")
+    op.set_psf_model("tensor")
+    try:
+        b = op.forward(x).clone()
+        bad = {name: r for name, fn in {"tensor forward": lambda: op.forward(x),
+                                        "tensor adjoint": lambda: op.adjoint(b)}.items() if (r := _repeat(fn))}
+    finally:
+        op.set_psf_model("collinear")
+    bz = op.forward_zdrive(x).clone()
+    bad.update({name: r for name, fn in {"z forward": lambda: op.forward_zdrive(x),
+                                         "z adjoint": lambda: op.adjoint_zdrive(bz)}.items() if (r := _repeat(fn))})
+    op.sync_check()
+    assert not bad, f"results changed between calls (elements, max |diff|): {bad}"
