@@ -33,6 +33,12 @@
  *   NULL = legacy default stream); calls return without waiting for the GPU unless
  *   stated. A handle may be used from one stream at a time.
  *
+ * Determinism
+ *   No kernel uses atomics; every sum runs in a fixed order. Repeating a call with
+ *   the same handle settings on the same input gives the same bits, on every path
+ *   and precision, for A, A^T, the stages, the z-drive scan, the power norm and the
+ *   solve.
+ *
  * Errors
  *   Every call returns 0 on success or a negative MPI_FFL_ERR_* code; nothing
  *   throws or aborts across the ABI. mpi_ffl_last_error() gives a message for the
