@@ -468,9 +468,61 @@ struct ColState {
     int nrows[2] = {0, 0};
     int *err = nullptr;
     int n_par = 1;
+    // A of the full line stage split once per call (forward: projections, adjoint: data),
+    // per direction and trajectory, sized for the tf32 chunk count
+    uint8_t *apk[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
 };
 
 ColState *cs(const mpi_ffl_handle *h) { return reinterpret_cast<ColState *>(h->col_state); }
+
+// Rows of one trajectory's full line stage for k_pack_lines.
+struct PackLines {
+    const int *arow;  // line index of each row
+    int M;            // rows
+    uint8_t *out;     // 1 KB blocks [chunk][hi, lo][group of 8 rows]
+};
+
+// A rows of the full line stage, split once per call into the canonical layout the
+// producer warps would write, as k_pack_rows does for the tensor PSF: row r of
+// trajectory blockIdx.y is line arow[r] of in (stride lda, Ka valid values, zero past
+// Ka and past the last row). One thread per 16-byte row of a block (8 bf16 or 4 tf32
+// values), split exactly as the producers split.
+__global__ void __launch_bounds__(256) k_pack_lines(const float *__restrict__ in, int64_t lda, int Ka, int nkc,
+                                                    int tf32, PackLines p0, PackLines p1) {
+    const PackLines p = blockIdx.y ? p1 : p0;
+    const int kpc = tf32 ? kBK / 2 : kBK, epk = tf32 ? 4 : 8;
+    const int G = (p.M + 7) / 8;
+    const long long total = (long long)G * nkc * 64;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int kg = (int)(t & 7), r7 = (int)((t >> 3) & 7);
+        const long long gc = t >> 6;  // block: (row group, chunk), row group fastest
+        const int gq = (int)(gc % G), c = (int)(gc / G);
+        const int r = 8 * gq + r7;
+        const int line = r < p.M ? __ldg(p.arow + r) : -1;
+        const float *src = line >= 0 ? in + (size_t)line * lda : nullptr;
+        const int k0 = c * kpc + kg * epk;
+        float v[8];
+        if (src && epk == 8 && k0 + 8 <= Ka && (lda % 4) == 0 && (reinterpret_cast<uintptr_t>(in) & 15) == 0) {
+            const float4 a = __ldg(reinterpret_cast<const float4 *>(src + k0));
+            const float4 b = __ldg(reinterpret_cast<const float4 *>(src + k0 + 4));
+            v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w, v[4] = b.x, v[5] = b.y, v[6] = b.z, v[7] = b.w;
+        } else {
+#pragma unroll
+            for (int e = 0; e < 8; ++e) v[e] = (src && e < epk && k0 + e < Ka) ? __ldg(src + k0 + e) : 0.f;
+        }
+        uint4 hi, lo;
+        if (tf32) {
+            const float f[4] = {v[0], v[1], v[2], v[3]};
+            split4_tf32(f, hi, lo);
+        } else {
+            split8(v, hi, lo);
+        }
+        const uint32_t off = (uint32_t)kg * 128u + (uint32_t)r7 * 16u;
+        *reinterpret_cast<uint4 *>(p.out + ((2 * (size_t)c) * G + gq) * 1024u + off) = hi;
+        *reinterpret_cast<uint4 *>(p.out + ((2 * (size_t)c + 1) * G + gq) * 1024u + off) = lo;
+    }
+}
 
 bool upload_packed(Packed &p, const std::vector<uint8_t> &v) {
     if (cudaMalloc((void **)&p.dev, v.size()) != cudaSuccess) {
@@ -690,6 +742,11 @@ void col_init(mpi_ffl_handle *h) {
                 if ((d.n_par == 1 ? 0 : (z & 1)) == par) rows.push_back(m * d.Nz + z);
         s->nrows[par] = (int)rows.size();
         if (cudaMalloc((void **)&s->rows[par], rows.size() * sizeof(int)) != cudaSuccess) return;
+        for (int dir = 0; dir < 2; ++dir) {  // K = N (forward) or 2 n_b (adjoint), tf32 chunks of 32
+            const int kmax = dir ? 2 * d.nb : d.N;
+            const size_t bytes = (size_t)((kmax + kBK / 2 - 1) / (kBK / 2)) * 2 * ((rows.size() + 7) / 8) * 1024;
+            if (cudaMalloc((void **)&s->apk[dir][par], std::max<size_t>(bytes, 1024)) != cudaSuccess) return;
+        }
         cudaMemcpy(s->rows[par], rows.data(), rows.size() * sizeof(int), cudaMemcpyHostToDevice);
     }
     if (cudaMalloc((void **)&s->err, sizeof(int)) != cudaSuccess) return;
@@ -712,6 +769,8 @@ void col_release(mpi_ffl_handle *h) {
             for (Packed *pk : {&s->evf_f[f][p], &s->evf_a[f][p], &s->full_f[f][p], &s->full_a[f][p]})
                 if (pk->dev) cudaFree(pk->dev);
         if (s->rows[p]) cudaFree(s->rows[p]);
+        for (int dir = 0; dir < 2; ++dir)
+            if (s->apk[dir][p]) cudaFree(s->apk[dir][p]);
     }
     if (s->err) cudaFree(s->err);
     delete s;
@@ -727,6 +786,28 @@ int col_take_error(mpi_ffl_handle *h) {
     return v;
 }
 
+// Splits the A rows of the full line stage once (k_pack_lines, one launch for both
+// trajectories) and points the problems at them: the loader warp then stages A with one
+// bulk copy per half next to B's, and the producer warps only run the epilogue.
+static void pack_full(mpi_ffl_handle *h, int dir, const float *in, GemmArgs *g, cudaStream_t st) {
+    ColState *s = cs(h);
+    PackLines pl[2] = {};
+    for (int par = 0; par < s->n_par; ++par) {
+        pl[par] = PackLines{g[par].arow, g[par].M, s->apk[dir][par]};
+        g[par].apk = s->apk[dir][par];
+        g[par].apk_jg = 1;
+        g[par].apk_gper = (g[par].M + 7) / 8;
+        g[par].apk_cbase = 0;
+        g[par].apk_cstep = 0;
+    }
+    const int G = (std::max(g[0].M, s->n_par > 1 ? g[1].M : 0) + 7) / 8;
+    const long long work = (long long)G * g[0].nkc * 64;
+    const int blocks = (int)std::min<long long>(4 * 152, (work + 255) / 256);
+    k_pack_lines<<<dim3(std::max(1, blocks), s->n_par), 256, 0, st>>>(in, g[0].lda, g[0].Ka, g[0].nkc, g[0].tf32, pl[0],
+                                                                       pl[1]);
+    h->launches++;  // a second kernel inside the caller's timed GEMM stage
+}
+
 // fine -> data (W) or proj -> data (W H), gain per line
 void col_forward(mpi_ffl_handle *h, const float *in, bool full, const float *gain, float *data, cudaStream_t st) {
     ColState *s = cs(h);
@@ -739,6 +820,7 @@ void col_forward(mpi_ffl_handle *h, const float *in, bool full, const float *gai
         g[par] = make_args(h, in, full ? d.N : d.Ne, full ? d.N : d.Ne, s->rows[par], s->nrows[par], *B[par], data,
                            2 * d.nb, s->rows[par], 2 * d.nb, gain, d.Nz);
     }
+    if (full) pack_full(h, 0, in, g, st);
     launch_problems(g, B, s->n_par, st);
 }
 
@@ -755,6 +837,7 @@ void col_adjoint(mpi_ffl_handle *h, const float *data, bool full, const float *g
         g[par] = make_args(h, data, 2 * d.nb, 2 * d.nb, s->rows[par], s->nrows[par], *B[par], out, nout, s->rows[par],
                            nout, gain, d.Nz);
     }
+    if (full) pack_full(h, 1, data, g, st);
     launch_problems(g, B, s->n_par, st);
 }
 
