@@ -1,7 +1,7 @@
 """Run-to-run determinism on the GPU: every kernel of A, A^T and the solve sums in a
 fixed order (no atomics), so repeating a call on the same input must give the same
-bits. Checked at the full 256^2 x 128, 36-angle size on the staged and full-GEMM
-paths, stage by stage, for a short solve, for the tensor-PSF operator and for the
+bits. Checked at the full 256^2 x 128, 36-angle size on every path (staged, fused,
+line-GEMM, full-GEMM), stage by stage, for a short solve, for the tensor-PSF operator and for the
 z-drive scan."""
 
 import pytest
@@ -37,7 +37,7 @@ def _repeat(fn, n=3):
     return bad
 
 
-@pytest.mark.parametrize("path", ["staged", "full_gemm"])
+@pytest.mark.parametrize("path", ["staged", "fused", "line_gemm", "full_gemm"])
 def test_operators_repeat_bit_for_bit(op_x, path):
     op, x = op_x
     op.set_path(path)
