@@ -142,6 +142,34 @@ def oracle_pair_seconds(cfg, x, n_angles_sample):
     return per_pair, f"A+A^T of {n_angles_sample} of {cfg['n_angles']} angles, scaled by {cfg['n_angles']}/{n_angles_sample}"
 
 
+def oracle_recon_seconds(power_iters=50):
+    """Seconds per reconstruction of the FP64 oracle (power iteration for tau, then the
+    workload's iterations of Eq. (26)): measured in full on the tiny workload, and
+    extrapolated on the phantom-scale one from the measured time of A+A^T on one angle
+    x angles x (power iterations + solve iterations)."""
+    from oracle import Setup, operator, solver
+    from oracle.data import make_data
+
+    out = {}
+    cfg = config("tiny")
+    st = Setup.from_config(cfg)
+    b, _ = make_data(st, phantom_for(cfg), noise=cfg["noise"], seed=cfg["seed"])
+    shape = (st.nz, st.nx, st.nx)
+    t0 = time.perf_counter()
+    ata = solver.power_norm(lambda v: operator.adjoint(operator.forward(v, st), st), shape, n_iter=power_iters)
+    lam = solver.default_lambda(ata, shape)
+    solver.solve(lambda v: operator.forward(v, st), lambda r: operator.adjoint(r, st), b, shape,
+                 solver.step_size(ata, lam, shape), lam, cfg["iters"])
+    out["tiny"] = {"s_per_recon": time.perf_counter() - t0, "iters": cfg["iters"], "power_iters": power_iters,
+                   "how": "measured"}
+    cfg = config("phantom")
+    per_pair, _ = oracle_pair_seconds(cfg, phantom_for(cfg).astype(np.float64), 1)
+    out["phantom"] = {"s_per_recon": per_pair * (power_iters + cfg["iters"]), "iters": cfg["iters"],
+                      "power_iters": power_iters,
+                      "how": "extrapolated: A+A^T of one angle measured, x angles x (power + solve iterations)"}
+    return out
+
+
 def cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -172,24 +200,44 @@ def whole_job_rate(units_per_rank, world, max_ms):
 
 
 def run_reference(args, cfg, rank):
+    """The reference arm: the FP64 oracle on the host cores. One step is A + A^T
+    restricted to one FFL angle (angles taken in turn), 1/M of a full pair, so that K
+    steps run in seconds; the value is full pairs per second, 1 / (M x median time
+    per step)."""
     if rank != 0:
         return
+    from oracle import Setup, operator
+
     x = phantom_for(cfg).astype(np.float64)
-    sample = max(1, min(cfg["n_angles"], args.oracle_angles))
-    oracle_pair_seconds(cfg, x, 1) if args.warmup > 0 else None  # warm caches / FFT plans
+    st = Setup.from_config(cfg)
+    rng = np.random.default_rng(5)
+    M = cfg["n_angles"]
+
+    def angle_step(m):
+        fs = operator.forward_stages(x, st, angles=np.array([m]))
+        y = fs["data"] + 0.01 * (rng.standard_normal(fs["data"].shape) + 1j * rng.standard_normal(fs["data"].shape))
+        operator.adjoint_stages(y, st, angles=np.array([m]))
+
+    for w in range(args.warmup):  # caches and FFT plans
+        angle_step(w % M)
     times = []
-    text = ""
-    for _ in range(args.steps):
-        t, text = oracle_pair_seconds(cfg, x, sample)
-        times.append(t)
-    per = statistics.median(times)
-    value = 1.0 / per
+    t_run = time.perf_counter()
+    for k in range(args.steps):
+        t0 = time.perf_counter()
+        angle_step(k % M)
+        times.append(time.perf_counter() - t0)
+    t_run = time.perf_counter() - t_run
+    per_step = statistics.median(times)
+    value = 1.0 / (per_step * M)
+    sample = (f"each step is A+A^T of one of the {M} angles (angles in turn, 1/{M} of a pair); "
+              f"value = 1 / ({M} x median step time), an extrapolation from the measured per-angle time")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": workload_desc(cfg)},
-        "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": cores(), "kind": "oracle", "sample": text},
+        "config": {"workload": workload_desc(cfg), "step": f"A+A^T restricted to one FFL angle (1/{M} of a pair)"},
+        "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": cores(), "kind": "oracle", "sample": sample,
+                         "measured_s_per_angle_step": per_step, "wall_s_timed_steps": t_run},
         "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -218,13 +266,12 @@ ALGO_BYTES = {
 
 # Shared-memory bytes the projector pair reads per launch: two interpolation taps of
 # 4 bytes for every (angle, ray, march step, slice) sample, M N N N_z = M n_vox samples. Both
-# kernels stage their operand in shared memory and are bound by its bandwidth, whose
-# peak is 128 B per clock per SM.
+# kernels stage their operand in shared memory and are bound by its bandwidth, held
+# against the bandwidth the library's probe kernel measures.
 SMEM_BYTES = {
     "project": lambda d: 8 * d["M"] * d["nvox"],
     "backproject": lambda d: 8 * d["M"] * d["nvox"],
 }
-SMEM_BYTES_PER_CLK_SM = 128
 
 # DRAM bytes (read + write) per launch from the ncu capture summarised in
 # profiles/projector_il_invivo.md (cold caches, 256^2x128, 36 angles). Reported only
@@ -256,15 +303,29 @@ def bf16_peak_tflops():
         return 1900.0, "fallback"
 
 
-def kernel_rooflines(prof, d, hbm, sm_mhz):
-    """Per kernel kind of the timed region: achieved algorithmic HBM GB/s against the
-    measured copy peak; for the projector pair also the shared-memory roofline; for the
-    GEMMs the tensor rate (3 products of 2 M N K flops) against the peak of the operand
-    type (measured bf16; tf32 from it by the nominal ratio)."""
+def smem_peak_gbs():
+    """Shared-memory read bandwidth of this GPU in GB/s, measured by the library's probe
+    kernel (conflict-free 16-byte loads on every SM, CUDA events)."""
+    import ctypes as C
+
     import torch
 
-    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
-    sm_peak = SMEM_BYTES_PER_CLK_SM * n_sm * sm_mhz * 1e6 / 1e9
+    from paper_2511_06627_gb300 import _lib
+
+    lib = _lib.load()
+    v = C.c_double(0.0)
+    rc = lib.mpi_ffl_probe_smem_bandwidth(C.byref(v), C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    if rc != _lib.OK:
+        raise RuntimeError(f"shared-memory probe failed: {rc}")
+    return v.value
+
+
+def kernel_rooflines(prof, d, hbm, sm_peak):
+    """Per kernel kind of the timed region: achieved algorithmic HBM GB/s against the
+    measured copy peak; for the projector pair also the shared-memory roofline against
+    the measured shared-memory bandwidth; for the GEMMs the tensor rate (3 products of
+    2 M N K flops, and the method's own single product) against the peak of the operand
+    type (measured bf16; tf32 from it by the nominal ratio)."""
     bf16, _ = bf16_peak_tflops()
     nz = d["nvox"] // (d["N"] * d["N"])
     nseg = d["M"] * nz
@@ -283,6 +344,7 @@ def kernel_rooflines(prof, d, hbm, sm_mhz):
             flops = 3 * 2 * nseg * (d["ndata"] // nseg) * rows_k
             e["tensor_tflops"] = flops / sec / 1e12
             e["tensor_frac"] = e["tensor_tflops"] / tensor_peak
+            e["method_tensor_frac"] = e["tensor_frac"] / 3  # one product of the method's 2 M N K
         out[k] = {kk: round(vv, 5) for kk, vv in e.items()}
     return out
 
@@ -576,23 +638,26 @@ def run_ours(args, cfg, rank, world, local_rank):
 
     # ---- roofline of the dominant kernel (times measured inside the timed region)
     hbm, src = peaks()
+    sm_peak = smem_peak_gbs()
     top = max((k for k in prof if prof[k][1] > 0 and k != "solver"), key=lambda k: prof[k][0])
     per_launch_ms = prof[top][0] / prof[top][1]
     algo = ALGO_BYTES[top](dict(dims, path=path))
     achieved = algo / (per_launch_ms / 1e3) / 1e9
-    onchip = None
+    traffic = DRAM_TRAFFIC.get(top) if args.workload == "invivo" and path.startswith("full_gemm") else None
+    roofline = {"kernel": top, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": traffic,
+                "peak_source": f"{src}: hbm_gbs of MEASURED_PEAKS.json (STREAM-style copy)",
+                "algorithmic_bytes_per_launch": algo, "avg_launch_ms": per_launch_ms}
     if top in SMEM_BYTES:
-        sm_mhz = clk.summary().get("sm_mhz") or 2070.0
-        n_sm = torch.cuda.get_device_properties(0).multi_processor_count
-        sm_peak = SMEM_BYTES_PER_CLK_SM * n_sm * sm_mhz * 1e6 / 1e9
         sm_bytes = SMEM_BYTES[top](dims)
         sm_ach = sm_bytes / (per_launch_ms / 1e3) / 1e9
-        onchip = {"bound": "smem", "achieved": sm_ach, "peak": sm_peak, "unit": "GB/s", "frac": sm_ach / sm_peak,
-                  "bytes_per_launch": sm_bytes,
-                  "peak_basis": f"{SMEM_BYTES_PER_CLK_SM} B/clk/SM x {n_sm} SMs x median SM clock {sm_mhz} MHz"}
-    traffic = DRAM_TRAFFIC.get(top) if args.workload == "invivo" and path.startswith("full_gemm") else None
+        roofline["smem"] = {"achieved": sm_ach, "peak": sm_peak, "unit": "GB/s", "frac": sm_ach / sm_peak,
+                            "bytes_per_launch": sm_bytes,
+                            "peak_source": "measured: mpi_ffl_probe_smem_bandwidth (conflict-free 16-byte loads)"}
+        roofline["note"] = ("the projector pair reads each voxel once from HBM but every interpolation tap from "
+                            "shared memory: it is bound on chip by shared-memory bandwidth (see smem), not by HBM")
     kernel_share = {k: round(v[0] / max(ms_prof, 1e-9), 4) for k, v in prof.items() if v[1] > 0}
-    kernel_roof = kernel_rooflines(prof, dict(dims, path=path), hbm, clk.summary().get("sm_mhz") or 2070.0)
+    kernel_roof = {path: kernel_rooflines(prof, dict(dims, path=path), hbm, sm_peak)}
     kernel_ms = {k: round(v[0] / v[1], 4) for k, v in prof.items() if v[1] > 0}
 
     # ---- the other evaluation paths of the same operator (same inputs, same timing rules)
@@ -611,6 +676,12 @@ def run_ours(args, cfg, rank, world, local_rank):
             pm = _timed_pairs(op, x, b, xa, aux_steps(args), flush, stream)
             n = aux_steps(args)
             paths[key] = {"pairs_per_s": n / (pm / 1e3), "ms_per_pair": pm / n}
+            # the same steps with the library's per-launch events: every kernel's roofline
+            op.profile(True)
+            op.profile_read()
+            _timed_pairs(op, x, b, xa, n, flush, stream)
+            kernel_roof[key] = kernel_rooflines(op.profile_read(), dict(dims, path=key), hbm, sm_peak)
+            op.profile(False)
         use_path(op, path)
     plain = paths.get("staged", {}).get("pairs_per_s")
 
@@ -625,19 +696,10 @@ def run_ours(args, cfg, rank, world, local_rank):
         "config": {"workload": workload_desc(cfg), "path": path,
                    "l2": "flushed (256 MB write) between timed steps",
                    "step": "b = A x then x' = A^T b, inputs resident in HBM"},
-        # the projector pair is bound by shared-memory bandwidth, not HBM: its roofline is
-        # the shared-memory one (peak from the SM count, 128 B/clk/SM and the measured
-        # clock); the HBM figures are kept beside it, with the DRAM traffic of the capture
-        "roofline": ({"kernel": top, "bound": "smem", "achieved": onchip["achieved"], "peak": onchip["peak"],
-                      "unit": "GB/s", "frac": onchip["frac"], "traffic": traffic,
-                      "peak_source": "derived: " + onchip["peak_basis"],
-                      "algorithmic_bytes_per_launch": onchip["bytes_per_launch"], "avg_launch_ms": per_launch_ms,
-                      "hbm": {"achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                              "peak_source": src, "algorithmic_bytes_per_launch": algo}}
-                     if onchip else
-                     {"kernel": top, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                      "frac": achieved / hbm, "traffic": traffic, "peak_source": src,
-                      "algorithmic_bytes_per_launch": algo, "avg_launch_ms": per_launch_ms}),
+        # HBM roofline of the dominant kernel on its algorithmic bytes (inputs read once,
+        # outputs written once) against the measured copy peak; for the projector pair
+        # the shared-memory roofline against the measured shared-memory bandwidth beside it
+        "roofline": roofline,
         "kernel_time_share": kernel_share,
         "profiled_ms_per_step": ms_prof / args.steps,
         "kernel_ms_per_launch": kernel_ms,
@@ -681,6 +743,28 @@ def run_ours(args, cfg, rank, world, local_rank):
             rec["rel_l2_vs_staged_fp32"] = {p: float((xs[p].double() - ref_x).norm() / ref_x.norm())
                                             for p in xs if p != "staged"}
         rec["note"] = "tau from a 20-step power iteration done before the timed solve"
+        # the tiny and phantom-scale workloads, timed like the oracle's s/recon: the
+        # 50-step power iteration for tau, then the workload's iterations of Eq. (26)
+        small = {}
+        for wname in ("tiny", "phantom"):
+            cw = config(wname)
+            ow = FFLOperator.from_config(cw)
+            xw = torch.from_numpy(phantom_for(cw)).cuda()
+            bw = ow.forward(xw).clone()
+            small[wname] = {"iters": cw["iters"], "power_iters": 50}
+            for p in ("full_gemm", "staged"):
+                use_path(ow, p)
+                ow.solve(bw, iters=2, n_power=2, report=False)
+                torch.cuda.synchronize()
+                r0 = torch.cuda.Event(enable_timing=True)
+                r1 = torch.cuda.Event(enable_timing=True)
+                r0.record(stream)
+                ow.solve(bw, iters=cw["iters"], n_power=50, report=False)
+                r1.record(stream)
+                torch.cuda.synchronize()
+                small[wname][p] = r0.elapsed_time(r1) / 1e3
+            ow.close()
+        rec["s_per_recon_smaller_workloads"] = small
         result["recon"] = rec
         use_path(op, path)
     if not args.quick:
@@ -890,6 +974,7 @@ def cpu_baseline_leg(cfg, x_np, op, args):
         stages[name] = worst
     del cur
     return {"value": 1.0 / per, "unit": "pairs/s", "cores": cores(), "kind": "oracle", "sample": text,
+            "s_per_recon": oracle_recon_seconds(),
             "gpu_error_vs_oracle": errs,
             "staged_error_per_stage": stages,
             "error_sample": f"angles {sample}: A x on the phantom and A^T y for random y on each angle alone, "

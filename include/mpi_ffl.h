@@ -427,8 +427,12 @@ int mpi_ffl_job_destroy(mpi_ffl_job *j);
  * cudaMalloc, cudaFree or allocating library routine.
  *
  * The first call on a device looks up the array's device address on the current
- * device (cudaGetSymbolAddress) once; make that first call before any stream
- * capture. Every call on a device shares the array and leaves its partial sums
+ * device (cudaGetSymbolAddress) once and keeps it for the life of the process; make
+ * that first call before any stream capture. The kept address does not survive a
+ * cudaDeviceReset of that device: a process that resets a device must not call this
+ * entry point on it afterwards. A launch error is returned as MPI_FFL_ERR_CUDA; an
+ * error that an earlier runtime call left pending on the calling thread is left
+ * pending, not reported as this call's. Every call on a device shares the array and leaves its partial sums
  * there; each call writes all the partials it reads before reading them, so nothing
  * has to be cleared between calls. Calls whose work overlaps on the GPU (on
  * different streams, unordered) race on the array and give wrong results: order
@@ -437,8 +441,40 @@ int mpi_ffl_job_destroy(mpi_ffl_job *j);
 #define MPI_FFL_NOALLOC_MAX_N ((int64_t)MPI_FFL_NOALLOC_MAX_PARTIALS * 1024)
 int mpi_ffl_dot_f64_noalloc(const float *d_a, const float *d_b, int64_t n, double *d_out, void *stream);
 
+/* ---- Failure-detection test hooks (not part of the method) ----------------------
+ * These let a test drive the library's error paths without faulting or hanging the
+ * GPU: the failures are made on the host (an allocation reported as failed) or by a
+ * bounded wait on a barrier that nothing arrives at. The paper has no counterpart.
+ *
+ * Every device allocation of the library goes through one wrapper. With nth > 0 the
+ * nth allocation from now (counted across the process and all handles) fails as
+ * cudaMalloc fails on a full device, without allocating; the caller sees
+ * MPI_FFL_ERR_OOM and must have freed everything it allocated before. 0 disables the
+ * countdown (its state after it fired). Negative nth: MPI_FFL_ERR_INVALID_ARG. */
+int mpi_ffl_test_fail_alloc(int32_t nth);
+/* Device allocations of the library currently live in this process, and their bytes
+ * (count and/or bytes may be NULL): a leak check for the tests. */
+int mpi_ffl_test_live_allocs(int64_t *count, int64_t *bytes);
+/* With polls > 0, the handle's next interleaved-projector (P) and full/line-GEMM
+ * launches do no work: before issuing any copy or MMA, every thread of every block
+ * waits at most `polls` polls on a barrier that nothing arrives at, then the block
+ * records a timeout (freeing its TMEM where it holds some) and returns, exactly as a
+ * block whose pipeline stalled past the kernels' own limit of 2^24 polls does. The
+ * results of those calls are undefined; mpi_ffl_sync_check then returns
+ * MPI_FFL_ERR_TIMEOUT, clears the flag and disarms the hook, and the handle is usable
+ * again. polls = 0 disarms it; polls > 2^24 is MPI_FFL_ERR_INVALID_ARG. Launches of
+ * other paths and kernels are unaffected. */
+int mpi_ffl_test_inject_timeout(mpi_ffl_handle *h, uint32_t polls);
+
 /* ---- Measurement hooks (not part of the method) ----------------------------------
- * Kernel kinds for the per-kernel timers below. */
+ * Measured shared-memory read bandwidth of the current device in GB/s: several waves
+ * of blocks on every SM read 16-byte words from shared memory in a conflict-free
+ * pattern; the best of five timed launches (CUDA events on `stream`, after a warm-up
+ * launch). It allocates and frees a small output buffer and synchronises the stream.
+ * The projector pair's on-chip roofline is held against this number. */
+int mpi_ffl_probe_smem_bandwidth(double *gbs, void *stream);
+
+/* Kernel kinds for the per-kernel timers below. */
 #define MPI_FFL_K_TRANSPOSE 0     /* volume x/y transpose for column-marched angles */
 #define MPI_FFL_K_PROJECT 1       /* P                                              */
 #define MPI_FFL_K_BACKPROJECT 2   /* P^T                                            */

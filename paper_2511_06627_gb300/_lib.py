@@ -132,6 +132,10 @@ PROTOTYPES = {
     "mpi_ffl_job_poll": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.c_void_p, ST]),
     "mpi_ffl_job_result": (C.c_int, [C.c_void_p, FP, ST]),
     "mpi_ffl_job_destroy": (C.c_int, [C.c_void_p]),
+    "mpi_ffl_test_fail_alloc": (C.c_int, [C.c_int32]),
+    "mpi_ffl_test_live_allocs": (C.c_int, [C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+    "mpi_ffl_test_inject_timeout": (C.c_int, [H, C.c_uint32]),
+    "mpi_ffl_probe_smem_bandwidth": (C.c_int, [C.POINTER(C.c_double), ST]),
 }
 
 KERNEL_KINDS = ["transpose", "project", "backproject", "psf_fwd", "psf_adj", "resample_fwd", "resample_adj",

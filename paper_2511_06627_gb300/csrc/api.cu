@@ -92,7 +92,7 @@ struct KTimer {
 template <class T>
 void dev_alloc(mpi_ffl_handle *h, T **p, size_t n) {
     if (n == 0) n = 1;
-    cudaError_t e = cudaMalloc((void **)p, n * sizeof(T));
+    cudaError_t e = dev_malloc((void **)p, n * sizeof(T));
     if (e != cudaSuccess) {
         *p = nullptr;
         cudaGetLastError();
@@ -367,19 +367,19 @@ void release(mpi_ffl_handle *h) {
                     h->s_xp, h->s_y, h->s_g, h->s_r, h->s_hist, h->s_flags, h->tc_twb, h->t_agroups,
                     h->t_tnf, h->t_vr, h->w_err, h->t_coil, h->w_projc, h->w_scanvol, h->w_volI, h->w_volTI};
     for (void *p : ptrs)
-        if (p) cudaFree(p);
+        if (p) dev_free(p);
     for (auto &r : h->prof_rec) {
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);
     }
     for (auto e : h->ev_pool) cudaEventDestroy(e);
     for (float *p : {h->hs_in[0], h->hs_in[1], h->hs_out})
-        if (p) cudaFree(p);
+        if (p) dev_free(p);
     for (void *p : {(void *)h->tz_ua, (void *)h->tz_n0, (void *)h->tz_plo, (void *)h->tz_phi, (void *)h->tz_tap_ptr,
                     (void *)h->tz_f0, (void *)h->tz_v, (void *)h->tz_taps, (void *)h->tz_optr, (void *)h->tz_otap,
                     (void *)h->w_zcoef, (void *)h->w_fine_z,
                     (void *)h->w_projT, (void *)h->w_tz})
-        if (p) cudaFree(p);
+        if (p) dev_free(p);
     for (int k = 0; k < 2; ++k) {
         if (h->hs_ready[k]) cudaEventDestroy(h->hs_ready[k]);
         if (h->hs_free[k]) cudaEventDestroy(h->hs_free[k]);
@@ -470,7 +470,7 @@ void stage_p(mpi_ffl_handle *h, const float *x, float *proj, cudaStream_t st) {
     if (h->w_volI) {  // the interleaved projector: both orientations from one pass over x
         TIMED(MPI_FFL_K_TRANSPOSE, launch_interleave(x, h->w_volI, h->w_volTI, h->d.N, h->d.Nz, st));
         TIMED(MPI_FFL_K_PROJECT, launch_project_il(h->w_volI, h->w_volTI, h->t_ang, h->t_agroups, h->n_agroups, proj,
-                                                   h->d.N, h->d.Nz, st, h->w_err));
+                                                   h->d.N, h->d.Nz, st, h->w_err, h->inject_polls));
         check_launch(h, "project");
         return;
     }
@@ -786,6 +786,10 @@ extern "C" int mpi_ffl_create(const mpi_ffl_geometry *geom, const mpi_ffl_trajec
         dev_alloc(h, &h->w_err, 1);
         CK(cudaMemset(h->w_err, 0, sizeof(int)));
         tc_init(h);
+        if (tc_init_oom(h)) {
+            set_err(h, "device allocation failed for the tensor-core tables");
+            throw Fail{MPI_FFL_ERR_OOM};
+        }
         CK(cudaDeviceSynchronize());
     } catch (const Fail &e) {
         if (g_create_error.empty()) g_create_error = h->err.empty() ? "create failed" : h->err;
@@ -874,7 +878,13 @@ static int set_path_impl(mpi_ffl_handle *h, int32_t path) {
         try {
             col_init(h);  // W and W H are built on first use
         } catch (...) {
+            col_release(h);
             h->err = "building the collapsed line operator failed";
+            return MPI_FFL_ERR_OOM;
+        }
+        if (col_init_oom(h)) {  // nothing of a failed build is kept: the next call retries
+            col_release(h);
+            h->err = "device allocation failed while building the collapsed line operator";
             return MPI_FFL_ERR_OOM;
         }
     }
@@ -938,7 +948,7 @@ extern "C" int mpi_ffl_set_coil_map(mpi_ffl_handle *h, const float *b_zu) {
         const Dims &d = h->d;
         CK(cudaDeviceSynchronize());
         if (!b_zu) {
-            if (h->t_coil) CK(cudaFree(h->t_coil));
+            if (h->t_coil) CK(dev_free(h->t_coil));
             h->t_coil = nullptr;
             return MPI_FFL_OK;
         }
@@ -970,8 +980,8 @@ extern "C" int mpi_ffl_set_scans(mpi_ffl_handle *h, int32_t scans) {
             dev_alloc(h, &r, (size_t)2 * d.ndata);
             dev_alloc(h, &w, (size_t)2 * d.ndata);
             dev_alloc(h, &h->w_scanvol, (size_t)2 * d.nvox);
-            CK(cudaFree(h->s_r));
-            CK(cudaFree(h->w_data));
+            CK(dev_free(h->s_r));
+            CK(dev_free(h->w_data));
             h->bytes -= (int64_t)(2 * d.ndata * sizeof(float));
             h->s_r = r;
             h->w_data = w;
@@ -1039,6 +1049,7 @@ extern "C" int mpi_ffl_set_psf_fwhm(mpi_ffl_handle *h, double fwhm) {
 extern "C" int mpi_ffl_sync_check(mpi_ffl_handle *h, void *stream) {
     return guarded(h, [&]() {
         CK(cudaStreamSynchronize(S(stream)));
+        h->inject_polls = 0;
         int werr = 0;
         CK(cudaMemcpy(&werr, h->w_err, sizeof(int), cudaMemcpyDeviceToHost));
         if (werr) CK(cudaMemset(h->w_err, 0, sizeof(int)));
@@ -1046,6 +1057,17 @@ extern "C" int mpi_ffl_sync_check(mpi_ffl_handle *h, void *stream) {
             h->err = "a tensor-core kernel gave up on a bounded wait";
             return MPI_FFL_ERR_TIMEOUT;
         }
+        return MPI_FFL_OK;
+    });
+}
+
+extern "C" int mpi_ffl_test_inject_timeout(mpi_ffl_handle *h, uint32_t polls) {
+    return guarded(h, [&]() {
+        if (polls > (1u << 24)) {
+            h->err = "polls above the kernels' own limit of 2^24";
+            return MPI_FFL_ERR_INVALID_ARG;
+        }
+        h->inject_polls = polls;
         return MPI_FFL_OK;
     });
 }
@@ -1449,7 +1471,7 @@ extern "C" int mpi_ffl_solve(mpi_ffl_handle *h, const float *d_b, float *d_x, co
         const double lam = p->lambda >= 0.0 ? p->lambda : 1e-3 * ata / tn;
         const double tau = p->tau > 0.0 ? p->tau : 1.0 / (ata + lam * tn);
         if (h->s_hist_len < p->iters + 1) {
-            if (h->s_hist) cudaFree(h->s_hist);
+            if (h->s_hist) dev_free(h->s_hist);
             h->s_hist = nullptr;
             dev_alloc(h, &h->s_hist, (size_t)p->iters + 1);
             h->s_hist_len = p->iters + 1;

@@ -65,7 +65,7 @@ bool staging_ready(size_t need) {
     for (int i = 0; i < 2; ++i) {
         if (s.ev[i]) cudaEventSynchronize(s.ev[i]);
         if (s.host[i]) cudaFreeHost(s.host[i]);
-        if (s.dev[i]) cudaFree(s.dev[i]);
+        if (s.dev[i]) dev_free(s.dev[i]);
         if (s.ev[i]) cudaEventDestroy(s.ev[i]);
         s.host[i] = s.dev[i] = nullptr;
         s.ev[i] = nullptr;
@@ -73,7 +73,7 @@ bool staging_ready(size_t need) {
     s.cap = std::max<size_t>(need, 1 << 20);
     for (int i = 0; i < 2; ++i) {
         if (cudaMallocHost((void **)&s.host[i], s.cap) != cudaSuccess) return false;
-        if (cudaMalloc((void **)&s.dev[i], s.cap) != cudaSuccess) return false;
+        if (dev_malloc((void **)&s.dev[i], s.cap) != cudaSuccess) return false;
         if (cudaEventCreateWithFlags(&s.ev[i], cudaEventDisableTiming) != cudaSuccess) return false;
     }
     s.dev_id = dev;
@@ -97,7 +97,7 @@ size_t put(std::vector<uint8_t> &buf, const std::vector<T> &v) {
 void free_job(mpi_ffl_job *j) {
     void *ptrs[] = {j->x, j->xp, j->y, j->g, j->r, j->b, j->hist, j->partials, j->flags};
     for (void *p : ptrs)
-        if (p) cudaFree(p);
+        if (p) dev_free(p);
 }
 
 }  // namespace
@@ -121,7 +121,7 @@ extern "C" int mpi_ffl_job_create(mpi_ffl_handle *h, const float *d_b, const flo
     j->nblk = std::max(1, std::min(1024, (int)((d.ndata + 4095) / 4096)));
     j->col_angles = handle_has_column_angles(h);
     auto alloc = [&](void **ptr, size_t bytes) {
-        if (cudaMalloc(ptr, bytes) != cudaSuccess) {
+        if (dev_malloc(ptr, bytes) != cudaSuccess) {
             cudaGetLastError();
             return false;
         }

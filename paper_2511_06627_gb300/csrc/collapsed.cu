@@ -67,6 +67,10 @@ struct GemmArgs {
     // apk_cbase + j * apk_cstep + kc, so each j is one contiguous copy per half.
     const uint8_t *apk;
     int apk_jg, apk_gper, apk_cbase, apk_cstep;
+    // failure-detection test hook: > 0 makes every block wait this many polls on the
+    // final-MMA barrier before any copy or MMA is issued (so nothing ever arrives
+    // there), record a timeout and free its TMEM (mpi_ffl_test_inject_timeout)
+    uint32_t inject;
 };
 
 // The tensor-core accumulation into TMEM is not round-to-nearest FP32, so its error
@@ -151,8 +155,15 @@ __device__ __forceinline__ void gemm_body(const GemmArgs &g, int mt, int nt, uin
     __syncthreads();
     ptx::tc_fence_after();
     const uint32_t tmem = *tslot;
+    ptx::grid_dep_wait();  // A (and the output rows) belong to earlier kernels of the stream
+    ptx::grid_dep_launch();
 
-    if (warp < kProdWarps) {
+    if (g.inject > 0) {
+        // test hook: no role runs, so the final-MMA barrier never completes and every
+        // thread's bounded wait on it runs out; the block then records a timeout and
+        // frees its TMEM below like a block whose pipeline stalled
+        if (!ptx::mbar_wait_bounded(&bars[2 * g.stages], 0, g.inject) && lane == 0) atomicExch(flag, 1);
+    } else if (warp < kProdWarps) {
         // ------------------------------------------------------------ A producers
         // Warp w fills row groups 2w and 2w+1 (rows 16w..16w+15). In one pass a lane
         // takes row 8rg + (lane & 7) and 16-byte core-matrix row kg = 4kh + (lane >> 3)
@@ -471,6 +482,7 @@ struct ColState {
     // A of the full line stage split once per call (forward: projections, adjoint: data),
     // per direction and trajectory, sized for the tf32 chunk count
     uint8_t *apk[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    bool oom = false;  // the shape is supported but a device allocation failed
 };
 
 ColState *cs(const mpi_ffl_handle *h) { return reinterpret_cast<ColState *>(h->col_state); }
@@ -490,6 +502,8 @@ struct PackLines {
 __global__ void __launch_bounds__(256) k_pack_lines(const float *__restrict__ in, int64_t lda, int Ka, int nkc,
                                                     int tf32, PackLines p0, PackLines p1) {
     const PackLines p = blockIdx.y ? p1 : p0;
+    ptx::grid_dep_wait();  // the rows come from the previous kernel
+    ptx::grid_dep_launch();
     const int kpc = tf32 ? kBK / 2 : kBK, epk = tf32 ? 4 : 8;
     const int G = (p.M + 7) / 8;
     const long long total = (long long)G * nkc * 64;
@@ -525,7 +539,7 @@ __global__ void __launch_bounds__(256) k_pack_lines(const float *__restrict__ in
 }
 
 bool upload_packed(Packed &p, const std::vector<uint8_t> &v) {
-    if (cudaMalloc((void **)&p.dev, v.size()) != cudaSuccess) {
+    if (dev_malloc((void **)&p.dev, v.size()) != cudaSuccess) {
         p.dev = nullptr;
         return false;
     }
@@ -565,6 +579,7 @@ GemmArgs make_args(const mpi_ffl_handle *h, const float *A, int64_t lda, int Ka,
     set_accumulators(g);
     g.err = cs(h)->err;
     g.done = nullptr;
+    g.inject = h->inject_polls;
     return g;
 }
 
@@ -582,8 +597,12 @@ void launch_problems(const GemmArgs *g, const Packed *const *B, int n, cudaStrea
     }
     const int n0 = mt0 * B[0]->ntile;
     const int n1 = (g[1].M + kBM - 1) / kBM * B[1]->ntile;
-    if (tf32) k_gemm_pair<1><<<n0 + n1, kGemmThreads, smem, st>>>(g[0], g[1], B[0]->ntile, n0, B[1]->ntile);
-    else k_gemm_pair<0><<<n0 + n1, kGemmThreads, smem, st>>>(g[0], g[1], B[0]->ntile, n0, B[1]->ntile);
+    if (tf32)
+        launch_dependent(k_gemm_pair<1>, dim3(n0 + n1), dim3(kGemmThreads), smem, st, g[0], g[1], B[0]->ntile, n0,
+                         B[1]->ntile);
+    else
+        launch_dependent(k_gemm_pair<0>, dim3(n0 + n1), dim3(kGemmThreads), smem, st, g[0], g[1], B[0]->ntile, n0,
+                         B[1]->ntile);
 }
 
 }  // namespace
@@ -732,8 +751,10 @@ void col_init(mpi_ffl_handle *h) {
             return bn;
         };
         if (!mk(s->evf_f, Wr, R, d.Ne, pick_bn(R)) || !mk(s->evf_a, Wt, d.Ne, R, pick_bn(d.Ne)) ||
-            !mk(s->full_f, WH, R, d.N, pick_bn(R)) || !mk(s->full_a, WHt, d.N, R, pick_bn(d.N)))
+            !mk(s->full_f, WH, R, d.N, pick_bn(R)) || !mk(s->full_a, WHt, d.N, R, pick_bn(d.N))) {
+            s->oom = true;
             return;
+        }
         s->W[par] = std::move(Wr);
         // lines of this trajectory
         std::vector<int> rows;
@@ -741,15 +762,24 @@ void col_init(mpi_ffl_handle *h) {
             for (int z = 0; z < d.Nz; ++z)
                 if ((d.n_par == 1 ? 0 : (z & 1)) == par) rows.push_back(m * d.Nz + z);
         s->nrows[par] = (int)rows.size();
-        if (cudaMalloc((void **)&s->rows[par], rows.size() * sizeof(int)) != cudaSuccess) return;
+        if (dev_malloc((void **)&s->rows[par], rows.size() * sizeof(int)) != cudaSuccess) {
+            s->oom = true;
+            return;
+        }
         for (int dir = 0; dir < 2; ++dir) {  // K = N (forward) or 2 n_b (adjoint), tf32 chunks of 32
             const int kmax = dir ? 2 * d.nb : d.N;
             const size_t bytes = (size_t)((kmax + kBK / 2 - 1) / (kBK / 2)) * 2 * ((rows.size() + 7) / 8) * 1024;
-            if (cudaMalloc((void **)&s->apk[dir][par], std::max<size_t>(bytes, 1024)) != cudaSuccess) return;
+            if (dev_malloc((void **)&s->apk[dir][par], std::max<size_t>(bytes, 1024)) != cudaSuccess) {
+                s->oom = true;
+                return;
+            }
         }
         cudaMemcpy(s->rows[par], rows.data(), rows.size() * sizeof(int), cudaMemcpyHostToDevice);
     }
-    if (cudaMalloc((void **)&s->err, sizeof(int)) != cudaSuccess) return;
+    if (dev_malloc((void **)&s->err, sizeof(int)) != cudaSuccess) {
+        s->oom = true;
+        return;
+    }
     cudaMemset(s->err, 0, sizeof(int));
     for (const void *k : {(const void *)k_gemm_split<0>, (const void *)k_gemm_split<1>, (const void *)k_gemm_pair<0>,
                           (const void *)k_gemm_pair<1>})
@@ -767,14 +797,19 @@ void col_release(mpi_ffl_handle *h) {
     for (int p = 0; p < 2; ++p) {
         for (int f = 0; f < 2; ++f)
             for (Packed *pk : {&s->evf_f[f][p], &s->evf_a[f][p], &s->full_f[f][p], &s->full_a[f][p]})
-                if (pk->dev) cudaFree(pk->dev);
-        if (s->rows[p]) cudaFree(s->rows[p]);
+                if (pk->dev) dev_free(pk->dev);
+        if (s->rows[p]) dev_free(s->rows[p]);
         for (int dir = 0; dir < 2; ++dir)
-            if (s->apk[dir][p]) cudaFree(s->apk[dir][p]);
+            if (s->apk[dir][p]) dev_free(s->apk[dir][p]);
     }
-    if (s->err) cudaFree(s->err);
+    if (s->err) dev_free(s->err);
     delete s;
     h->col_state = nullptr;
+}
+
+bool col_init_oom(const mpi_ffl_handle *h) {
+    const ColState *s = cs(h);
+    return s && s->oom;
 }
 
 int col_take_error(mpi_ffl_handle *h) {
@@ -803,8 +838,8 @@ static void pack_full(mpi_ffl_handle *h, int dir, const float *in, GemmArgs *g, 
     const int G = (std::max(g[0].M, s->n_par > 1 ? g[1].M : 0) + 7) / 8;
     const long long work = (long long)G * g[0].nkc * 64;
     const int blocks = (int)std::min<long long>(4 * 152, (work + 255) / 256);
-    k_pack_lines<<<dim3(std::max(1, blocks), s->n_par), 256, 0, st>>>(in, g[0].lda, g[0].Ka, g[0].nkc, g[0].tf32, pl[0],
-                                                                       pl[1]);
+    launch_dependent(k_pack_lines, dim3(std::max(1, blocks), s->n_par), dim3(256), 0, st, in, g[0].lda, g[0].Ka,
+                     g[0].nkc, g[0].tf32, pl[0], pl[1]);
     h->launches++;  // a second kernel inside the caller's timed GEMM stage
 }
 
@@ -1102,9 +1137,9 @@ bool pack_dev(Packed &p, Src src, int Nv, long long Kv, int BN, int tf32) {
     p.ntile = (Nv + BN - 1) / BN;
     p.nkc = (int)((Kv + kpc - 1) / kpc);
     const size_t bytes = (size_t)p.ntile * p.nkc * 2 * BN * kBK * 2;
-    if (p.dev) cudaFree(p.dev);
+    if (p.dev) dev_free(p.dev);
     p.dev = nullptr;
-    if (cudaMalloc((void **)&p.dev, bytes) != cudaSuccess) {
+    if (dev_malloc((void **)&p.dev, bytes) != cudaSuccess) {
         p.dev = nullptr;
         cudaGetLastError();
         return false;
@@ -1130,7 +1165,7 @@ double h_uu_host(double u, double z, double a) {
 
 template <class T>
 bool talloc(T **p, size_t n) {
-    if (cudaMalloc((void **)p, std::max<size_t>(1, n) * sizeof(T)) != cudaSuccess) {
+    if (dev_malloc((void **)p, std::max<size_t>(1, n) * sizeof(T)) != cudaSuccess) {
         *p = nullptr;
         cudaGetLastError();
         return false;
@@ -1162,8 +1197,8 @@ bool ten_build_wd(const mpi_ffl_handle *h, ColState *s, TensorState *t) {
             dW, dg, t->Wd, R, d.Ne, d.N, d.Nz, d.D, d.Q, kmin, Lk);
         ok = cudaDeviceSynchronize() == cudaSuccess;
     }
-    if (dW) cudaFree(dW);
-    if (dg) cudaFree(dg);
+    if (dW) dev_free(dW);
+    if (dg) dev_free(dg);
     cudaGetLastError();
     return ok;
 }
@@ -1281,8 +1316,8 @@ bool ten_prepare(const mpi_ffl_handle *h, ColState *s, TensorState *t, int fmt) 
     t->n_items_f = (int)items[0].size();
     t->n_items_a = (int)items[1].size();
     items[0].insert(items[0].end(), items[1].begin(), items[1].end());
-    if (t->dargs) cudaFree(t->dargs);
-    if (t->ditems) cudaFree(t->ditems);
+    if (t->dargs) dev_free(t->dargs);
+    if (t->ditems) dev_free(t->ditems);
     t->dargs = nullptr;
     t->ditems = nullptr;
     if (!talloc(&t->dargs, args.size()) || !talloc(&t->ditems, items[0].size())) return false;
@@ -1299,10 +1334,10 @@ void ten_release(ColState *s) {
     if (!t) return;
     for (int p = 0; p < 2; ++p)
         for (Packed *pk : {&t->fwd[p], &t->adj[p]})
-            if (pk->dev) cudaFree(pk->dev);
+            if (pk->dev) dev_free(pk->dev);
     for (void *p : {(void *)t->Wd, (void *)t->apk_f, (void *)t->apk_a, (void *)t->c_fwd, (void *)t->c_adj,
                     (void *)t->idx, (void *)t->dargs, (void *)t->ditems})
-        if (p) cudaFree(p);
+        if (p) dev_free(p);
     delete t;
     s->ten = nullptr;
 }

@@ -9,6 +9,7 @@ namespace mpiffl {
 void col_init(mpi_ffl_handle *h);        // builds W and W H in double precision and uploads them
 void col_release(mpi_ffl_handle *h);
 bool col_supported(const mpi_ffl_handle *h);
+bool col_init_oom(const mpi_ffl_handle *h);  // col_init failed on a device allocation
 int col_take_error(mpi_ffl_handle *h);   // 1 if a GEMM gave up on a bounded wait (clears it)
 // full = false: fine -> data with W; full = true: proj -> data with W H (per-line gain)
 void col_forward(mpi_ffl_handle *h, const float *in, bool full, const float *gain, float *data, cudaStream_t st);

@@ -136,6 +136,10 @@ struct mpi_ffl_handle {
     int s_hist_len = 0;
     int *s_flags = nullptr;
     int *w_err = nullptr;      // set by kernels that gave up on a bounded wait
+    // failure-detection test hook (mpi_ffl_test_inject_timeout): > 0 makes the next
+    // interleaved-projector and line-GEMM launches give up after this many polls of a
+    // barrier that nothing arrives at; cleared by mpi_ffl_sync_check
+    uint32_t inject_polls = 0;
     // measurement hooks
     int prof_on = 0;
     int64_t launches = 0;
@@ -254,8 +258,33 @@ void launch_stop_batch(const StopJob *jobs, int n, cudaStream_t st);
 void launch_update_batch(const UpdateJob *jobs, const int *offs, int n, int total, cudaStream_t st);
 void launch_freeze_batch(const StopJob *jobs, int n, cudaStream_t st);  // done = stop verdict
 
+// Launch with programmatic stream serialization: the kernel may be scheduled while the
+// previous kernel of the stream finishes (its blocks run their prologue, then wait in
+// ptx::grid_dep_wait before touching memory that earlier kernels write or read).
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_dependent(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                                    Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // Message returned by mpi_ffl_last_error(NULL) on this thread.
 void set_thread_error(const std::string &msg);
+
+// Every device allocation and release of the library (alloc.cu): cudaMalloc and
+// cudaFree plus a registry of live allocations, and the failure-injection countdown
+// of mpi_ffl_test_fail_alloc.
+cudaError_t dev_malloc(void **p, size_t bytes);
+cudaError_t dev_free(void *p);
 
 // ---------------------------------------------------------------- launchers
 // Projector (k_projector.cu)
@@ -265,7 +294,7 @@ bool project_il_ok(int N);
 size_t il_len(int N, int Nz);
 void launch_interleave(const float *vol, float *volI, float *volTI, int N, int Nz, cudaStream_t st);
 void launch_project_il(const float *volI, const float *volTI, const AngleParam *ang, const int *agroups,
-                       int n_agroups, float *proj, int N, int Nz, cudaStream_t st, int *err);
+                       int n_agroups, float *proj, int N, int Nz, cudaStream_t st, int *err, uint32_t inject = 0);
 void launch_project(const float *vol, const float *volT, const AngleParam *ang, const int *agroups,
                     int n_agroups, float *proj, int N, int Nz, cudaStream_t st, int *err);
 constexpr int kProjAnglesPerBlock = 2;  // angle slots per projector block (k_projector.cu)

@@ -84,12 +84,12 @@ extern "C" int mpi_ffl_box_stats(const float *d_vol, int32_t nz, int32_t ny, int
     double *d_mean = nullptr, *d_part = nullptr;
     auto release = [&]() {
         for (void *p : {(void *)d_boxes, (void *)d_grp, (void *)d_mean, (void *)d_part})
-            if (p) cudaFree(p);
+            if (p) dev_free(p);
     };
-    if (cudaMalloc((void **)&d_boxes, sizeof(int) * 6 * n_boxes) != cudaSuccess ||
-        cudaMalloc((void **)&d_grp, sizeof(int) * n_boxes) != cudaSuccess ||
-        cudaMalloc((void **)&d_mean, sizeof(double) * ng) != cudaSuccess ||
-        cudaMalloc((void **)&d_part, sizeof(double) * 3 * n_boxes) != cudaSuccess) {
+    if (dev_malloc((void **)&d_boxes, sizeof(int) * 6 * n_boxes) != cudaSuccess ||
+        dev_malloc((void **)&d_grp, sizeof(int) * n_boxes) != cudaSuccess ||
+        dev_malloc((void **)&d_mean, sizeof(double) * ng) != cudaSuccess ||
+        dev_malloc((void **)&d_part, sizeof(double) * 3 * n_boxes) != cudaSuccess) {
         release();
         cudaGetLastError();
         mpiffl::set_thread_error("box_stats: device allocation failed");

@@ -54,7 +54,8 @@ __global__ void __launch_bounds__(kThreads) k_dot_total(const double *__restrict
     if (threadIdx.x == 0) *out = t;
 }
 
-// Device address of g_partials on the current device, looked up once per device.
+// Device address of g_partials on the current device, looked up once per device and
+// kept for the life of the process (a cudaDeviceReset of that device makes it stale).
 int partials_address(double **out) {
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
@@ -95,10 +96,15 @@ extern "C" int mpi_ffl_dot_f64_noalloc(const float *d_a, const float *d_b, int64
     if (rc != MPI_FFL_OK) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     const int nblk = n > 0 ? (int)((n + kPerBlock - 1) / kPerBlock) : 1;
+    // An error left pending by an earlier runtime call of the caller's is neither
+    // reported as this call's nor cleared: only a launch error that replaced it (or
+    // appeared where none was pending) is this call's, and only that one is consumed.
+    const cudaError_t before = cudaPeekAtLastError();
     k_dot_blocks<<<nblk, kThreads, 0, st>>>(d_a, d_b, n, partials);
     k_dot_total<<<1, kThreads, 0, st>>>(partials, nblk, d_out);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) {
+    const cudaError_t e = cudaPeekAtLastError();
+    if (e != cudaSuccess && e != before) {
+        (void)cudaGetLastError();
         mpiffl::set_thread_error(std::string("mpi_ffl_dot_f64_noalloc launch: ") + cudaGetErrorString(e));
         return MPI_FFL_ERR_CUDA;
     }

@@ -75,6 +75,7 @@ struct TcState {
     int *wbase = nullptr;   // adjoint window base cell per (trajectory, 32-period block)
     int n_sm = 1;
     bool ok = false;
+    bool oom = false;  // the shape is supported but a device allocation failed
 };
 
 __host__ __device__ inline uint32_t align_up(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
@@ -634,7 +635,7 @@ bool plan(const Dims &d, TcCfg &c, int win_len) {
 
 template <class T>
 void upload_vec(T **p, const std::vector<T> &v) {
-    if (cudaMalloc((void **)p, v.size() * sizeof(T)) != cudaSuccess) {
+    if (dev_malloc((void **)p, v.size() * sizeof(T)) != cudaSuccess) {
         *p = nullptr;
         return;
     }
@@ -771,9 +772,12 @@ void tc_init(mpi_ffl_handle *h) {
     s->n_adj = (int)ja.size();
     upload_vec(&s->jobs_fwd, jf);
     upload_vec(&s->jobs_adj, ja);
-    cudaMalloc((void **)&s->err, sizeof(int));
+    dev_malloc((void **)&s->err, sizeof(int));
     if (s->err) cudaMemset(s->err, 0, sizeof(int));
-    if (!s->twB || !s->twA || !s->tw2 || !s->jobs_fwd || !s->jobs_adj || !s->err || !s->wbase) return;
+    if (!s->twB || !s->twA || !s->tw2 || !s->jobs_fwd || !s->jobs_adj || !s->err || !s->wbase) {
+        s->oom = true;
+        return;
+    }
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&s->n_sm, cudaDevAttrMultiProcessorCount, dev);
@@ -784,12 +788,17 @@ void tc_init(mpi_ffl_handle *h) {
     s->ok = true;
 }
 
+bool tc_init_oom(const mpi_ffl_handle *h) {
+    const TcState *s = state(h);
+    return s && s->oom;
+}
+
 void tc_release(mpi_ffl_handle *h) {
     TcState *s = state(h);
     if (!s) return;
     void *ptrs[] = {s->jobs_fwd, s->jobs_adj, s->twB, s->twA, s->tw2, s->err, s->wbase};
     for (void *p : ptrs)
-        if (p) cudaFree(p);
+        if (p) dev_free(p);
     delete s;
     h->tc_state = nullptr;
 }

@@ -82,6 +82,17 @@ __device__ __forceinline__ bool mbar_wait_sleep_bounded(uint64_t *bar, uint32_t 
     return false;
 }
 
+// ------------------------------------------------------------------ dependent launch
+// A kernel launched with programmatic stream serialization (launch_dependent) may start
+// while the previous kernel of its stream is finishing. Before it reads anything an
+// earlier kernel wrote, or writes anything an earlier kernel may still read, every
+// thread waits here until the earlier grids have completed and their memory is
+// visible; for an ordinary launch the wait returns at once.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+// Lets the next kernel of the stream, if launched as a dependent, be scheduled once
+// every block of this grid has signalled (or exited); it still waits in grid_dep_wait.
+__device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // ------------------------------------------------------------------ fences
 __device__ __forceinline__ void fence_proxy_async_smem() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");

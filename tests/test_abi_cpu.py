@@ -92,3 +92,17 @@ def test_product_package_does_not_import_the_oracle():
                 text = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"^\s*(import|from)\s+oracle\b", text, re.M), f
                 assert "oracle/" not in text, f
+
+
+def test_failure_hooks_validate_their_arguments(lib):
+    """The allocation-failure countdown and the live-allocation registry need no GPU."""
+    from paper_2511_06627_gb300 import _lib
+
+    assert lib.mpi_ffl_test_fail_alloc(-1) == _lib.ERR_INVALID_ARG
+    assert lib.mpi_ffl_test_fail_alloc(3) == _lib.OK
+    assert lib.mpi_ffl_test_fail_alloc(0) == _lib.OK
+    n, b = C.c_int64(-1), C.c_int64(-1)
+    assert lib.mpi_ffl_test_live_allocs(C.byref(n), C.byref(b)) == _lib.OK
+    assert n.value >= 0 and b.value >= 0
+    assert lib.mpi_ffl_test_live_allocs(None, None) == _lib.OK
+    assert lib.mpi_ffl_test_inject_timeout(None, 4) == _lib.ERR_INVALID_ARG

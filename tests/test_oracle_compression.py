@@ -81,3 +81,26 @@ def test_pure_harmonic_lands_on_its_bin():
     expect = np.zeros(st.n_bins, complex)
     expect[list(st.bins).index(k * st.P)] = math.sqrt(L) / 2
     np.testing.assert_allclose(b, expect, atol=1e-12)
+
+
+def test_information_retained_closed_forms():
+    """Eq. (30) on signals whose spectra are known in closed form.
+
+    A cosine on bin w0 (0 < w0 < L/2) splits its energy equally between bins w0 and
+    L - w0, so keeping w0 alone retains exactly 1/sqrt(2) and keeping both retains 1.
+    A constant sits on bin 0 alone. For a cos(w1) + c cos(w2), keeping the pair of w1
+    retains |a| / sqrt(a^2 + c^2): a ratio of norms, not of energies, which a dropped
+    square root would turn into a^2 / (a^2 + c^2)."""
+    L, P, k = 96, 8, 3
+    j = np.arange(L)
+    w0 = k * P
+    s = np.cos(2 * math.pi * w0 * j / L + 0.4)
+    assert abs(operator.information_retained(s, np.array([w0])) - 1 / math.sqrt(2)) < 1e-12
+    assert abs(operator.information_retained(s, np.array([w0, L - w0])) - 1.0) < 1e-12
+    assert operator.information_retained(s, np.array([w0 + 1, L - w0 - 1])) < 1e-12
+    assert abs(operator.information_retained(np.full(L, 2.5), np.array([0])) - 1.0) < 1e-12
+    a, c, w1, w2 = 3.0, 4.0, 2 * P, 5 * P
+    s2 = a * np.cos(2 * math.pi * w1 * j / L) + c * np.cos(2 * math.pi * w2 * j / L - 1.1)
+    assert abs(operator.information_retained(s2, np.array([w1, L - w1])) - 0.6) < 1e-12
+    assert abs(operator.information_retained(s2, np.array([w2, L - w2])) - 0.8) < 1e-12
+    assert abs(operator.information_retained(s2, np.array([w1])) - 0.6 / math.sqrt(2)) < 1e-12
