@@ -25,10 +25,10 @@ __global__ void __launch_bounds__(kProbeThreads) k_smem_probe(float *__restrict_
     const uint32_t base = (uint32_t)__cvta_generic_to_shared(buf);
 #pragma unroll 16
     for (int r = 0; r < kProbeRounds; ++r) {
-        // a volatile asm load: the compiler may neither merge the repeated addresses
-        // nor drop a load
+        // a volatile load: neither the compiler nor the assembler may merge the
+        // addresses that repeat every few rounds, or drop a load
         float4 v;
-        asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+        asm volatile("ld.volatile.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
                      : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
                      : "r"(base + 16u * (uint32_t)idx));
         acc.x += v.x;
