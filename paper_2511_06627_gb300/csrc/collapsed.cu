@@ -483,6 +483,7 @@ struct ColState {
     // per direction and trajectory, sized for the tf32 chunk count
     uint8_t *apk[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
     bool oom = false;  // the shape is supported but a device allocation failed
+    bool psf_stale = false;  // W H was built for another PSF width (W itself holds no PSF)
 };
 
 ColState *cs(const mpi_ffl_handle *h) { return reinterpret_cast<ColState *>(h->col_state); }
@@ -805,6 +806,15 @@ void col_release(mpi_ffl_handle *h) {
     if (s->err) dev_free(s->err);
     delete s;
     h->col_state = nullptr;
+}
+
+void col_mark_psf_stale(mpi_ffl_handle *h) {
+    if (ColState *s = cs(h)) s->psf_stale = true;
+}
+
+bool col_psf_stale(const mpi_ffl_handle *h) {
+    const ColState *s = cs(h);
+    return s && s->psf_stale;
 }
 
 bool col_init_oom(const mpi_ffl_handle *h) {

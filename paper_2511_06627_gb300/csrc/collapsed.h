@@ -10,6 +10,8 @@ void col_init(mpi_ffl_handle *h);        // builds W and W H in double precision
 void col_release(mpi_ffl_handle *h);
 bool col_supported(const mpi_ffl_handle *h);
 bool col_init_oom(const mpi_ffl_handle *h);  // col_init failed on a device allocation
+void col_mark_psf_stale(mpi_ffl_handle *h);  // the PSF changed: W H must be rebuilt before use
+bool col_psf_stale(const mpi_ffl_handle *h);
 int col_take_error(mpi_ffl_handle *h);   // 1 if a GEMM gave up on a bounded wait (clears it)
 // full = false: fine -> data with W; full = true: proj -> data with W H (per-line gain)
 void col_forward(mpi_ffl_handle *h, const float *in, bool full, const float *gain, float *data, cudaStream_t st);

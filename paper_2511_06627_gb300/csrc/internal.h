@@ -79,6 +79,9 @@ struct Dims {
 };
 
 constexpr int kGroup = 8;          // lines per SegGroup in the staged kernels
+constexpr int kRaMaxEntries = 80;  // CSR entries per fine cell the tiled E V B transpose holds
+constexpr int kRaTileCells = 256;  // fine cells per tile of the tiled E V B transpose
+constexpr int kRaMaxWindow = 24576;  // samples of a tile's window it stages (96 KB)
 constexpr int kPsfT = 8;           // outputs per thread in the PSF kernels
 constexpr int kMaxHw = 8;          // largest supported half-width
 
@@ -107,6 +110,14 @@ struct mpi_ffl_handle {
     int2 *t_tnf = nullptr;                // n_par * L: (cell n, fraction f as float bits)
     std::vector<int> traj_n;              // host copy of the cells n, n_par * L
     float *t_vr = nullptr;                // n_par * S: velocity v_j, which depends on j mod S only
+    // tiled E V B transpose (k_resample_adj_tiled): per (parity, tile of kRaTileCells cells)
+    // the sample window (j_lo, len, first cell, cells), and the CSR entries [k][cell] with j
+    // relative to the window (ra_cap = the zero word for padding); ra_ntile = 0 when the
+    // trajectory does not fit, and the plain CSR gather serves instead
+    int4 *t_ra_tile = nullptr;
+    uint16_t *t_ra_j = nullptr;
+    float *t_ra_w = nullptr;
+    int ra_ntile = 0, ra_cap = 0;
     int *t_csr_ptr = nullptr;             // n_par * (Ne + 1)
     mpiffl::CsrEntry *t_csr = nullptr;    // n_par * 2L
     float *t_tw1 = nullptr;               // P * W: cos(2 pi d p / P) d=0..hw, sin d=1..hw
@@ -307,6 +318,9 @@ void launch_psf_adj(const float *fine, const float *htab, float *proj, const Dim
 void launch_resample_fwd(const float *fine, const TrajEntry *traj, const float *gain,
                          const SegGroup *groups, int n_groups, float *sig, const Dims &d,
                          cudaStream_t st);
+void launch_resample_adj_tiled(const float *sig, const int4 *tiles, const uint16_t *tj, const float *tw,
+                               const float *gain, float *fine, const Dims &d, int ntile, int cap, int *err,
+                               cudaStream_t st);
 void launch_resample_adj(const float *sig, const int *csr_ptr, const CsrEntry *csr,
                          const float *gain, const SegGroup *groups, int n_groups, float *fine,
                          const Dims &d, cudaStream_t st);

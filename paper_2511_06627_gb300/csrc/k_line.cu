@@ -13,6 +13,7 @@
 //       exactly equal to Eq. (27) on the kept bins. The inner sum over periods
 //       costs 2w+1 FMAs per sample (the signal is real); the outer one is small.
 #include "internal.h"
+#include "tc_ptx.cuh"
 
 namespace mpiffl {
 
@@ -199,6 +200,122 @@ void launch_resample_adj(const float *sig, const int *csr_ptr, const CsrEntry *c
     k_resample_adj<<<grid, 128, 0, st>>>(sig, csr_ptr, csr, gain, groups, fine, d);
 }
 
+// Tiled transpose of E V B. A block owns a tile of kRaCells fine cells of one angle and
+// trajectory parity and runs over a chunk of that parity's lines. The CSR entries of its
+// cells (sample j, weight w; ascending j per cell) are line-independent: each thread
+// keeps its share of them in registers, with j relative to the tile's sample window
+// [j_lo, j_lo + len), which covers every sample that touches a cell of the tile. Per
+// line, one thread bulk-copies that window into shared memory (two buffers, the next
+// line's copy in flight while this one is summed), and each cell sums its entries from
+// there: the signal is read from HBM once per tile, in full 16-byte-aligned runs.
+// Entry k of a cell belongs to half k & 1 of the block (threads c and c + kRaCells); the
+// halves are added in that order. Padding entries point at a zero word past the window.
+constexpr int kRaCells = kRaTileCells;
+constexpr int kRaHalf = kRaMaxEntries / 2;
+static_assert(kRaHalf % 2 == 0, "two 16-bit sample offsets per register");
+
+__global__ void __launch_bounds__(2 * kRaCells, 1) k_resample_adj_tiled(
+    const float *__restrict__ sig, const int4 *__restrict__ tiles, const uint16_t *__restrict__ tj,
+    const float *__restrict__ tw, const float *__restrict__ gain, float *__restrict__ fine, Dims d, int ntile,
+    int cap, int lines_per_block, int *err) {
+    extern __shared__ __align__(128) float ra_sm[];  // 2 windows of cap + 4 floats, 2 x kRaCells partials
+    float *win0 = ra_sm, *win1 = ra_sm + (cap + 4);
+    float *part = ra_sm + 2 * (cap + 4);  // [2][kRaCells]
+    uint64_t *full = reinterpret_cast<uint64_t *>(part + 2 * kRaCells);
+    const int tid = threadIdx.x, c = tid % kRaCells, half = tid / kRaCells;
+    // block -> (angle, parity, tile, chunk of lines)
+    const int nl_par = (d.Nz + d.n_par - 1) / d.n_par;  // lines of one parity (upper bound)
+    const int nchunk = (nl_par + lines_per_block - 1) / lines_per_block;
+    int b = blockIdx.x;
+    const int chunk = b % nchunk;
+    b /= nchunk;
+    const int tile = b % ntile;
+    b /= ntile;
+    const int par = b % d.n_par;
+    const int m = b / d.n_par;
+    const int4 T = tiles[par * ntile + tile];  // (j_lo, len, e0, ncell)
+    // this thread's entries, j relative to the window (cap = the zero word)
+    uint32_t jr[kRaHalf / 2];
+    float w[kRaHalf];
+    {
+        const size_t base = (size_t)(par * ntile + tile) * kRaMaxEntries * kRaCells;
+#pragma unroll
+        for (int q = 0; q < kRaHalf; ++q) {
+            const size_t at = base + (size_t)(2 * q + half) * kRaCells + c;
+            w[q] = __ldg(tw + at);
+            const uint32_t jv = __ldg(tj + at);
+            if (q & 1) jr[q >> 1] |= jv << 16;
+            else jr[q >> 1] = jv;
+        }
+    }
+    if (tid == 0) {
+        ptx::mbar_init(&full[0], 1);
+        ptx::mbar_init(&full[1], 1);
+        ptx::fence_mbar_init();
+    }
+    if (tid < 2) (tid ? win1 : win0)[cap] = 0.f;  // the padding entries' zero word
+    __syncthreads();
+    // lines of this parity: z = par + n_par * q; this block takes q in [q0, q1)
+    const int q0 = chunk * lines_per_block;
+    const int nz_par = (d.Nz - par + d.n_par - 1) / d.n_par;
+    const int q1 = min(q0 + lines_per_block, nz_par);
+    const uint32_t bytes = (uint32_t)T.y * 4u;
+    auto issue = [&](int q, float *dst, uint64_t *bar) {
+        const int z = par + d.n_par * q;
+        ptx::mbar_arrive_expect_tx(bar, bytes);
+        ptx::bulk_g2s(dst, sig + ((size_t)m * d.Nz + z) * d.L + T.x, bytes, bar);
+    };
+    if (tid == 0) {
+        if (q0 < q1) issue(q0, win0, &full[0]);
+        if (q0 + 1 < q1) issue(q0 + 1, win1, &full[1]);
+    }
+    const float gm = __ldg(gain + m);
+    for (int q = q0; q < q1; ++q) {
+        const int k = q - q0, bufi = k & 1;
+        float *wn = bufi ? win1 : win0;
+        const bool got = ptx::mbar_wait_bounded(&full[bufi], (k >> 1) & 1, 1u << 24);
+        if (!__syncthreads_and(got)) {  // one decision for the whole block
+            if (tid == 0) {
+                atomicExch(err, 1);
+                // the other buffer's copy, if one was issued, lands before the block leaves
+                if (q + 1 < q1) ptx::mbar_wait_bounded(&full[bufi ^ 1], ((k + 1) >> 1) & 1, 1u << 24);
+            }
+            __syncthreads();
+            break;
+        }
+        float acc = 0.f;
+#pragma unroll
+        for (int e = 0; e < kRaHalf; ++e) {
+            const uint32_t jj = (jr[e >> 1] >> ((e & 1) * 16)) & 0xffffu;
+            acc = fmaf(w[e], wn[jj], acc);
+        }
+        float *pt = part + bufi * kRaCells;
+        if (half) pt[c] = acc;
+        __syncthreads();  // window k read by all, partials written
+        if (!half && c < T.w) {
+            const int z = par + d.n_par * q;
+            fine[((size_t)m * d.Nz + z) * d.Ne + T.z + c] = gm * (acc + pt[c]);
+        }
+        if (tid == 0 && q + 2 < q1) {
+            ptx::fence_proxy_async_smem();  // the generic reads of the window, then its refill
+            issue(q + 2, wn, &full[bufi]);
+        }
+    }
+}
+
+void launch_resample_adj_tiled(const float *sig, const int4 *tiles, const uint16_t *tj, const float *tw,
+                               const float *gain, float *fine, const Dims &d, int ntile, int cap, int *err,
+                               cudaStream_t st) {
+    const int lines_per_block = 32;
+    const int nl_par = (d.Nz + d.n_par - 1) / d.n_par;
+    const int nchunk = (nl_par + lines_per_block - 1) / lines_per_block;
+    const size_t smem = sizeof(float) * (2 * (size_t)(cap + 4) + 2 * kRaCells) + 2 * sizeof(uint64_t);
+    cudaFuncSetAttribute(k_resample_adj_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    const int blocks = d.M * d.n_par * ntile * nchunk;
+    k_resample_adj_tiled<<<blocks, 2 * kRaCells, smem, st>>>(sig, tiles, tj, tw, gain, fine, d, ntile, cap,
+                                                             lines_per_block, err);
+}
+
 // ----------------------------------------------------------------------------- S D F
 
 // Twiddle table tw1[p][0..W): cos(2 pi d p / P) for d = 0..hw, then sin(2 pi d p / P)
@@ -221,13 +338,22 @@ __global__ void __launch_bounds__(128) k_dft_fwd(const float *__restrict__ sig,
         float ac[HW + 1], as[HW + 1];
 #pragma unroll
         for (int k = 0; k <= HW; ++k) ac[k] = as[k] = 0.f;
-        for (int p = 0; p < d.P; ++p) {
-            const float v = __ldg(s + (size_t)p * d.S + r);
-            const float *t = stw + p * W;
+        // eight periods' samples in flight before their products (the same products, in
+        // the same order, as one period at a time)
+        constexpr int kU = 8;
+        for (int p0 = 0; p0 < d.P; p0 += kU) {
+            float v[kU];
 #pragma unroll
-            for (int k = 0; k <= HW; ++k) ac[k] = fmaf(v, t[k], ac[k]);
+            for (int u = 0; u < kU; ++u) v[u] = p0 + u < d.P ? __ldg(s + (size_t)(p0 + u) * d.S + r) : 0.f;
 #pragma unroll
-            for (int k = 1; k <= HW; ++k) as[k] = fmaf(v, t[HW + k], as[k]);
+            for (int u = 0; u < kU; ++u) {
+                if (p0 + u >= d.P) break;
+                const float *t = stw + (p0 + u) * W;
+#pragma unroll
+                for (int k = 0; k <= HW; ++k) ac[k] = fmaf(v[u], t[k], ac[k]);
+#pragma unroll
+                for (int k = 1; k <= HW; ++k) as[k] = fmaf(v[u], t[HW + k], as[k]);
+            }
         }
 #pragma unroll
         for (int k = -HW; k <= HW; ++k) {

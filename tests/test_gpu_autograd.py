@@ -128,3 +128,115 @@ def test_calibration_fit_recovers_gains_and_psf_width():
     xj, gj, wj, hist = calibrate(op, b, iters=50, gains0=[1.0] * 8, fwhm0=3.0)
     assert hist[-1] < 0.2 * hist[0]
     assert float(xj.min()) >= 0.0
+
+
+# ---------------------------------------------------------------------------------
+# The calibration workload at its own geometry: the phantom-scale scan (128^2 x 64,
+# 24 angles, 64 lines x 256 periods x 64 samples, harmonics 1..12 at +-3 bins, FWHM 3)
+# with unknown per-angle gains and PSF width.
+
+from phantoms import config, phantom_for  # noqa: E402
+
+PH = {k: config("phantom")[k] for k in ("nx", "nz", "n_angles", "S", "P", "A", "phi0", "zigzag", "Q", "fwhm",
+                                         "k_min", "k_max", "half_width")}
+
+
+@pytest.fixture(scope="module")
+def phantom_fd():
+    """Central differences (h = 1e-3) of loss(g, w) = <gb, A(g, w) x> by the FP64 oracle.
+    loss is a sum over angles and angle m alone depends on g_m, so the difference for
+    g_m needs only angle m's data at g_m +- h; the width moves every angle."""
+    rng = np.random.default_rng(61)
+    M = PH["n_angles"]
+    gains = rng.uniform(0.95, 1.05, M).astype(np.float32).astype(np.float64)
+    x = phantom_for(config("phantom")).astype(np.float64)
+    nb = (PH["k_max"] - PH["k_min"] + 1) * (2 * PH["half_width"] + 1)
+    shape = (M, PH["nz"], nb)
+    gb = (rng.standard_normal(shape) + 1j * rng.standard_normal(shape)).astype(np.complex64).astype(np.complex128)
+    h = 1e-3
+
+    def angle_loss(m, g_m, w):
+        st = Setup(**{**PH, "fwhm": w}, gains=np.full(M, g_m))
+        d = operator.forward_stages(x, st, angles=np.array([m]))["data"][0]
+        return float(np.sum((d * np.conj(gb[m])).real))
+
+    fd_g = np.array([(angle_loss(m, gains[m] + h, 3.0) - angle_loss(m, gains[m] - h, 3.0)) / (2 * h)
+                     for m in range(M)])
+
+    b_plus = operator.forward(x, Setup(**{**PH, "fwhm": 3.0 + h}, gains=gains))
+    b_minus = operator.forward(x, Setup(**{**PH, "fwhm": 3.0 - h}, gains=gains))
+    fd_w = (float(np.sum((b_plus * np.conj(gb)).real)) - float(np.sum((b_minus * np.conj(gb)).real))) / (2 * h)
+    # |<gb, (dA/dw) x>| is a sum of terms of random sign; an error of relative size e in
+    # the vector (dA/dw) x moves it by at most e ||gb|| ||(dA/dw) x|| (Cauchy-Schwarz)
+    scale_w = float(np.linalg.norm(gb) * np.linalg.norm((b_plus - b_minus) / (2 * h)))
+    return dict(x=x, gb=gb, gains=gains, fd_g=fd_g, fd_w=fd_w, scale_w=scale_w)
+
+
+@pytest.mark.parametrize("path", ["staged", "fused", "line_gemm", "full_gemm"])
+def test_calibration_gradients_at_the_phantom_geometry(phantom_fd, path):
+    from paper_2511_06627_gb300 import FFLOperator
+
+    op = FFLOperator(**PH, gains=phantom_fd["gains"])
+    op.set_path(path)  # P = 256: every path takes this shape, the fused one included
+    gg, gw = op.param_grad(_t(phantom_fd["x"]), _t(to_interleaved(phantom_fd["gb"])))
+    gg = gg.cpu().numpy().astype(np.float64)
+    gw = float(gw.cpu().numpy()[0])
+    assert rel_l2(gg, phantom_fd["fd_g"]) < 1e-4
+    # the width gradient within 1e-4 of the difference, or, where its terms cancel,
+    # within what the operator tolerance on (dA/dw) x allows (Cauchy-Schwarz)
+    bound = max(1e-4 * abs(phantom_fd["fd_w"]), OP_TOL * phantom_fd["scale_w"])
+    assert abs(gw - phantom_fd["fd_w"]) <= bound, (gw, phantom_fd["fd_w"], bound)
+    op.close()
+
+
+def test_joint_fit_at_the_phantom_geometry():
+    """200 iterations of the joint volume + calibration fit (x >= 0 by projected
+    gradient, gains and width by Adam) on data from unknown gains U(0.95, 1.05) and a
+    PSF width of 3.3 voxels, started at unit gains and width 3. The volume and the gains
+    share one scale (A(c g) x / c = A(g) x), so the gains are compared after dividing by
+    their mean."""
+    from paper_2511_06627_gb300 import FFLOperator
+    from paper_2511_06627_gb300.autograd import calibrate
+
+    rng = np.random.default_rng(62)
+    M = PH["n_angles"]
+    g_true = rng.uniform(0.95, 1.05, M)
+    w_true = 3.3
+    x_true = phantom_for(config("phantom")).astype(np.float64)
+    st = Setup(**{**PH, "fwhm": w_true}, gains=g_true)
+    b = _t(to_interleaved(operator.forward(x_true, st)))
+    op = FFLOperator(**PH)
+    op.set_path("line_gemm")  # W holds no PSF: a new width only replaces the PSF taps
+    xj, gj, wj, hist = calibrate(op, b, iters=200, gains0=[1.0] * M, fwhm0=3.0)
+    gj = gj.cpu().numpy().astype(np.float64)
+    wj = float(wj.cpu().numpy()[0])
+    assert len(hist) == 200 and hist[-1] < 0.05 * hist[0], (hist[0], hist[-1])
+    assert float(xj.min()) >= 0.0
+    err0 = np.max(np.abs(1.0 - g_true / g_true.mean()))
+    err = np.max(np.abs(gj / gj.mean() - g_true / g_true.mean()))
+    assert err < 0.5 * err0, (err, err0)
+    assert abs(wj - w_true) < 0.5 * abs(3.0 - w_true), wj
+    op.close()
+
+
+def test_width_change_off_the_full_gemm_path_rebuilds_w_h_on_return():
+    """A new PSF width set while another path is selected leaves W H stale; selecting
+    the full-GEMM path again rebuilds it for the new width."""
+    from paper_2511_06627_gb300 import FFLOperator
+
+    x = _t(phantom_ellipsoids(GEOM["nx"], GEOM["nz"], seed=7, n_ellipsoids=4, n_points=2))
+    op = FFLOperator(**GEOM)
+    op.set_path("full_gemm")
+    op.forward(x)
+    op.set_path("line_gemm")
+    op.set_fwhm(3.4)
+    b_line = op.forward(x).clone()
+    op.set_path("full_gemm")
+    b_full = op.forward(x).clone()
+    fresh = FFLOperator(**{**GEOM, "fwhm": 3.4})
+    fresh.set_path("full_gemm")
+    assert torch.equal(b_full, fresh.forward(x))
+    st = Setup(**{**GEOM, "fwhm": 3.4})
+    ref = to_interleaved(operator.forward(x.cpu().numpy().astype(np.float64), st))
+    assert rel_l2(b_full.cpu().numpy(), ref) < OP_TOL
+    assert rel_l2(b_line.cpu().numpy(), ref) < OP_TOL
