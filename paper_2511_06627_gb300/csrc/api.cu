@@ -315,105 +315,9 @@ void trajectory_tables(mpi_ffl_handle *h) {
     upload(h, &h->t_vr, vr);
     upload(h, &h->t_csr_ptr, ptr);
     upload(h, &h->t_csr, csr);
-    // tiles of the tiled transpose: the window of samples touching each tile's cells
-    // (start rounded down to 4 samples for 16-byte copies, length a multiple of 4), and
-    // each cell's entries in ascending j, padded with (zero word, weight 0)
-    const int ntile = (d.Ne + kRaTileCells - 1) / kRaTileCells;
-    std::vector<int4> tiles((size_t)d.n_par * ntile);
-    bool fits = d.L % 4 == 0;
-    int cap = 0;
-    for (int par = 0; par < d.n_par && fits; ++par) {
-        const int *P = ptr.data() + (size_t)par * (d.Ne + 1);
-        const CsrEntry *C = csr.data() + (size_t)par * 2 * d.L;
-        for (int t = 0; t < ntile && fits; ++t) {
-            const int e0 = t * kRaTileCells, e1 = std::min(d.Ne, e0 + kRaTileCells);
-            int jlo = d.L, jhi = -1;
-            for (int e = e0; e < e1; ++e) {
-                if (P[e + 1] - P[e] > kRaMaxEntries) fits = false;
-                for (int k = P[e]; k < P[e + 1]; ++k) {
-                    jlo = std::min(jlo, C[k].j);
-                    jhi = std::max(jhi, C[k].j);
-                }
-            }
-            if (jhi < 0) jlo = jhi = 0;
-            jlo &= ~3;
-            const int len = std::min(d.L - jlo, (jhi - jlo + 1 + 3) & ~3);
-            cap = std::max(cap, len);
-            tiles[(size_t)par * ntile + t] = make_int4(jlo, len, e0, e1 - e0);
-        }
-    }
-    cap = (cap + 3) & ~3;
-    if (fits && cap <= kRaMaxWindow) {
-        const size_t per = (size_t)kRaMaxEntries * kRaTileCells;
-        std::vector<uint16_t> tj((size_t)d.n_par * ntile * per, (uint16_t)cap);
-        std::vector<float> tw((size_t)d.n_par * ntile * per, 0.f);
-        // Entry k of a cell goes to half k & 1. Within a half, the 32 cells of a warp read
-        // one entry each per step from the shared window, and two of them conflict when
-        // their samples sit in the same 4-byte bank (j mod 32) at different addresses. Each
-        // step therefore takes the largest set of lanes whose entries lie in distinct banks
-        // (a bipartite matching of lanes to banks by augmenting paths, longest remaining
-        // lists first); the other lanes take any entry. This only reorders the terms of
-        // each cell's two partial sums: a fixed order per trajectory.
-        for (int par = 0; par < d.n_par; ++par) {
-            const int *P = ptr.data() + (size_t)par * (d.Ne + 1);
-            const CsrEntry *C = csr.data() + (size_t)par * 2 * d.L;
-            for (int t = 0; t < ntile; ++t) {
-                const int4 T = tiles[(size_t)par * ntile + t];
-                const size_t base = (size_t)(par * ntile + t) * per;
-                for (int c0 = 0; c0 < T.w; c0 += 32)
-                    for (int half = 0; half < 2; ++half) {
-                        const int nl = std::min(32, T.w - c0);
-                        std::vector<std::vector<CsrEntry>> rem(nl);
-                        for (int l = 0; l < nl; ++l) {
-                            const int e = T.z + c0 + l;
-                            for (int k = P[e] + half; k < P[e + 1]; k += 2) rem[l].push_back(C[k]);
-                        }
-                        auto bank = [&](const CsrEntry &en) { return (en.j - T.x) & 31; };
-                        for (int slot = 0;; ++slot) {
-                            std::vector<int> lanes;
-                            for (int l = 0; l < nl; ++l)
-                                if (!rem[l].empty()) lanes.push_back(l);
-                            if (lanes.empty()) break;
-                            std::stable_sort(lanes.begin(), lanes.end(),
-                                             [&](int a, int b) { return rem[a].size() > rem[b].size(); });
-                            int owner[32];
-                            std::fill(owner, owner + 32, -1);
-                            std::vector<int> choice(nl, -1);
-                            std::function<bool(int, uint32_t &)> augment = [&](int l, uint32_t &seen) {
-                                for (size_t q = 0; q < rem[l].size(); ++q) {
-                                    const int bk = bank(rem[l][q]);
-                                    if (seen >> bk & 1u) continue;
-                                    seen |= 1u << bk;
-                                    if (owner[bk] < 0 || augment(owner[bk], seen)) {
-                                        owner[bk] = l;
-                                        choice[l] = (int)q;
-                                        return true;
-                                    }
-                                }
-                                return false;
-                            };
-                            for (int l : lanes) {
-                                uint32_t seen = 0;
-                                augment(l, seen);
-                            }
-                            for (int l : lanes) {
-                                const size_t q = choice[l] >= 0 ? (size_t)choice[l] : 0;
-                                const CsrEntry en = rem[l][q];
-                                rem[l].erase(rem[l].begin() + (long)q);
-                                const size_t at = base + (size_t)(2 * slot + half) * kRaTileCells + c0 + l;
-                                tj[at] = (uint16_t)(en.j - T.x);
-                                tw[at] = en.w;
-                            }
-                        }
-                    }
-            }
-        }
-        upload(h, &h->t_ra_tile, tiles);
-        upload(h, &h->t_ra_j, tj);
-        upload(h, &h->t_ra_w, tw);
-        h->ra_ntile = ntile;
-        h->ra_cap = cap;
-    }
+    // the staged transpose's tiles are built from these on its first use
+    h->csr_ptr_host = std::move(ptr);
+    h->csr_host = std::move(csr);
 }
 
 void dft_tables(mpi_ffl_handle *h) {
@@ -437,6 +341,13 @@ void dft_tables(mpi_ffl_handle *h) {
         }
     }
     upload(h, &h->t_tw1, tw1);
+    // the same period twiddles as one table, e^{2 pi i q / P} for q = k p mod P
+    std::vector<float2> twp(d.P);
+    for (int q = 0; q < d.P; ++q) {
+        const double ang = 2.0 * kPi * (double)q / d.P;
+        twp[q] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+    }
+    upload(h, &h->t_twp, twp);
     upload(h, &h->t_tw2_ro, ro);
     upload(h, &h->t_tw2_qr, qr);
     std::vector<float2> dg(d.nb);
@@ -466,7 +377,7 @@ void release(mpi_ffl_handle *h) {
                     h->w_proj, h->w_fine, h->w_sig, h->w_data, h->w_vol2, h->w_red, h->w_scal,
                     h->s_xp, h->s_y, h->s_g, h->s_r, h->s_hist, h->s_flags, h->tc_twb, h->t_agroups,
                     h->t_tnf, h->t_vr, h->w_err, h->t_coil, h->w_projc, h->w_scanvol, h->w_volI, h->w_volTI,
-                    h->t_ra_tile, h->t_ra_j, h->t_ra_w};
+                    h->t_ra_tile, h->t_ra_j, h->t_ra_w, h->t_twp};
     for (void *p : ptrs)
         if (p) dev_free(p);
     for (auto &r : h->prof_rec) {
@@ -580,9 +491,119 @@ void stage_p(mpi_ffl_handle *h, const float *x, float *proj, cudaStream_t st) {
     check_launch(h, "project");
 }
 
+// Tiles of the staged E V B transpose, built on its first use (only the staged path and
+// the stage entry point run it): the window of samples touching each tile's cells
+// (start rounded down to 4 samples for 16-byte copies, length a multiple of 4), and each
+// cell's entries, padded with (zero word, weight 0). ra_ntile stays 0 (the CSR gather
+// serves) when a cell holds more entries, or a window more samples, than the kernel takes.
+void ensure_ra_tables(mpi_ffl_handle *h) {
+    if (h->ra_built) return;
+    h->ra_built = true;
+    const Dims &d = h->d;
+    const std::vector<int> &ptr = h->csr_ptr_host;
+    const std::vector<CsrEntry> &csr = h->csr_host;
+    const int ntile = (d.Ne + kRaTileCells - 1) / kRaTileCells;
+    std::vector<int4> tiles((size_t)d.n_par * ntile);
+    bool fits = d.L % 4 == 0;
+    int cap = 0;
+    for (int par = 0; par < d.n_par && fits; ++par) {
+        const int *P = ptr.data() + (size_t)par * (d.Ne + 1);
+        const CsrEntry *C = csr.data() + (size_t)par * 2 * d.L;
+        for (int t = 0; t < ntile && fits; ++t) {
+            const int e0 = t * kRaTileCells, e1 = std::min(d.Ne, e0 + kRaTileCells);
+            int jlo = d.L, jhi = -1;
+            for (int e = e0; e < e1; ++e) {
+                if (P[e + 1] - P[e] > kRaMaxEntries) fits = false;
+                for (int k = P[e]; k < P[e + 1]; ++k) {
+                    jlo = std::min(jlo, C[k].j);
+                    jhi = std::max(jhi, C[k].j);
+                }
+            }
+            if (jhi < 0) jlo = jhi = 0;
+            jlo &= ~3;
+            const int len = std::min(d.L - jlo, (jhi - jlo + 1 + 3) & ~3);
+            cap = std::max(cap, len);
+            tiles[(size_t)par * ntile + t] = make_int4(jlo, len, e0, e1 - e0);
+        }
+    }
+    cap = (cap + 3) & ~3;
+    if (fits && cap <= kRaMaxWindow) {
+        const size_t per = (size_t)kRaMaxEntries * kRaTileCells;
+        std::vector<uint16_t> tj((size_t)d.n_par * ntile * per, (uint16_t)cap);
+        std::vector<float> tw((size_t)d.n_par * ntile * per, 0.f);
+        // Entry k of a cell goes to half k & 1. Within a half, the 32 cells of a warp read
+        // one entry each per step from the shared window, and two of them conflict when
+        // their samples sit in the same 4-byte bank (j mod 32) at different addresses. Each
+        // step therefore takes the largest set of lanes whose entries lie in distinct banks
+        // (a bipartite matching of lanes to banks by augmenting paths, longest remaining
+        // lists first); the other lanes take any entry. This only reorders the terms of
+        // each cell's two partial sums: a fixed order per trajectory.
+        for (int par = 0; par < d.n_par; ++par) {
+            const int *P = ptr.data() + (size_t)par * (d.Ne + 1);
+            const CsrEntry *C = csr.data() + (size_t)par * 2 * d.L;
+            for (int t = 0; t < ntile; ++t) {
+                const int4 T = tiles[(size_t)par * ntile + t];
+                const size_t base = (size_t)(par * ntile + t) * per;
+                for (int c0 = 0; c0 < T.w; c0 += 32)
+                    for (int half = 0; half < 2; ++half) {
+                        const int nl = std::min(32, T.w - c0);
+                        std::vector<std::vector<CsrEntry>> rem(nl);
+                        for (int l = 0; l < nl; ++l) {
+                            const int e = T.z + c0 + l;
+                            for (int k = P[e] + half; k < P[e + 1]; k += 2) rem[l].push_back(C[k]);
+                        }
+                        auto bank = [&](const CsrEntry &en) { return (en.j - T.x) & 31; };
+                        for (int slot = 0;; ++slot) {
+                            std::vector<int> lanes;
+                            for (int l = 0; l < nl; ++l)
+                                if (!rem[l].empty()) lanes.push_back(l);
+                            if (lanes.empty()) break;
+                            std::stable_sort(lanes.begin(), lanes.end(),
+                                             [&](int a, int b) { return rem[a].size() > rem[b].size(); });
+                            int owner[32];
+                            std::fill(owner, owner + 32, -1);
+                            std::vector<int> choice(nl, -1);
+                            std::function<bool(int, uint32_t &)> augment = [&](int l, uint32_t &seen) {
+                                for (size_t q = 0; q < rem[l].size(); ++q) {
+                                    const int bk = bank(rem[l][q]);
+                                    if (seen >> bk & 1u) continue;
+                                    seen |= 1u << bk;
+                                    if (owner[bk] < 0 || augment(owner[bk], seen)) {
+                                        owner[bk] = l;
+                                        choice[l] = (int)q;
+                                        return true;
+                                    }
+                                }
+                                return false;
+                            };
+                            for (int l : lanes) {
+                                uint32_t seen = 0;
+                                augment(l, seen);
+                            }
+                            for (int l : lanes) {
+                                const size_t q = choice[l] >= 0 ? (size_t)choice[l] : 0;
+                                const CsrEntry en = rem[l][q];
+                                rem[l].erase(rem[l].begin() + (long)q);
+                                const size_t at = base + (size_t)(2 * slot + half) * kRaTileCells + c0 + l;
+                                tj[at] = (uint16_t)(en.j - T.x);
+                                tw[at] = en.w;
+                            }
+                        }
+                    }
+            }
+        }
+        upload(h, &h->t_ra_tile, tiles);
+        upload(h, &h->t_ra_j, tj);
+        upload(h, &h->t_ra_w, tw);
+        h->ra_ntile = ntile;
+        h->ra_cap = cap;
+    }
+}
+
 // E V B transpose: the tiled kernel where the trajectory fits it, else the CSR gather
 void resample_adj(mpi_ffl_handle *h, const float *sig, float *fine, cudaStream_t st) {
     const Dims &d = h->d;
+    ensure_ra_tables(h);
     if (h->ra_ntile > 0)
         launch_resample_adj_tiled(sig, h->t_ra_tile, h->t_ra_j, h->t_ra_w, h->t_gain, fine, d, h->ra_ntile, h->ra_cap,
                                   h->w_err, st);
@@ -631,7 +652,7 @@ void line_forward_impl(mpi_ffl_handle *h, const float *proj, float *b, const flo
     ensure_sig(h);
     TIMED(MPI_FFL_K_RESAMPLE_FWD, launch_resample_fwd(h->w_fine, h->t_traj, gain, h->t_groups, h->n_groups, h->w_sig, d, st));
     check_launch(h, "resample_fwd");
-    TIMED(MPI_FFL_K_DFT_FWD, launch_dft_fwd(h->w_sig, h->t_tw1, h->t_tw2_ro, h->t_dgam, b, d, st));
+    TIMED(MPI_FFL_K_DFT_FWD, launch_dft_fwd(h->w_sig, h->t_tw1, h->t_twp, h->t_tw2_ro, h->t_dgam, b, d, h->w_err, st));
     check_launch(h, "dft_fwd");
 }
 
@@ -1442,7 +1463,7 @@ extern "C" int mpi_ffl_apply_stage(mpi_ffl_handle *h, int32_t stage, int32_t tra
             case 3: TIMED(MPI_FFL_K_PSF_ADJ, launch_psf_adj(in, h->t_htab, out, d, st)); break;
             case 4: TIMED(MPI_FFL_K_RESAMPLE_FWD, launch_resample_fwd(in, h->t_traj, h->t_gain, h->t_groups, h->n_groups, out, d, st)); break;
             case 5: TIMED(MPI_FFL_K_RESAMPLE_ADJ, resample_adj(h, in, out, st)); break;
-            case 6: TIMED(MPI_FFL_K_DFT_FWD, launch_dft_fwd(in, h->t_tw1, h->t_tw2_ro, h->t_dgam, out, d, st)); break;
+            case 6: TIMED(MPI_FFL_K_DFT_FWD, launch_dft_fwd(in, h->t_tw1, h->t_twp, h->t_tw2_ro, h->t_dgam, out, d, h->w_err, st)); break;
             case 7: TIMED(MPI_FFL_K_DFT_ADJ, launch_dft_adj(in, h->t_tw1, h->t_tw2_qr, h->t_dgam, out, d, st)); break;
         }
         check_launch(h, "apply_stage");
@@ -1541,7 +1562,7 @@ extern "C" int mpi_ffl_band_energy(mpi_ffl_handle *h, const float *d_x, double *
         const int nbr = reduce_blocks(d.nsig);
         TIMED(MPI_FFL_K_SOLVER, launch_dot(h->w_sig, h->w_sig, d.nsig, h->w_red, nbr, st));
         TIMED(MPI_FFL_K_SOLVER, launch_finalize(h->w_red, nbr, d_total, st));
-        TIMED(MPI_FFL_K_DFT_FWD, launch_dft_fwd(h->w_sig, h->t_tw1, h->t_tw2_ro, h->t_dgam_unit, h->w_data, d, st));
+        TIMED(MPI_FFL_K_DFT_FWD, launch_dft_fwd(h->w_sig, h->t_tw1, h->t_twp, h->t_tw2_ro, h->t_dgam_unit, h->w_data, d, h->w_err, st));
         TIMED(MPI_FFL_K_SOLVER, launch_bin_energy(h->w_data, d.nseg, d.nb, d_bin_energy, st));
         check_launch(h, "band energy");
         return MPI_FFL_OK;

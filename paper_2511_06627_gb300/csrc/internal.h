@@ -118,6 +118,10 @@ struct mpi_ffl_handle {
     uint16_t *t_ra_j = nullptr;
     float *t_ra_w = nullptr;
     int ra_ntile = 0, ra_cap = 0;
+    bool ra_built = false;                // the tiles are built on the transpose's first use
+    std::vector<int> csr_ptr_host;        // host copies of the CSR, n_par * (Ne + 1) and n_par * 2L
+    std::vector<mpiffl::CsrEntry> csr_host;
+    float2 *t_twp = nullptr;              // [P] e^{2 pi i q / P}: the period twiddles of the band DFT
     int *t_csr_ptr = nullptr;             // n_par * (Ne + 1)
     mpiffl::CsrEntry *t_csr = nullptr;    // n_par * 2L
     float *t_tw1 = nullptr;               // P * W: cos(2 pi d p / P) d=0..hw, sin d=1..hw
@@ -324,8 +328,8 @@ void launch_resample_adj_tiled(const float *sig, const int4 *tiles, const uint16
 void launch_resample_adj(const float *sig, const int *csr_ptr, const CsrEntry *csr,
                          const float *gain, const SegGroup *groups, int n_groups, float *fine,
                          const Dims &d, cudaStream_t st);
-void launch_dft_fwd(const float *sig, const float *tw1, const float2 *tw2_ro, const float2 *dgam,
-                    float *data, const Dims &d, cudaStream_t st);
+void launch_dft_fwd(const float *sig, const float *tw1, const float2 *twp, const float2 *tw2_ro, const float2 *dgam,
+                    float *data, const Dims &d, int *err, cudaStream_t st);
 void launch_dft_adj(const float *data, const float *tw1, const float2 *tw2_qr, const float2 *dgam,
                     float *sig, const Dims &d, cudaStream_t st);
 

@@ -157,9 +157,38 @@ __global__ void __launch_bounds__(256) k_resample_fwd(const float *__restrict__ 
     }
 }
 
+// Four consecutive samples per thread (L % 4 == 0, 16-byte aligned signal): the same
+// products as k_resample_fwd, stored with one 16-byte store per line.
+__global__ void __launch_bounds__(256) k_resample_fwd4(const float *__restrict__ fine,
+                                                       const TrajEntry *__restrict__ traj,
+                                                       const float *__restrict__ gain,
+                                                       const SegGroup *__restrict__ groups,
+                                                       float *__restrict__ sig, Dims d) {
+    const int j0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+    if (j0 >= d.L) return;
+    const SegGroup g = groups[blockIdx.y];
+    TrajEntry te[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) te[u] = traj[(size_t)g.parity * d.L + j0 + u];
+    const float gm = gain[g.m];
+    for (int l = 0; l < g.count; ++l) {
+        const int seg = g.m * d.Nz + g.z0 + l * g.zstride;
+        const float *row = fine + (size_t)seg * d.Ne;
+        float v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = gm * fmaf(te[u].w0, __ldg(row + te[u].n), te[u].w1 * __ldg(row + te[u].n + 1));
+        *reinterpret_cast<float4 *>(sig + (size_t)seg * d.L + j0) = make_float4(v[0], v[1], v[2], v[3]);
+    }
+}
+
 void launch_resample_fwd(const float *fine, const TrajEntry *traj, const float *gain,
                          const SegGroup *groups, int n_groups, float *sig, const Dims &d,
                          cudaStream_t st) {
+    if (d.L % 4 == 0 && (reinterpret_cast<uintptr_t>(sig) & 15) == 0) {
+        dim3 grid((d.L / 4 + 255) / 256, n_groups);
+        k_resample_fwd4<<<grid, 256, 0, st>>>(fine, traj, gain, groups, sig, d);
+        return;
+    }
     dim3 grid((d.L + 255) / 256, n_groups);
     k_resample_fwd<<<grid, 256, 0, st>>>(fine, traj, gain, groups, sig, d);
 }
@@ -338,22 +367,13 @@ __global__ void __launch_bounds__(128) k_dft_fwd(const float *__restrict__ sig,
         float ac[HW + 1], as[HW + 1];
 #pragma unroll
         for (int k = 0; k <= HW; ++k) ac[k] = as[k] = 0.f;
-        // eight periods' samples in flight before their products (the same products, in
-        // the same order, as one period at a time)
-        constexpr int kU = 8;
-        for (int p0 = 0; p0 < d.P; p0 += kU) {
-            float v[kU];
+        for (int p = 0; p < d.P; ++p) {
+            const float v = __ldg(s + (size_t)p * d.S + r);
+            const float *t = stw + p * W;
 #pragma unroll
-            for (int u = 0; u < kU; ++u) v[u] = p0 + u < d.P ? __ldg(s + (size_t)(p0 + u) * d.S + r) : 0.f;
+            for (int k = 0; k <= HW; ++k) ac[k] = fmaf(v, t[k], ac[k]);
 #pragma unroll
-            for (int u = 0; u < kU; ++u) {
-                if (p0 + u >= d.P) break;
-                const float *t = stw + (p0 + u) * W;
-#pragma unroll
-                for (int k = 0; k <= HW; ++k) ac[k] = fmaf(v[u], t[k], ac[k]);
-#pragma unroll
-                for (int k = 1; k <= HW; ++k) as[k] = fmaf(v[u], t[HW + k], as[k]);
-            }
+            for (int k = 1; k <= HW; ++k) as[k] = fmaf(v, t[HW + k], as[k]);
         }
 #pragma unroll
         for (int k = -HW; k <= HW; ++k) {
@@ -434,6 +454,153 @@ __global__ void __launch_bounds__(128) k_dft_adj(const float *__restrict__ data,
     }
 }
 
+// Streaming form (S % 4 == 0, S <= 128): a warp owns one segment. Lane 0 bulk-copies the
+// segment's signal through a ring of kDfStages chunks of kDfChunk periods (the warp's own
+// mbarriers), and lane l sums the four phases 4l..4l+3 with one 16-byte load per period.
+// The period twiddles e^{2 pi i k p / P} come from one table of e^{2 pi i q / P} at
+// q = k p mod P, the same values as the per-(p, k) table. The phase sums are the same
+// FMAs in the same order as the one-phase-per-thread form; the synthesis over phases
+// then runs as there, in the warp's own ring memory.
+constexpr int kDfWarps = 8;
+constexpr int kDfChunk = 8;
+constexpr int kDfStages = 3;
+
+template <int HW>
+__global__ void __launch_bounds__(32 * kDfWarps) k_dft_fwd_stream(const float *__restrict__ sig,
+                                                                  const float2 *__restrict__ twp,
+                                                                  const float2 *__restrict__ tw2_ro,
+                                                                  const float2 *__restrict__ dgam,
+                                                                  float *__restrict__ data, Dims d,
+                                                                  float inv_sqrt_l, int *err) {
+    constexpr int W = 2 * HW + 1;
+    extern __shared__ __align__(128) float df_sm[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ring_f = kDfStages * kDfChunk * d.S;  // floats per warp
+    float *ring = df_sm + (size_t)warp * ring_f;
+    float2 *stp = reinterpret_cast<float2 *>(df_sm + (size_t)kDfWarps * ring_f);  // [P] e^{2 pi i q / P}
+    uint64_t *bars = reinterpret_cast<uint64_t *>(stp + d.P) + warp * kDfStages;
+    for (int i = threadIdx.x; i < d.P; i += blockDim.x) stp[i] = twp[i];
+    if (lane == 0) {
+        for (int k = 0; k < kDfStages; ++k) ptx::mbar_init(&bars[k], 1);
+        ptx::fence_mbar_init();
+    }
+    __syncthreads();
+    const int seg = blockIdx.x * kDfWarps + warp;
+    if (seg >= d.nseg) return;
+    const float *src = sig + (size_t)seg * d.L;
+    const int nchunk = (d.P + kDfChunk - 1) / kDfChunk;
+    auto issue = [&](int c) {
+        const int per = min(kDfChunk, d.P - c * kDfChunk);
+        const uint32_t bytes = (uint32_t)per * d.S * 4u;
+        uint64_t *bar = &bars[c % kDfStages];
+        ptx::mbar_arrive_expect_tx(bar, bytes);
+        ptx::bulk_g2s(ring + (size_t)(c % kDfStages) * kDfChunk * d.S, src + (size_t)c * kDfChunk * d.S, bytes, bar);
+    };
+    if (lane == 0)
+        for (int c = 0; c < kDfStages && c < nchunk; ++c) issue(c);
+    const int nq = d.S / 4;
+    const bool act = lane < nq;
+    float ac[4][HW + 1], as[4][HW + 1];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int k = 0; k <= HW; ++k) ac[i][k] = as[i][k] = 0.f;
+    int idx[HW + 1];  // k p mod P
+#pragma unroll
+    for (int k = 0; k <= HW; ++k) idx[k] = 0;
+    bool good = true;
+    for (int c = 0; c < nchunk; ++c) {
+        const bool got = ptx::mbar_wait_bounded(&bars[c % kDfStages], (c / kDfStages) & 1, 1u << 24);
+        if (!__all_sync(0xffffffffu, got)) {
+            good = false;
+            break;
+        }
+        const float *stage = ring + (size_t)(c % kDfStages) * kDfChunk * d.S;
+        const int per = min(kDfChunk, d.P - c * kDfChunk);
+        for (int pl = 0; pl < per; ++pl) {
+            float2 t[HW + 1];
+#pragma unroll
+            for (int k = 0; k <= HW; ++k) t[k] = stp[idx[k]];
+            if (act) {
+                const float4 v4 = reinterpret_cast<const float4 *>(stage + (size_t)pl * d.S)[lane];
+                const float v[4] = {v4.x, v4.y, v4.z, v4.w};
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+#pragma unroll
+                    for (int k = 0; k <= HW; ++k) ac[i][k] = fmaf(v[i], t[k].x, ac[i][k]);
+#pragma unroll
+                    for (int k = 1; k <= HW; ++k) as[i][k] = fmaf(v[i], t[k].y, as[i][k]);
+                }
+            }
+#pragma unroll
+            for (int k = 1; k <= HW; ++k) {
+                idx[k] += k;
+                if (idx[k] >= d.P) idx[k] -= d.P;
+            }
+        }
+        __syncwarp();
+        if (lane == 0 && c + kDfStages < nchunk) {
+            ptx::fence_proxy_async_smem();  // the warp's reads of the stage, then its refill
+            issue(c + kDfStages);
+        }
+    }
+    if (!good) {
+        if (lane == 0) atomicExch(err, 1);
+        return;
+    }
+    __syncwarp();
+    // the warp's ring now holds sT[r][W] (complex), then the synthesis over phases
+    float2 *sT = reinterpret_cast<float2 *>(ring);
+    if (act) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int r = 4 * lane + i;
+#pragma unroll
+            for (int k = -HW; k <= HW; ++k) {
+                const int a = k < 0 ? -k : k;
+                sT[r * W + (k + HW)] = make_float2(ac[i][a], k < 0 ? -as[i][a] : as[i][a]);
+            }
+        }
+    }
+    __syncwarp();
+    for (int o = lane; o < d.nb; o += 32) {
+        const int di = o % W;
+        float re = 0.f, im = 0.f;
+        for (int r = 0; r < d.S; ++r) {
+            const float2 t = sT[r * W + di];
+            const float2 w = __ldg(tw2_ro + (size_t)r * d.nb + o);
+            re = fmaf(t.x, w.x, fmaf(-t.y, w.y, re));
+            im = fmaf(t.x, w.y, fmaf(t.y, w.x, im));
+        }
+        const float2 g = dgam[o];
+        re *= inv_sqrt_l;
+        im *= inv_sqrt_l;
+        float2 *out = (float2 *)data + (size_t)seg * d.nb + o;
+        *out = make_float2(g.x * re - g.y * im, g.x * im + g.y * re);
+    }
+}
+
+size_t dft_stream_smem(const Dims &d) {
+    return sizeof(float) * (size_t)kDfWarps * kDfStages * kDfChunk * d.S + sizeof(float2) * d.P +
+           sizeof(uint64_t) * kDfWarps * kDfStages;
+}
+
+// The streaming form takes S % 4 == 0, S <= 128, a signal whose segments start on 16
+// bytes, and a ring that can hold the S x W synthesis inputs afterwards.
+bool dft_stream_ok(const Dims &d, const float *sig) {
+    return d.S % 4 == 0 && d.S <= 128 && d.L % 4 == 0 && (reinterpret_cast<uintptr_t>(sig) & 15) == 0 &&
+           (size_t)d.S * d.W * 2 <= (size_t)kDfStages * kDfChunk * d.S && dft_stream_smem(d) <= 227 * 1024;
+}
+
+template <int HW>
+static void dft_fwd_stream_hw(const float *sig, const float2 *twp, const float2 *tw2_ro, const float2 *dgam,
+                              float *data, const Dims &d, int *err, cudaStream_t st) {
+    const size_t smem = dft_stream_smem(d);
+    cudaFuncSetAttribute(k_dft_fwd_stream<HW>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    k_dft_fwd_stream<HW><<<(d.nseg + kDfWarps - 1) / kDfWarps, 32 * kDfWarps, smem, st>>>(
+        sig, twp, tw2_ro, dgam, data, d, (float)(1.0 / sqrt((double)d.L)), err);
+}
+
 template <int HW>
 static void dft_fwd_hw(const float *sig, const float *tw1, const float2 *tw2_ro, const float2 *dgam,
                        float *data, const Dims &d, cudaStream_t st) {
@@ -467,8 +634,12 @@ static void dft_adj_hw(const float *data, const float *tw1, const float2 *tw2_qr
         default: FN<8>(__VA_ARGS__); break;         \
     }
 
-void launch_dft_fwd(const float *sig, const float *tw1, const float2 *tw2_ro, const float2 *dgam,
-                    float *data, const Dims &d, cudaStream_t st) {
+void launch_dft_fwd(const float *sig, const float *tw1, const float2 *twp, const float2 *tw2_ro, const float2 *dgam,
+                    float *data, const Dims &d, int *err, cudaStream_t st) {
+    if (twp && err && dft_stream_ok(d, sig)) {
+        MPIFFL_HW_DISPATCH(dft_fwd_stream_hw, sig, twp, tw2_ro, dgam, data, d, err, st);
+        return;
+    }
     MPIFFL_HW_DISPATCH(dft_fwd_hw, sig, tw1, tw2_ro, dgam, data, d, st);
 }
 
