@@ -6,9 +6,11 @@
 // iteration each, as one launch per kernel kind for all of them: momentum, residual,
 // residual norm and stop test, update for every job; x/y transpose, projector, line
 // GEMM, adjoint line GEMM and backprojector for the jobs on the full-GEMM path (jobs
-// on other paths apply their A and A^T alone between those launches). Each block
-// finds its job through an offset table. Jobs that have met their stop test do no
-// further work on the device (their update only keeps the final iterate).
+// on other paths apply their A and A^T alone between those launches). Each launch is
+// persistent: a grid of what the GPU holds at once loops over the work items of every
+// job (found through an offset table), so the launch count per iteration does not grow
+// with the number of jobs. Jobs that have met their stop test do no further work on
+// the device (their update only keeps the final iterate).
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -239,11 +241,12 @@ extern "C" int mpi_ffl_job_step(mpi_ffl_job *const *jobs, int32_t n, void *strea
     std::vector<int4> itf(item_cap), ita(item_cap);
     int nif = 0, nia = 0, npf = 0, npa = 0;
     size_t smf = 0, sma = 0;
+    uint32_t tcf = 32, tca = 32;
     if (nb > 0) {
         npf = col_batch_prepare(hs.data(), gin_f.data(), gout_f.data(), dn.data(), nb, false, gf.data(), itf.data(),
-                                arg_cap, item_cap, nif, smf);
+                                arg_cap, item_cap, nif, smf, tcf);
         npa = col_batch_prepare(hs.data(), gin_a.data(), gout_a.data(), dn.data(), nb, true, ga.data(), ita.data(),
-                                arg_cap, item_cap, nia, sma);
+                                arg_cap, item_cap, nia, sma, tca);
         if (npf < 0 || npa < 0) return MPI_FFL_ERR_UNSUPPORTED;
     }
     const size_t o_mom = put(buf, mom), o_offm = put(buf, off_m);
@@ -274,13 +277,13 @@ extern "C" int mpi_ffl_job_step(mpi_ffl_job *const *jobs, int32_t n, void *strea
                                    off_t.back(), st);
         launch_project_batch((const ProjectJob *)at(o_pj), (const int *)at(o_offp), nb, off_p[nb], maxN,
                              batch[0]->h->w_err, st);
-        col_batch_launch(at(o_gf), (const int4 *)at(o_itf), nif, smf, st);
+        col_batch_launch(at(o_gf), (const int4 *)at(o_itf), nif, smf, tcf, st);
     }
     for (mpi_ffl_job *j : single) forward_for_job(j->h, j->y, j->r, st);
     launch_residual_batch((const ResidualJob *)at(o_rs), (const int *)at(o_offr), na, off_r[na], st);
     launch_stop_batch((const StopJob *)at(o_sp), na, st);
     if (nb > 0) {
-        col_batch_launch(at(o_ga), (const int4 *)at(o_ita), nia, sma, st);
+        col_batch_launch(at(o_ga), (const int4 *)at(o_ita), nia, sma, tca, st);
         launch_backproject_batch((const BackprojectJob *)at(o_bp), (const int *)at(o_offb), nb, off_b[nb], st);
     }
     for (mpi_ffl_job *j : single) adjoint_for_job(j->h, j->r, j->g, st);

@@ -126,8 +126,10 @@ struct AChunk {
 };
 
 // MODE 0: bf16 operands, 1: tf32, 2: as g.tf32 says (batches that may mix both).
+// One output tile. With tslot_ext NULL the block allocates (and at the end frees) its own
+// TMEM columns; a persistent block passes the slot of columns it holds for all its tiles.
 template <int MODE>
-__device__ __forceinline__ void gemm_body(const GemmArgs &g, int mt, int nt, uint8_t *sm) {
+__device__ __forceinline__ void gemm_tile(const GemmArgs &g, int mt, int nt, uint8_t *sm, const uint32_t *tslot_ext) {
     const bool tf32 = MODE == 2 ? g.tf32 != 0 : MODE == 1;
     const uint32_t bytesA = kBM * kBK * 2;          // one of hi | lo
     const uint32_t bytesB = (uint32_t)g.BN * kBK * 2;
@@ -147,14 +149,14 @@ __device__ __forceinline__ void gemm_body(const GemmArgs &g, int mt, int nt, uin
         ptx::fence_mbar_init();
         *flag = 0;
     }
-    if (warp == 0) {
+    if (!tslot_ext && warp == 0) {
         ptx::tmem_alloc(tslot, g.tmem_cols);
         ptx::tmem_relinquish();
     }
     ptx::tc_fence_before();
     __syncthreads();
     ptx::tc_fence_after();
-    const uint32_t tmem = *tslot;
+    const uint32_t tmem = tslot_ext ? *tslot_ext : *tslot;
     ptx::grid_dep_wait();  // A (and the output rows) belong to earlier kernels of the stream
     ptx::grid_dep_launch();
 
@@ -370,7 +372,12 @@ __device__ __forceinline__ void gemm_body(const GemmArgs &g, int mt, int nt, uin
     ptx::tc_fence_before();
     __syncthreads();
     if (tid == 0 && *flag) atomicExch(g.err, 1);
-    if (warp == 0) ptx::tmem_dealloc(tmem, g.tmem_cols);
+    if (!tslot_ext && warp == 0) ptx::tmem_dealloc(tmem, g.tmem_cols);
+}
+
+template <int MODE>
+__device__ __forceinline__ void gemm_body(const GemmArgs &g, int mt, int nt, uint8_t *sm) {
+    gemm_tile<MODE>(g, mt, nt, sm, nullptr);
 }
 
 template <int MODE>
@@ -390,14 +397,40 @@ __global__ void __launch_bounds__(kGemmThreads, 2) k_gemm_pair(GemmArgs g0, Gemm
     else gemm_body<MODE>(g1, (b - n0) / nt1, (b - n0) % nt1, sm);
 }
 
-// One launch for several GEMM problems: items[b] = (problem, m tile, n tile).
+// One persistent launch for several GEMM problems: items[i] = (problem, m tile, n tile).
+// A block holds `cols` TMEM columns (the largest problem's need, at most 256, so two
+// blocks share an SM) for all its items; each item sets up its own barriers, which are
+// invalidated once the item is done.
 __global__ void __launch_bounds__(kGemmThreads, 2) k_gemm_batch(const GemmArgs *__restrict__ args,
-                                                       const int4 *__restrict__ items) {
+                                                       const int4 *__restrict__ items, int n_items,
+                                                       uint32_t cols, uint32_t slot_off) {
     extern __shared__ __align__(128) uint8_t sm[];
-    const int4 it = items[blockIdx.x];
-    const GemmArgs g = args[it.x];
-    if (g.done && *g.done) return;
-    gemm_body<2>(g, it.y, it.z, sm);
+    // the TMEM address lives past every item's layout (slot_off = the largest item's bytes)
+    uint32_t &tslot = *reinterpret_cast<uint32_t *>(sm + slot_off);
+    const int warp = threadIdx.x >> 5;
+    if (warp == 0) {
+        ptx::tmem_alloc(&tslot, cols);
+        ptx::tmem_relinquish();
+    }
+    ptx::tc_fence_before();
+    __syncthreads();
+    ptx::tc_fence_after();
+    for (int i = blockIdx.x; i < n_items; i += gridDim.x) {
+        const int4 it = items[i];
+        const GemmArgs g = args[it.x];
+        if (g.done && *g.done) continue;  // uniform over the block
+        gemm_tile<2>(g, it.y, it.z, sm, &tslot);
+        if (threadIdx.x == 0) {
+            const uint32_t stage = 2u * kBM * kBK * 2 + 2u * (uint32_t)g.BN * kBK * 2;
+            uint64_t *bars = reinterpret_cast<uint64_t *>(sm + g.stages * stage);
+            for (int k = 0; k < 2 * g.stages + 1; ++k) ptx::mbar_inval(&bars[k]);
+        }
+        __syncthreads();
+    }
+    ptx::tc_fence_before();
+    __syncthreads();
+    ptx::tc_fence_after();
+    if (warp == 0) ptx::tmem_dealloc(tslot, cols);
 }
 
 uint16_t bf16_bits(double x) {
@@ -893,11 +926,12 @@ size_t gemm_args_size() { return sizeof(GemmArgs); }
 // layout), already uploaded by the caller before this launch runs.
 int col_batch_prepare(mpi_ffl_handle *const *hs, const float *const *in, float *const *out, const int *const *done,
                       int n, bool adjoint, void *args, int4 *items, int arg_cap, int item_cap, int &n_items,
-                      size_t &smem) {
+                      size_t &smem, uint32_t &tmem_cols) {
     GemmArgs *a = reinterpret_cast<GemmArgs *>(args);
     int np = 0;
     n_items = 0;
     smem = 0;
+    tmem_cols = 32;
     for (int j = 0; j < n; ++j) {
         if (np + 2 > arg_cap) return -1;
         const int base_items = n_items;
@@ -907,15 +941,33 @@ int col_batch_prepare(mpi_ffl_handle *const *hs, const float *const *in, float *
         for (int i = 0; i < k; ++i) {
             int st = 0;
             smem = std::max(smem, smem_for(a[np + i].BN, st));
+            tmem_cols = std::max(tmem_cols, a[np + i].tmem_cols);
         }
         np += k;
     }
     return np;
 }
 
-void col_batch_launch(const void *dargs, const int4 *ditems, int n_items, size_t smem, cudaStream_t st) {
+void col_batch_launch(const void *dargs, const int4 *ditems, int n_items, size_t smem, uint32_t tmem_cols,
+                      cudaStream_t st) {
     if (n_items <= 0) return;
-    k_gemm_batch<<<n_items, kGemmThreads, smem, st>>>(reinterpret_cast<const GemmArgs *>(dargs), ditems);
+    static int n_sm = 0;
+    if (!n_sm) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+        if (n_sm <= 0) n_sm = 1;
+    }
+    int per = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_gemm_batch, kGemmThreads, smem + 16) != cudaSuccess ||
+        per < 1) {
+        (void)cudaGetLastError();
+        per = 1;
+    }
+    per = std::min(per, (int)(512 / std::max(32u, tmem_cols)));  // the TMEM columns of an SM
+    const int grid = std::max(1, std::min(n_items, per * n_sm));
+    k_gemm_batch<<<grid, kGemmThreads, smem + 16, st>>>(reinterpret_cast<const GemmArgs *>(dargs), ditems, n_items,
+                                                        tmem_cols, (uint32_t)smem);
 }
 
 void col_batch_init() {
@@ -980,6 +1032,7 @@ struct TensorState {
     int4 *ditems = nullptr;    // forward items, then adjoint items
     int n_items_f = 0, n_items_a = 0;
     size_t smem[2] = {0, 0};   // dynamic shared memory of the forward and adjoint launches
+    uint32_t cols[2] = {32, 32};  // TMEM columns a block of the forward and adjoint launches holds
 };
 
 // W_{par,d}[o][i] = sum_e W_par[o][e] g_d[e - D - Q i - kmin] in FP64 (g_d[k - kmin] =
@@ -1313,6 +1366,7 @@ bool ten_prepare(const mpi_ffl_handle *h, ColState *s, TensorState *t, int fmt) 
                 }
                 g.err = s->err;
                 g.done = nullptr;
+                t->cols[dir] = std::max(t->cols[dir], g.tmem_cols);
                 const int pi = (int)args.size() - base;
                 args.push_back(g);
                 for (int mt = 0; mt < mtiles; ++mt)
@@ -1429,7 +1483,9 @@ void ten_forward(mpi_ffl_handle *h, const float *proj, const float *coil, float 
     const Dims &d = h->d;
     const long long rows = (long long)d.M * d.Nz;
     ten_pack(t, proj, coil, d.M, d.Nz, d.N, t->Np, 0, st);
-    k_gemm_batch<<<t->n_items_f, kGemmThreads, t->smem[0], st>>>(t->dargs, t->ditems);
+    // one block per item (each holds up to 512 TMEM columns, one block per SM)
+    k_gemm_batch<<<t->n_items_f, kGemmThreads, t->smem[0] + 16, st>>>(t->dargs, t->ditems, t->n_items_f, t->cols[0],
+                                                                      (uint32_t)t->smem[0]);
     launch_coil_pad(t->c_fwd, nullptr, data, rows, d.Nz, 2 * d.nb, 2 * d.nb, st, t->nsplit[0], rows * 2 * d.nb);
 }
 
@@ -1440,7 +1496,8 @@ void ten_adjoint(mpi_ffl_handle *h, const float *data, const float *coil, float 
     const Dims &d = h->d;
     const long long rows = (long long)d.M * d.Nz;
     ten_pack(t, data, nullptr, d.M, d.Nz, 2 * d.nb, t->Op, 1, st);
-    k_gemm_batch<<<t->n_items_a, kGemmThreads, t->smem[1], st>>>(t->dargs + t->n_prob_f, t->ditems + t->n_items_f);
+    k_gemm_batch<<<t->n_items_a, kGemmThreads, t->smem[1] + 16, st>>>(t->dargs + t->n_prob_f, t->ditems + t->n_items_f,
+                                                                      t->n_items_a, t->cols[1], (uint32_t)t->smem[1]);
     launch_coil_pad(t->c_adj, coil, proj, rows, d.Nz, d.N, d.N, st, t->nsplit[1], rows * d.N);
 }
 

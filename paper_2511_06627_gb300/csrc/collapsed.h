@@ -24,8 +24,9 @@ void col_adjoint(mpi_ffl_handle *h, const float *data, bool full, const float *g
 size_t gemm_args_size();
 int col_batch_prepare(mpi_ffl_handle *const *hs, const float *const *in, float *const *out, const int *const *done,
                       int n, bool adjoint, void *args, int4 *items, int arg_cap, int item_cap, int &n_items,
-                      size_t &smem);
-void col_batch_launch(const void *dargs, const int4 *ditems, int n_items, size_t smem, cudaStream_t st);
+                      size_t &smem, uint32_t &tmem_cols);
+void col_batch_launch(const void *dargs, const int4 *ditems, int n_items, size_t smem, uint32_t tmem_cols,
+                      cudaStream_t st);
 void col_batch_init();
 
 // Slice-coupled operator of the tensor PSF (Appendix B, Eq. (31)): per-offset folded

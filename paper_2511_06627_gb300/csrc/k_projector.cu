@@ -5,6 +5,8 @@
 // geometry, so the interpolation weights are computed once per kZc samples.
 // Column-marched angles read a transposed copy of the volume, so that every
 // staged voxel line is contiguous.
+#include <algorithm>
+
 #include "internal.h"
 #include "tc_ptx.cuh"
 
@@ -687,43 +689,62 @@ __device__ __forceinline__ int batch_find(const int *__restrict__ offs, int n, i
     return lo;
 }
 
-__global__ void k_transpose_batch(const TransposeJob *__restrict__ jobs, const int *__restrict__ offs, int n) {
-    const int j = batch_find(offs, n, blockIdx.x);
-    const TransposeJob J = jobs[j];
-    if (J.done && *J.done) return;
-    int b = blockIdx.x - offs[j];
-    const int gx = (J.N + 31) / 32;
-    const int bx = b % gx, by = (b / gx) % gx, bz = b / (gx * gx);
-    transpose_body(J.vol, J.volT, J.N, bx, by, bz);
+// The batched kernels are persistent: a grid of at most as many blocks as the GPU holds
+// at once loops over the work items of every job (see batch_find). An item's arithmetic
+// does not depend on the block that runs it, so a job gives the same bits alone and in
+// any mix.
+__global__ void k_transpose_batch(const TransposeJob *__restrict__ jobs, const int *__restrict__ offs, int n,
+                                  int total) {
+    for (int bi = blockIdx.x; bi < total; bi += gridDim.x) {
+        const int j = batch_find(offs, n, bi);
+        const TransposeJob J = jobs[j];
+        if (J.done && *J.done) continue;
+        int b = bi - offs[j];
+        const int gx = (J.N + 31) / 32;
+        const int bx = b % gx, by = (b / gx) % gx, bz = b / (gx * gx);
+        __syncthreads();  // the tile of the previous item has been read
+        transpose_body(J.vol, J.volT, J.N, bx, by, bz);
+    }
 }
 
 template <int LD>
 __global__ void __launch_bounds__(1024 + 32) k_project_batch(const ProjectJob *__restrict__ jobs,
-                                                             const int *__restrict__ offs, int n, int *err) {
+                                                             const int *__restrict__ offs, int n, int total,
+                                                             int *err) {
     extern __shared__ __align__(128) float psm[];
-    const int j = batch_find(offs, n, blockIdx.x);
-    const ProjectJob J = jobs[j];
-    if (J.done && *J.done) return;
-    const int b = blockIdx.x - offs[j];
-    const int rays = (J.N + 31) / 32 * 32;
-    if ((int)threadIdx.x >= rays * kProjAnglesPerBlock + 32) {
-        // threads beyond this problem's block shape take no part (barrier counts use its shape)
+    uint64_t *bars = reinterpret_cast<uint64_t *>(psm + kPStages * kZc * LD);
+    for (int bi = blockIdx.x; bi < total; bi += gridDim.x) {
+        const int j = batch_find(offs, n, bi);
+        const ProjectJob J = jobs[j];
+        if (J.done && *J.done) continue;  // uniform over the block
+        const int b = bi - offs[j];
+        const int rays = (J.N + 31) / 32 * 32;
+        if ((int)threadIdx.x < rays * kProjAnglesPerBlock + 32)
+            project_pipe_body<LD>(J.vol, J.volT, J.ang, J.agroups, J.proj, J.N, J.Nz, rays, err, b % J.n_agroups,
+                                  b / J.n_agroups, psm);
+        else
+            __syncthreads();  // threads beyond this problem's block shape meet the body's one barrier
+        // every thread has left the item: its barriers are idle and are set up anew
         __syncthreads();
-        return;
+        if (threadIdx.x == 0)
+            for (int k = 0; k < 2 * kPStages; ++k) ptx::mbar_inval(&bars[k]);
+        __syncthreads();
     }
-    project_pipe_body<LD>(J.vol, J.volT, J.ang, J.agroups, J.proj, J.N, J.Nz, rays, err, b % J.n_agroups,
-                          b / J.n_agroups, psm);
 }
 
 __global__ void __launch_bounds__(kBpTX * kBpTY) k_backproject_batch(const BackprojectJob *__restrict__ jobs,
-                                                                    const int *__restrict__ offs, int n) {
+                                                                    const int *__restrict__ offs, int n, int total) {
     __shared__ BpShared S;
-    const int j = batch_find(offs, n, blockIdx.x);
-    const BackprojectJob J = jobs[j];
-    if (J.done && *J.done) return;
-    const int b = blockIdx.x - offs[j];
-    const int gx = (J.N + kBpTX - 1) / kBpTX, gy = (J.N + kBpTY - 1) / kBpTY;
-    backproject_body(J.proj, J.ang, J.vol, J.N, J.Nz, J.M, b % gx, (b / gx) % gy, b / (gx * gy), S);
+    for (int bi = blockIdx.x; bi < total; bi += gridDim.x) {
+        const int j = batch_find(offs, n, bi);
+        const BackprojectJob J = jobs[j];
+        if (J.done && *J.done) continue;  // uniform over the block
+        const int b = bi - offs[j];
+        const int gx = (J.N + kBpTX - 1) / kBpTX, gy = (J.N + kBpTY - 1) / kBpTY;
+        // the body starts each chunk of angles with a barrier, so the previous item's
+        // staging is no longer read when this one overwrites it
+        backproject_body(J.proj, J.ang, J.vol, J.N, J.Nz, J.M, b % gx, (b / gx) % gy, b / (gx * gy), S);
+    }
 }
 
 int transpose_blocks(int N, int Nz) { return ((N + 31) / 32) * ((N + 31) / 32) * Nz; }
@@ -732,8 +753,28 @@ int backproject_blocks(int N, int Nz) {
     return ((N + kBpTX - 1) / kBpTX) * ((N + kBpTY - 1) / kBpTY) * ((Nz + kBpZ - 1) / kBpZ);
 }
 
+// Blocks of a persistent batched launch: what the GPU holds at once, at most one per item.
+template <class K>
+int persistent_grid_p(K kernel, int threads, size_t smem, int total) {
+    static int n_sm = 0;
+    if (!n_sm) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+        if (n_sm <= 0) n_sm = 1;
+    }
+    int per = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, smem) != cudaSuccess || per < 1) {
+        (void)cudaGetLastError();  // a failed query is not the caller's error
+        per = 1;
+    }
+    return std::max(1, std::min(total, per * n_sm));
+}
+
 void launch_transpose_batch(const TransposeJob *jobs, const int *offs, int n, int total, cudaStream_t st) {
-    k_transpose_batch<<<total, dim3(32, 8), 0, st>>>(jobs, offs, n);
+    if (total <= 0) return;
+    k_transpose_batch<<<persistent_grid_p(k_transpose_batch, 256, 0, total), dim3(32, 8), 0, st>>>(jobs, offs, n,
+                                                                                                   total);
 }
 
 bool project_batch_ok(int N) { return N % 4 == 0 && pipe_ld(N) > 0; }
@@ -742,7 +783,8 @@ template <int LD>
 void launch_pbatch(const ProjectJob *jobs, const int *offs, int n, int total, int threads, int *err,
                    cudaStream_t st) {
     cudaFuncSetAttribute(k_project_batch<LD>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    k_project_batch<LD><<<total, threads, pipe_smem(LD), st>>>(jobs, offs, n, err);
+    const int grid = persistent_grid_p(k_project_batch<LD>, threads, pipe_smem(LD), total);
+    k_project_batch<LD><<<grid, threads, pipe_smem(LD), st>>>(jobs, offs, n, total, err);
 }
 
 // Every problem in the batch has N % 4 == 0 and N <= 512 (project_batch_ok); the ring
@@ -762,7 +804,9 @@ void launch_project_batch(const ProjectJob *jobs, const int *offs, int n, int to
 }
 
 void launch_backproject_batch(const BackprojectJob *jobs, const int *offs, int n, int total, cudaStream_t st) {
-    k_backproject_batch<<<total, dim3(kBpTX, kBpTY), 0, st>>>(jobs, offs, n);
+    if (total <= 0) return;
+    const int grid = persistent_grid_p(k_backproject_batch, kBpTX * kBpTY, 0, total);
+    k_backproject_batch<<<grid, dim3(kBpTX, kBpTY), 0, st>>>(jobs, offs, n, total);
 }
 
 }  // namespace mpiffl

@@ -270,76 +270,90 @@ __device__ __forceinline__ int batch_find_s(const int *__restrict__ offs, int n,
 
 constexpr int kVecPerBlock = 256 * 8;  // elements per block of the batched element-wise kernels
 
+// The batched kernels are persistent: a grid of at most as many blocks as the GPU holds
+// at once loops over the work items (item b belongs to the job j with offs[j] <= b <
+// offs[j + 1]), so one launch per kind serves every job whatever their count and sizes.
+// An item's arithmetic does not depend on the block that runs it.
 __global__ void __launch_bounds__(256) k_momentum_batch(const MomentumJob *__restrict__ jobs,
-                                                        const int *__restrict__ offs, int n) {
-    const int j = batch_find_s(offs, n, blockIdx.x);
-    const MomentumJob J = jobs[j];
-    if (J.done && *J.done) return;
-    const int64_t base = (int64_t)(blockIdx.x - offs[j]) * kVecPerBlock;
+                                                        const int *__restrict__ offs, int n, int total) {
+    for (int bi = blockIdx.x; bi < total; bi += gridDim.x) {
+        const int j = batch_find_s(offs, n, bi);
+        const MomentumJob J = jobs[j];
+        if (J.done && *J.done) continue;
+        const int64_t base = (int64_t)(bi - offs[j]) * kVecPerBlock;
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-        const int64_t i = base + u * 256 + threadIdx.x;
-        if (i < J.n) {
-            const float xi = J.x[i];
-            J.y[i] = fmaf(J.beta, xi - J.xp[i], xi);
+        for (int u = 0; u < 8; ++u) {
+            const int64_t i = base + u * 256 + threadIdx.x;
+            if (i < J.n) {
+                const float xi = J.x[i];
+                J.y[i] = fmaf(J.beta, xi - J.xp[i], xi);
+            }
         }
     }
 }
 
 __global__ void __launch_bounds__(kRedThreads) k_residual_batch(const ResidualJob *__restrict__ jobs,
-                                                                const int *__restrict__ offs, int n) {
-    const int j = batch_find_s(offs, n, blockIdx.x);
-    const ResidualJob J = jobs[j];
-    if (J.done && *J.done) return;
-    const int b = blockIdx.x - offs[j];
-    double acc = 0.0;
-    for (int64_t i = (int64_t)b * blockDim.x + threadIdx.x; i < J.n; i += (int64_t)J.nblk * blockDim.x) {
-        const float v = J.r[i] - J.b[i];
-        J.r[i] = v;
-        acc += (double)v * (double)v;
+                                                                const int *__restrict__ offs, int n, int total) {
+    for (int bi = blockIdx.x; bi < total; bi += gridDim.x) {
+        const int j = batch_find_s(offs, n, bi);
+        const ResidualJob J = jobs[j];
+        if (J.done && *J.done) continue;  // uniform over the block
+        const int b = bi - offs[j];
+        double acc = 0.0;
+        for (int64_t i = (int64_t)b * blockDim.x + threadIdx.x; i < J.n; i += (int64_t)J.nblk * blockDim.x) {
+            const float v = J.r[i] - J.b[i];
+            J.r[i] = v;
+            acc += (double)v * (double)v;
+        }
+        const double t = block_sum(acc);
+        if (threadIdx.x == 0) J.partials[b] = t;
+        __syncthreads();  // block_sum's shared words are reused by the next item
     }
-    const double t = block_sum(acc);
-    if (threadIdx.x == 0) J.partials[b] = t;
 }
 
 // one block per problem: partial sums in index order, then the stop test
-__global__ void __launch_bounds__(kRedThreads) k_stop_batch(const StopJob *__restrict__ jobs) {
-    const StopJob J = jobs[blockIdx.x];
-    if (*J.done) return;
-    double acc = 0.0;
-    for (int i = threadIdx.x; i < J.nblk; i += blockDim.x) acc += J.partials[i];
-    const double t = block_sum(acc);
-    if (threadIdx.x == 0) {
-        const double r = sqrt(t);
-        J.hist[J.k] = r;
-        J.flags[1] = J.k + 1;
-        if (!(r == r) || r > 1e300) {
-            J.flags[0] = 2;
-        } else if (J.stop_rel > 0.0 && J.k > 0) {
-            const double prev = J.hist[J.k - 1];
-            if (fabs(prev - r) <= J.stop_rel * prev) J.flags[0] = 1;
+__global__ void __launch_bounds__(kRedThreads) k_stop_batch(const StopJob *__restrict__ jobs, int n) {
+    for (int bi = blockIdx.x; bi < n; bi += gridDim.x) {
+        const StopJob J = jobs[bi];
+        if (*J.done) continue;
+        double acc = 0.0;
+        for (int i = threadIdx.x; i < J.nblk; i += blockDim.x) acc += J.partials[i];
+        const double t = block_sum(acc);
+        if (threadIdx.x == 0) {
+            const double r = sqrt(t);
+            J.hist[J.k] = r;
+            J.flags[1] = J.k + 1;
+            if (!(r == r) || r > 1e300) {
+                J.flags[0] = 2;
+            } else if (J.stop_rel > 0.0 && J.k > 0) {
+                const double prev = J.hist[J.k - 1];
+                if (fabs(prev - r) <= J.stop_rel * prev) J.flags[0] = 1;
+            }
         }
+        __syncthreads();
     }
 }
 
 __global__ void __launch_bounds__(128) k_update_batch(const UpdateJob *__restrict__ jobs, const int *__restrict__ offs,
-                                                      int n) {
-    const int j = batch_find_s(offs, n, blockIdx.x);
-    const UpdateJob J = jobs[j];
-    const int b = blockIdx.x - offs[j];
-    const int gx = (J.N + 127) / 128;
-    const int xx = (b % gx) * 128 + threadIdx.x;
-    const int yy = (b / gx) % J.N, z = b / (gx * J.N);
-    if (xx >= J.N) return;
-    const size_t i = ((size_t)z * J.N + yy) * J.N + xx;
-    if (J.done && *J.done) {  // frozen: keep the final iterate in the buffer that becomes x
-        J.xo[i] = J.xcur[i];
-        return;
+                                                      int n, int total) {
+    for (int bi = blockIdx.x; bi < total; bi += gridDim.x) {
+        const int j = batch_find_s(offs, n, bi);
+        const UpdateJob J = jobs[j];
+        const int b = bi - offs[j];
+        const int gx = (J.N + 127) / 128;
+        const int xx = (b % gx) * 128 + threadIdx.x;
+        const int yy = (b / gx) % J.N, z = b / (gx * J.N);
+        if (xx >= J.N) continue;
+        const size_t i = ((size_t)z * J.N + yy) * J.N + xx;
+        if (J.done && *J.done) {  // frozen: keep the final iterate in the buffer that becomes x
+            J.xo[i] = J.xcur[i];
+            continue;
+        }
+        const float grad = fmaf(J.lam, ttt_at(J.y, J.N, J.Nz, z, yy, xx), J.g[i]);
+        float v = fmaf(-J.tau, grad, J.y[i]);
+        if (J.nonneg) v = fmaxf(v, 0.f);
+        J.xo[i] = v;
     }
-    const float grad = fmaf(J.lam, ttt_at(J.y, J.N, J.Nz, z, yy, xx), J.g[i]);
-    float v = fmaf(-J.tau, grad, J.y[i]);
-    if (J.nonneg) v = fmaxf(v, 0.f);
-    J.xo[i] = v;
 }
 
 int update_blocks(int N, int Nz) { return ((N + 127) / 128) * N * Nz; }
@@ -353,15 +367,40 @@ void launch_freeze_batch(const StopJob *jobs, int n, cudaStream_t st) {
     k_freeze_batch<<<(n + 127) / 128, 128, 0, st>>>(jobs, n);
 }
 
+// Blocks of a persistent batched launch: what the GPU holds at once, at most one per item.
+template <class K>
+int persistent_grid(K kernel, int threads, size_t smem, int total) {
+    static int n_sm = 0;
+    if (!n_sm) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+        if (n_sm <= 0) n_sm = 1;
+    }
+    int per = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, smem) != cudaSuccess || per < 1) {
+        (void)cudaGetLastError();  // a failed query is not the caller's error
+        per = 1;
+    }
+    return std::max(1, std::min(total, per * n_sm));
+}
+
 void launch_momentum_batch(const MomentumJob *jobs, const int *offs, int n, int total, cudaStream_t st) {
-    k_momentum_batch<<<total, 256, 0, st>>>(jobs, offs, n);
+    if (total <= 0) return;
+    k_momentum_batch<<<persistent_grid(k_momentum_batch, 256, 0, total), 256, 0, st>>>(jobs, offs, n, total);
 }
 void launch_residual_batch(const ResidualJob *jobs, const int *offs, int n, int total, cudaStream_t st) {
-    k_residual_batch<<<total, kRedThreads, 0, st>>>(jobs, offs, n);
+    if (total <= 0) return;
+    k_residual_batch<<<persistent_grid(k_residual_batch, kRedThreads, 0, total), kRedThreads, 0, st>>>(jobs, offs, n,
+                                                                                                       total);
 }
-void launch_stop_batch(const StopJob *jobs, int n, cudaStream_t st) { k_stop_batch<<<n, kRedThreads, 0, st>>>(jobs); }
+void launch_stop_batch(const StopJob *jobs, int n, cudaStream_t st) {
+    if (n <= 0) return;
+    k_stop_batch<<<persistent_grid(k_stop_batch, kRedThreads, 0, n), kRedThreads, 0, st>>>(jobs, n);
+}
 void launch_update_batch(const UpdateJob *jobs, const int *offs, int n, int total, cudaStream_t st) {
-    k_update_batch<<<total, 128, 0, st>>>(jobs, offs, n);
+    if (total <= 0) return;
+    k_update_batch<<<persistent_grid(k_update_batch, 128, 0, total), 128, 0, st>>>(jobs, offs, n, total);
 }
 
 }  // namespace mpiffl
