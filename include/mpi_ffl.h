@@ -353,6 +353,16 @@ int mpi_ffl_line_adjoint(mpi_ffl_handle *h, const float *d_b_ri, float *d_proj, 
  * workspace (n_sig floats, allocated on first use). */
 int mpi_ffl_band_energy(mpi_ffl_handle *h, const float *d_x, double *d_bin_energy, double *d_total, void *stream);
 
+/* The information retained (Appendix A, Eq. (30)) by sub-bands of the kept bins, for the
+ * time signal of x (as mpi_ffl_band_energy computes it): for a = 0..n_k-1 and
+ * c = 0..n_w-1, d_out[a n_w + c] (device, FP64) = sqrt(2 sum_{q in S'} e_q / total) with
+ * S' the kept bins of harmonics k_min..k_max[a] and |delta| <= half_width[c], each bin
+ * counted with its conjugate. k_max (host, n_k <= 16 values in k_min..k_max of the
+ * handle) and half_width (host, n_w <= 16 values in 0..half_width of the handle); other
+ * values are MPI_FFL_ERR_INVALID_ARG. Uses the time-signal workspace. */
+int mpi_ffl_information_retained(mpi_ffl_handle *h, const float *d_x, int32_t n_k, const int32_t *k_max,
+                                 int32_t n_w, const int32_t *half_width, double *d_out, void *stream);
+
 /* T^T T x (Sec. 3.3, Eq. (25)) on a volume. */
 int mpi_ffl_apply_ttt(mpi_ffl_handle *h, const float *d_x, float *d_out, void *stream);
 

@@ -136,6 +136,8 @@ PROTOTYPES = {
     "mpi_ffl_test_live_allocs": (C.c_int, [C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "mpi_ffl_test_inject_timeout": (C.c_int, [H, C.c_uint32]),
     "mpi_ffl_probe_smem_bandwidth": (C.c_int, [C.POINTER(C.c_double), ST]),
+    "mpi_ffl_information_retained": (C.c_int, [H, FP, C.c_int32, C.POINTER(C.c_int32), C.c_int32,
+                                               C.POINTER(C.c_int32), FP, ST]),
 }
 
 KERNEL_KINDS = ["transpose", "project", "backproject", "psf_fwd", "psf_adj", "resample_fwd", "resample_adj",

@@ -377,7 +377,7 @@ void release(mpi_ffl_handle *h) {
                     h->w_proj, h->w_fine, h->w_sig, h->w_data, h->w_vol2, h->w_red, h->w_scal,
                     h->s_xp, h->s_y, h->s_g, h->s_r, h->s_hist, h->s_flags, h->tc_twb, h->t_agroups,
                     h->t_tnf, h->t_vr, h->w_err, h->t_coil, h->w_projc, h->w_scanvol, h->w_volI, h->w_volTI,
-                    h->t_ra_tile, h->t_ra_j, h->t_ra_w, h->t_twp};
+                    h->t_ra_tile, h->t_ra_j, h->t_ra_w, h->t_twp, h->w_bins};
     for (void *p : ptrs)
         if (p) dev_free(p);
     for (auto &r : h->prof_rec) {
@@ -1565,6 +1565,35 @@ extern "C" int mpi_ffl_band_energy(mpi_ffl_handle *h, const float *d_x, double *
         TIMED(MPI_FFL_K_DFT_FWD, launch_dft_fwd(h->w_sig, h->t_tw1, h->t_twp, h->t_tw2_ro, h->t_dgam_unit, h->w_data, d, h->w_err, st));
         TIMED(MPI_FFL_K_SOLVER, launch_bin_energy(h->w_data, d.nseg, d.nb, d_bin_energy, st));
         check_launch(h, "band energy");
+        return MPI_FFL_OK;
+    });
+}
+
+extern "C" int mpi_ffl_information_retained(mpi_ffl_handle *h, const float *d_x, int32_t n_k, const int32_t *k_max,
+                                            int32_t n_w, const int32_t *half_width, double *d_out, void *stream) {
+    return guarded(h, [&]() {
+        const Dims &d = h->d;
+        if (!d_x || !d_out || !k_max || !half_width || n_k < 1 || n_k > 16 || n_w < 1 || n_w > 16) {
+            h->err = "NULL buffer or sub-band count outside 1..16";
+            return MPI_FFL_ERR_INVALID_ARG;
+        }
+        for (int i = 0; i < n_k; ++i)
+            if (k_max[i] < d.kmin || k_max[i] > d.kmin + d.K - 1) {
+                h->err = "harmonic limit outside the kept harmonics";
+                return MPI_FFL_ERR_INVALID_ARG;
+            }
+        for (int i = 0; i < n_w; ++i)
+            if (half_width[i] < 0 || half_width[i] > d.hw) {
+                h->err = "half-width outside the kept bins";
+                return MPI_FFL_ERR_INVALID_ARG;
+            }
+        if (!h->w_bins) dev_alloc(h, &h->w_bins, (size_t)d.nb + 1);
+        const int rc = mpi_ffl_band_energy(h, d_x, h->w_bins, h->w_bins + d.nb, stream);
+        if (rc != MPI_FFL_OK) return rc;
+        cudaStream_t st = S(stream);
+        TIMED(MPI_FFL_K_SOLVER, launch_info_retained(h->w_bins, h->w_bins + d.nb, d.kmin, d.hw, n_k, k_max, n_w,
+                                                     half_width, d_out, st));
+        check_launch(h, "information retained");
         return MPI_FFL_OK;
     });
 }

@@ -122,6 +122,7 @@ struct mpi_ffl_handle {
     std::vector<int> csr_ptr_host;        // host copies of the CSR, n_par * (Ne + 1) and n_par * 2L
     std::vector<mpiffl::CsrEntry> csr_host;
     float2 *t_twp = nullptr;              // [P] e^{2 pi i q / P}: the period twiddles of the band DFT
+    double *w_bins = nullptr;             // n_bins + 1: kept-bin energies and the total (information retained)
     int *t_csr_ptr = nullptr;             // n_par * (Ne + 1)
     mpiffl::CsrEntry *t_csr = nullptr;    // n_par * 2L
     float *t_tw1 = nullptr;               // P * W: cos(2 pi d p / P) d=0..hw, sin d=1..hw
@@ -345,6 +346,8 @@ void launch_update(const float *y, const float *g, float *xout, float tau, float
                    int N, int Nz, const int *done, cudaStream_t st, const float *xcur = nullptr);
 void launch_freeze(const int *stop, int *frozen, cudaStream_t st);
 void launch_bin_energy(const float *data, int nseg, int nb, double *out, cudaStream_t st);
+void launch_info_retained(const double *bin_energy, const double *total, int kmin, int w_all, int n_k,
+                          const int *hk, int n_w, const int *hw, double *out, cudaStream_t st);
 void launch_transpose_2d(const float *in, float *out, int batch, int rows, int cols, cudaStream_t st);
 void launch_resample_z_fwd(const float *cz, const ZTables &T, const float *gain, float *sig, const Dims &d,
                            int zigzag, cudaStream_t st);

@@ -9,6 +9,39 @@
 
 namespace mpiffl {
 
+// Information retained by sub-bands of the kept bins (Appendix A, Eq. (30)): thread t =
+// (harmonic limit a, half-width c) sums, in a fixed order, the per-bin energies of the
+// bins with harmonics k_min..hk[a] and |delta| <= hw[c] (each bin counted with its
+// conjugate, which carries the same energy for a real signal) and writes
+// sqrt(2 sum / total), 0 for a zero total.
+struct InfoBands {
+    int n_k, n_w;
+    int hk[16], hw[16];
+};
+
+__global__ void k_info_retained(const double *__restrict__ bin_energy, const double *__restrict__ total, int kmin,
+                                int w_all, InfoBands B, double *__restrict__ out) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= B.n_k * B.n_w) return;
+    const int a = t / B.n_w, c = t - a * B.n_w;
+    const int W = 2 * w_all + 1;
+    double sub = 0.0;
+    for (int k = 0; k <= B.hk[a] - kmin; ++k)
+        for (int dd = -B.hw[c]; dd <= B.hw[c]; ++dd) sub += bin_energy[k * W + w_all + dd];
+    const double tot = *total;
+    out[t] = tot > 0.0 ? sqrt(2.0 * sub / tot) : 0.0;
+}
+
+void launch_info_retained(const double *bin_energy, const double *total, int kmin, int w_all, int n_k,
+                          const int *hk, int n_w, const int *hw, double *out, cudaStream_t st) {
+    InfoBands B{};
+    B.n_k = n_k;
+    B.n_w = n_w;
+    for (int i = 0; i < n_k; ++i) B.hk[i] = hk[i];
+    for (int i = 0; i < n_w; ++i) B.hw[i] = hw[i];
+    k_info_retained<<<(n_k * n_w + 127) / 128, 128, 0, st>>>(bin_energy, total, kmin, w_all, B, out);
+}
+
 // Block per box: over the box's voxels, part[b] = (count, sum, max) when pass == 0,
 // (count, sum |v - mean[g[b]]|, max) when pass == 1. Each thread visits a fixed set of
 // voxels and the block reduces in a fixed order: the sums are reproducible.

@@ -184,21 +184,20 @@ class FFLOperator:
     def information_retained(self, x, harmonics, half_widths):
         """I(s, S) of Eq. (30) for the time signal of x, for every sub-band of the kept
         bins with harmonics k_min..K (K in `harmonics`) and |delta| <= w (w in
-        `half_widths`), each bin counted with its conjugate L - omega. Returns a
-        [len(harmonics), len(half_widths)] numpy array."""
-        import numpy as np
-
-        e, tot = self.band_energy(x)
-        w_all = self.half_width
-        e = e.reshape(self.k_max - self.k_min + 1, 2 * w_all + 1)
-        out = np.zeros((len(harmonics), len(half_widths)))
-        for a, K in enumerate(harmonics):
-            for c, w in enumerate(half_widths):
-                if not (self.k_min <= K <= self.k_max and 0 <= w <= w_all):
-                    raise ValueError("sub-band outside the kept bins")
-                sub = e[: K - self.k_min + 1, w_all - w: w_all + w + 1].sum()
-                out[a, c] = math.sqrt(2.0 * sub / tot) if tot > 0 else 0.0
-        return out
+        `half_widths`), each bin counted with its conjugate L - omega (computed by the
+        library: mpi_ffl_information_retained). Returns a [len(harmonics),
+        len(half_widths)] numpy array."""
+        self._check(x, self.vol_shape, "x")
+        ks = [int(k) for k in harmonics]
+        ws = [int(w) for w in half_widths]
+        if not all(self.k_min <= k <= self.k_max for k in ks) or not all(0 <= w <= self.half_width for w in ws):
+            raise ValueError("sub-band outside the kept bins")
+        out = torch.empty((len(ks), len(ws)), device=self.device, dtype=torch.float64)
+        ka = (C.c_int32 * len(ks))(*ks)
+        wa = (C.c_int32 * len(ws))(*ws)
+        check(self._lib.mpi_ffl_information_retained(self._h, _ptr(x), len(ks), ka, len(ws), wa, _ptr(out),
+                                                     _stream()), self._h)
+        return out.cpu().numpy()
 
     def apply_ttt(self, x):
         self._check(x, self.vol_shape, "x")
