@@ -567,7 +567,13 @@ struct __align__(16) BpShared {
     float seg[kBpChunk][kBpSeg][kBpRow];
     AngleParam ang[kBpChunk];
     int ilo[kBpChunk];
+    // per angle and march step s = (row-major ? y_lo : x_lo) + ds of the tile: the
+    // step's Q32.32 base position fx_a + s fx_b, and slope (s - c) + c of the nearest-ray
+    // estimate, the same operations the thread would do for its own step
+    long long gs[kBpChunk][kBpTX];
+    float bs[kBpChunk][kBpTX];
 };
+static_assert(kBpTX >= kBpTY, "the per-step tables hold the tile's longer side");
 
 __device__ __forceinline__ int nearest_ray(const AngleParam &a, int s, int q, float c) {
     const float sm = (float)s - c;
@@ -619,19 +625,27 @@ __device__ __forceinline__ void backproject_body(const float *__restrict__ proj,
             for (int g4 = 0; g4 < kBpZ / 4; ++g4)
                 dst[g4] = make_float4(v[4 * g4], v[4 * g4 + 1], v[4 * g4 + 2], v[4 * g4 + 3]);
         }
+        for (int t = tid; t < na * kBpTX; t += kBpTX * kBpTY) {
+            const int a = t / kBpTX, ds = t - a * kBpTX;
+            const AngleParam A = S.ang[a];
+            const int s = (A.row_major ? ylo : xlo) + ds;
+            S.gs[a][ds] = A.fx_a + (long long)s * A.fx_b;
+            S.bs[a][ds] = fmaf(A.slope, (float)s - c, c);
+        }
         __syncthreads();
         for (int a = 0; a < na; ++a) {
-            const AngleParam A = S.ang[a];
-            const int s = A.row_major ? iy : ix;  // march step holding this voxel
-            const int q = A.row_major ? ix : iy;  // its index along the step's line
+            const bool rm = S.ang[a].row_major != 0;
+            const int ds = rm ? iy - ylo : ix - xlo;  // march step holding this voxel, within the tile
+            const int q = rm ? ix : iy;              // its index along the step's line
+            const long long fxd = S.ang[a].fx_d;
             // nearest ray (estimate): inv_c (i - c) + slope (s - c) + c = q
-            const int i1 = __float2int_rn(fmaf((float)q - fmaf(A.slope, (float)s - c, c), A.inv_c_rcp, c));
+            const int i1 = __float2int_rn(fmaf((float)q - S.bs[a][ds], S.ang[a].inv_c_rcp, c));
             // the forward's fixed-point positions of rays i1-1, i1, i1+1 at step s, and
             // the weights it gives cell q: 1 - t from a ray in cell q, t from one in q-1
-            long long g = A.fx_a + (long long)s * A.fx_b + (long long)(i1 - 1) * A.fx_d;
+            long long g = S.gs[a][ds] + (long long)(i1 - 1) * fxd;
             float w[3];
 #pragma unroll
-            for (int u = 0; u < 3; ++u, g += A.fx_d) {
+            for (int u = 0; u < 3; ++u, g += fxd) {
                 int k;
                 float t;
                 fx_split(g, k, t);
@@ -661,7 +675,7 @@ __device__ __forceinline__ void backproject_body(const float *__restrict__ proj,
     }
 }
 
-__global__ void __launch_bounds__(kBpTX * kBpTY) k_backproject(const float *__restrict__ proj,
+__global__ void __launch_bounds__(kBpTX * kBpTY, 2) k_backproject(const float *__restrict__ proj,
                                                               const AngleParam *__restrict__ ang,
                                                               float *__restrict__ vol, int N, int Nz, int M) {
     __shared__ BpShared S;
@@ -732,7 +746,7 @@ __global__ void __launch_bounds__(1024 + 32) k_project_batch(const ProjectJob *_
     }
 }
 
-__global__ void __launch_bounds__(kBpTX * kBpTY) k_backproject_batch(const BackprojectJob *__restrict__ jobs,
+__global__ void __launch_bounds__(kBpTX * kBpTY, 2) k_backproject_batch(const BackprojectJob *__restrict__ jobs,
                                                                     const int *__restrict__ offs, int n, int total) {
     __shared__ BpShared S;
     for (int bi = blockIdx.x; bi < total; bi += gridDim.x) {
