@@ -678,7 +678,7 @@ void line_adjoint_body(mpi_ffl_handle *h, const float *b, float *proj, cudaStrea
         check_launch(h, "tc_adjoint");
     } else {
         ensure_sig(h);
-        TIMED(MPI_FFL_K_DFT_ADJ, launch_dft_adj(b, h->t_tw1, h->t_tw2_qr, h->t_dgam, h->w_sig, d, st));
+        TIMED(MPI_FFL_K_DFT_ADJ, launch_dft_adj(b, h->t_tw1, h->t_twp, h->t_tw2_qr, h->t_dgam, h->w_sig, d, st));
         check_launch(h, "dft_adj");
         TIMED(MPI_FFL_K_RESAMPLE_ADJ, resample_adj(h, h->w_sig, h->w_fine, st));
         check_launch(h, "resample_adj");
@@ -1464,7 +1464,7 @@ extern "C" int mpi_ffl_apply_stage(mpi_ffl_handle *h, int32_t stage, int32_t tra
             case 4: TIMED(MPI_FFL_K_RESAMPLE_FWD, launch_resample_fwd(in, h->t_traj, h->t_gain, h->t_groups, h->n_groups, out, d, st)); break;
             case 5: TIMED(MPI_FFL_K_RESAMPLE_ADJ, resample_adj(h, in, out, st)); break;
             case 6: TIMED(MPI_FFL_K_DFT_FWD, launch_dft_fwd(in, h->t_tw1, h->t_twp, h->t_tw2_ro, h->t_dgam, out, d, h->w_err, st)); break;
-            case 7: TIMED(MPI_FFL_K_DFT_ADJ, launch_dft_adj(in, h->t_tw1, h->t_tw2_qr, h->t_dgam, out, d, st)); break;
+            case 7: TIMED(MPI_FFL_K_DFT_ADJ, launch_dft_adj(in, h->t_tw1, h->t_twp, h->t_tw2_qr, h->t_dgam, out, d, st)); break;
         }
         check_launch(h, "apply_stage");
         return MPI_FFL_OK;

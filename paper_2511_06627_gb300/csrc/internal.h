@@ -82,7 +82,7 @@ constexpr int kGroup = 8;          // lines per SegGroup in the staged kernels
 constexpr int kRaMaxEntries = 80;  // CSR entries per fine cell the tiled E V B transpose holds
 constexpr int kRaTileCells = 256;  // fine cells per tile of the tiled E V B transpose
 constexpr int kRaMaxWindow = 24576;  // samples of a tile's window it stages (96 KB)
-constexpr int kPsfT = 8;           // outputs per thread in the PSF kernels
+constexpr int kPsfT = 16;          // tap-table padding, in outputs per phase, of the PSF kernels' windows
 constexpr int kMaxHw = 8;          // largest supported half-width
 
 }  // namespace mpiffl
@@ -331,7 +331,7 @@ void launch_resample_adj(const float *sig, const int *csr_ptr, const CsrEntry *c
                          const Dims &d, cudaStream_t st);
 void launch_dft_fwd(const float *sig, const float *tw1, const float2 *twp, const float2 *tw2_ro, const float2 *dgam,
                     float *data, const Dims &d, int *err, cudaStream_t st);
-void launch_dft_adj(const float *data, const float *tw1, const float2 *tw2_qr, const float2 *dgam,
+void launch_dft_adj(const float *data, const float *tw1, const float2 *twp, const float2 *tw2_qr, const float2 *dgam,
                     float *sig, const Dims &d, cudaStream_t st);
 
 // Solver and reductions (k_solver.cu)

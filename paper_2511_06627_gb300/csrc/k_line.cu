@@ -3,8 +3,8 @@
 // of one angle: proj[seg][N] -> fine[seg][N_e] -> sig[seg][L] -> data[seg][nb].
 //
 // H   : full-support polyphase convolution on the fine grid. Output e has phase
-//       (e - D) mod Q; a thread owns kPsfT outputs of one phase and slides a
-//       register window over the tap table, so each tap load feeds kPsfT FMAs.
+//       (e - D) mod Q; a thread owns kPsfTF outputs of one phase and slides a
+//       register window over the tap table, so each tap load feeds kPsfTF FMAs.
 // EVB : velocity-weighted linear interpolation at the FFL positions; the
 //       trajectory table is read once per group of kGroup lines that share it.
 //       The transpose gathers through a per-trajectory CSR (fine cell <- samples).
@@ -19,6 +19,15 @@ namespace mpiffl {
 
 // ----------------------------------------------------------------------------- H
 
+// Nine outputs per thread: at Q = 8 the 30 register blocks of the 8 phases of a
+// 256-bin line fill one round of 256 threads, and lanes of different blocks read taps
+// 9 Q words apart, in distinct banks (with eight, 34 blocks took two rounds and four
+// lanes shared each bank).
+constexpr int kPsfTF = 9;
+// sixteen outputs per lane in the transpose: 16 FMAs per pair of shared loads
+constexpr int kPsfTA = 16;
+static_assert(kPsfTF <= kPsfT && kPsfTA <= kPsfT, "the tap table is padded for the windows");
+
 __global__ void __launch_bounds__(256) k_psf_fwd(const float *__restrict__ proj,
                                                  const float *__restrict__ htab,
                                                  float *__restrict__ fine, Dims d) {
@@ -31,29 +40,32 @@ __global__ void __launch_bounds__(256) k_psf_fwd(const float *__restrict__ proj,
     __syncthreads();
     const int Q = d.Q;
     const int n_a = (d.Ne + Q - 1) / Q;               // fine points per phase (upper bound)
-    const int n_ab = (n_a + kPsfT - 1) / kPsfT;       // register blocks per phase
+    const int n_ab = (n_a + kPsfTF - 1) / kPsfTF;       // register blocks per phase
     for (int task = threadIdx.x; task < Q * n_ab; task += blockDim.x) {
         const int q = task % Q;
         const int ab = task / Q;
-        const int base = q - d.D + d.htab_off + Q * ab * kPsfT;
-        float w[kPsfT], acc[kPsfT];
+        const int base = q - d.D + d.htab_off + Q * ab * kPsfTF;
+        float w[kPsfTF], acc[kPsfTF];
 #pragma unroll
-        for (int t = 0; t < kPsfT; ++t) {
+        for (int t = 0; t < kPsfTF; ++t) {
             w[t] = sh[base + Q * t];
             acc[t] = 0.f;
         }
+        // unrolled by the window length, so that the window's shift is a renaming of
+        // registers rather than moves
+#pragma unroll kPsfTF
         for (int i = 0; i < d.N; ++i) {
             const float pi = sp[i];
 #pragma unroll
-            for (int t = 0; t < kPsfT; ++t) acc[t] = fmaf(pi, w[t], acc[t]);
+            for (int t = 0; t < kPsfTF; ++t) acc[t] = fmaf(pi, w[t], acc[t]);
 #pragma unroll
-            for (int t = kPsfT - 1; t > 0; --t) w[t] = w[t - 1];
+            for (int t = kPsfTF - 1; t > 0; --t) w[t] = w[t - 1];
             w[0] = sh[base - Q * (i + 1)];
         }
         float *out = fine + (size_t)seg * d.Ne;
 #pragma unroll
-        for (int t = 0; t < kPsfT; ++t) {
-            const int e = q + Q * (ab * kPsfT + t);
+        for (int t = 0; t < kPsfTF; ++t) {
+            const int e = q + Q * (ab * kPsfTF + t);
             if (e < d.Ne) out[e] = acc[t];
         }
     }
@@ -67,7 +79,7 @@ void launch_psf_fwd(const float *proj, const float *htab, float *fine, const Dim
 }
 
 // H^T: proj[i] = sum_e fine[e] h((e - D)/Q - i). Lanes of a warp are
-// (segment s = lane / Q, phase q = lane % Q): each owns kPsfT outputs i0..i0+T-1 of its
+// (segment s = lane / Q, phase q = lane % Q): each owns kPsfTA outputs i0..i0+T-1 of its
 // segment and sums the fine points of its phase with a sliding tap window; the Q
 // phase partials are then added with shuffles. Rows sit kPsfRowPad floats apart
 // modulo 32 so that the lanes' row reads fall in distinct banks, and the tap
@@ -94,34 +106,35 @@ __global__ void __launch_bounds__(kPsfAdjThreads) k_psf_adj(const float *__restr
     const int nwarps = blockDim.x >> 5;
     const int q = lane % Q;
     const int sl = lane / Q;               // segment within the block handled by this lane
-    const int n_ib = (d.N + kPsfT - 1) / kPsfT;
+    const int n_ib = (d.N + kPsfTA - 1) / kPsfTA;
     const bool active_seg = sl < nsg;
     const float *row = sf + (active_seg ? sl : 0) * row_stride;
     for (int ib = warp; ib < n_ib; ib += nwarps) {
-        const int i0 = ib * kPsfT;
-        float acc[kPsfT];
+        const int i0 = ib * kPsfTA;
+        float acc[kPsfTA];
 #pragma unroll
-        for (int t = 0; t < kPsfT; ++t) acc[t] = 0.f;
+        for (int t = 0; t < kPsfTA; ++t) acc[t] = 0.f;
         const int baseq = q - d.D - Q * i0 + d.htab_off;
-        float w[kPsfT];
+        float w[kPsfTA];
 #pragma unroll
-        for (int t = 0; t < kPsfT; ++t) w[t] = sh[baseq - Q * t];
+        for (int t = 0; t < kPsfTA; ++t) w[t] = sh[baseq - Q * t];
+#pragma unroll kPsfTA
         for (int a = 0, e = q; e < d.Ne; ++a, e += Q) {
             const float c = row[e];
 #pragma unroll
-            for (int t = 0; t < kPsfT; ++t) acc[t] = fmaf(c, w[t], acc[t]);
+            for (int t = 0; t < kPsfTA; ++t) acc[t] = fmaf(c, w[t], acc[t]);
 #pragma unroll
-            for (int t = kPsfT - 1; t > 0; --t) w[t] = w[t - 1];
+            for (int t = kPsfTA - 1; t > 0; --t) w[t] = w[t - 1];
             w[0] = sh[baseq + Q * (a + 1)];
         }
         // add the Q phase partials (lanes sl*Q .. sl*Q+Q-1)
 #pragma unroll
-        for (int t = 0; t < kPsfT; ++t)
+        for (int t = 0; t < kPsfTA; ++t)
             for (int o = 1; o < Q; o <<= 1) acc[t] += __shfl_xor_sync(0xffffffffu, acc[t], o);
         if (active_seg && q == 0) {
             float *out = proj + (size_t)(seg0 + sl) * d.N;
 #pragma unroll
-            for (int t = 0; t < kPsfT; ++t)
+            for (int t = 0; t < kPsfTA; ++t)
                 if (i0 + t < d.N) out[i0 + t] = acc[t];
         }
     }
@@ -611,6 +624,96 @@ static void dft_fwd_hw(const float *sig, const float *tw1, const float2 *tw2_ro,
     k_dft_fwd<HW><<<d.nseg, 128, smem, st>>>(sig, tw1, tw2_ro, dgam, data, d, (float)(1.0 / sqrt((double)d.L)));
 }
 
+// Streaming transpose (S % 4 == 0, S <= 128): a warp owns one segment and lane l the
+// phases 4l..4l+3. Each lane forms its phases' coefficients A_d, B_d as the
+// one-phase-per-thread form does, then writes the segment period by period with one
+// 16-byte store (four phases) per lane: 512 contiguous bytes per warp and period. The
+// period twiddles come from the e^{2 pi i q / P} table at q = d p mod P (the same values).
+template <int HW>
+__global__ void __launch_bounds__(32 * kDfWarps) k_dft_adj_stream(const float *__restrict__ data,
+                                                                  const float2 *__restrict__ twp,
+                                                                  const float2 *__restrict__ tw2_qr,
+                                                                  const float2 *__restrict__ dgam,
+                                                                  float *__restrict__ sig, Dims d,
+                                                                  float inv_sqrt_l) {
+    constexpr int W = 2 * HW + 1;
+    extern __shared__ __align__(16) float da_sm[];
+    float2 *stp = reinterpret_cast<float2 *>(da_sm);  // [P]
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float2 *sy = stp + d.P + (size_t)warp * d.nb;     // this warp's conj(D) y / sqrt(L)
+    for (int i = threadIdx.x; i < d.P; i += blockDim.x) stp[i] = twp[i];
+    const int seg = blockIdx.x * kDfWarps + warp;
+    if (seg < d.nseg)
+        for (int o = lane; o < d.nb; o += 32) {
+            const float2 y = ((const float2 *)data)[(size_t)seg * d.nb + o];
+            const float2 g = dgam[o];
+            sy[o] = make_float2((g.x * y.x + g.y * y.y) * inv_sqrt_l, (g.x * y.y - g.y * y.x) * inv_sqrt_l);
+        }
+    __syncthreads();
+    if (seg >= d.nseg || lane >= d.S / 4) return;
+    float A[4][HW + 1], B[4][HW + 1];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int r = 4 * lane + i;
+        float ur[W], ui[W];
+#pragma unroll
+        for (int k = 0; k < W; ++k) ur[k] = ui[k] = 0.f;
+        for (int k = 0; k < d.K; ++k) {
+#pragma unroll
+            for (int di = 0; di < W; ++di) {
+                const int o = k * W + di;
+                const float2 y = sy[o];
+                const float2 w = __ldg(tw2_qr + (size_t)o * d.S + r);
+                ur[di] = fmaf(y.x, w.x, fmaf(y.y, w.y, ur[di]));
+                ui[di] = fmaf(y.y, w.x, fmaf(-y.x, w.y, ui[di]));
+            }
+        }
+        A[i][0] = ur[HW];
+        B[i][0] = 0.f;
+#pragma unroll
+        for (int k = 1; k <= HW; ++k) {
+            A[i][k] = ur[HW + k] + ur[HW - k];
+            B[i][k] = ui[HW + k] - ui[HW - k];
+        }
+    }
+    float4 *out = reinterpret_cast<float4 *>(sig + (size_t)seg * d.L) + lane;
+    int idx[HW + 1];  // d p mod P
+#pragma unroll
+    for (int k = 0; k <= HW; ++k) idx[k] = 0;
+    const int q4 = d.S / 4;
+    for (int p = 0; p < d.P; ++p) {
+        float2 t[HW + 1];
+#pragma unroll
+        for (int k = 0; k <= HW; ++k) t[k] = stp[idx[k]];
+        float v[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            float acc = 0.f;
+#pragma unroll
+            for (int k = 0; k <= HW; ++k) acc = fmaf(A[i][k], t[k].x, acc);
+#pragma unroll
+            for (int k = 1; k <= HW; ++k) acc = fmaf(B[i][k], t[k].y, acc);
+            v[i] = acc;
+        }
+        out[(size_t)p * q4] = make_float4(v[0], v[1], v[2], v[3]);
+#pragma unroll
+        for (int k = 1; k <= HW; ++k) {
+            idx[k] += k;
+            if (idx[k] >= d.P) idx[k] -= d.P;
+        }
+    }
+}
+
+template <int HW>
+static void dft_adj_stream_hw(const float *data, const float2 *twp, const float2 *tw2_qr, const float2 *dgam,
+                              float *sig, const Dims &d, cudaStream_t st) {
+    const size_t smem = sizeof(float2) * ((size_t)d.P + (size_t)kDfWarps * d.nb);
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(k_dft_adj_stream<HW>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    k_dft_adj_stream<HW><<<(d.nseg + kDfWarps - 1) / kDfWarps, 32 * kDfWarps, smem, st>>>(
+        data, twp, tw2_qr, dgam, sig, d, (float)(1.0 / sqrt((double)d.L)));
+}
+
 template <int HW>
 static void dft_adj_hw(const float *data, const float *tw1, const float2 *tw2_qr, const float2 *dgam,
                        float *sig, const Dims &d, cudaStream_t st) {
@@ -643,8 +746,13 @@ void launch_dft_fwd(const float *sig, const float *tw1, const float2 *twp, const
     MPIFFL_HW_DISPATCH(dft_fwd_hw, sig, tw1, tw2_ro, dgam, data, d, st);
 }
 
-void launch_dft_adj(const float *data, const float *tw1, const float2 *tw2_qr, const float2 *dgam,
+void launch_dft_adj(const float *data, const float *tw1, const float2 *twp, const float2 *tw2_qr, const float2 *dgam,
                     float *sig, const Dims &d, cudaStream_t st) {
+    if (twp && d.S % 4 == 0 && d.S <= 128 && d.L % 4 == 0 && (reinterpret_cast<uintptr_t>(sig) & 15) == 0 &&
+        sizeof(float2) * ((size_t)d.P + (size_t)kDfWarps * d.nb) <= 200 * 1024) {
+        MPIFFL_HW_DISPATCH(dft_adj_stream_hw, data, twp, tw2_qr, dgam, sig, d, st);
+        return;
+    }
     MPIFFL_HW_DISPATCH(dft_adj_hw, data, tw1, tw2_qr, dgam, sig, d, st);
 }
 
