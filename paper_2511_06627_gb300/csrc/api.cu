@@ -478,17 +478,23 @@ void ensure_sig(mpi_ffl_handle *h) {
 }
 
 // ------------------------------------------------------------ stages
-void stage_p(mpi_ffl_handle *h, const float *x, float *proj, cudaStream_t st) {
+// With pack.out[0] set, the interleaved projector writes the forward full stage's A
+// operand instead of the projections; returns whether it did (the other projector
+// always stores the projections).
+bool stage_p(mpi_ffl_handle *h, const float *x, float *proj, cudaStream_t st, const ProjPack &pack = ProjPack{}) {
     if (h->w_volI) {  // the interleaved projector: both orientations from one pass over x
+        const bool packed = pack.out[0] != nullptr;
         TIMED(MPI_FFL_K_TRANSPOSE, launch_interleave(x, h->w_volI, h->w_volTI, h->d.N, h->d.Nz, st));
-        TIMED(MPI_FFL_K_PROJECT, launch_project_il(h->w_volI, h->w_volTI, h->t_ang, h->t_agroups, h->n_agroups, proj,
-                                                   h->d.N, h->d.Nz, st, h->w_err, h->inject_polls));
+        TIMED(MPI_FFL_K_PROJECT, launch_project_il(h->w_volI, h->w_volTI, h->t_ang, h->t_agroups, h->n_agroups,
+                                                   packed ? nullptr : proj, h->d.N, h->d.Nz, st, h->w_err,
+                                                   h->inject_polls, pack));
         check_launch(h, "project");
-        return;
+        return packed;
     }
     if (any_column_angle(h)) TIMED(MPI_FFL_K_TRANSPOSE, launch_transpose_xy(x, h->w_volT, h->d.N, h->d.Nz, st));
     TIMED(MPI_FFL_K_PROJECT, launch_project(x, h->w_volT, h->t_ang, h->t_agroups, h->n_agroups, proj, h->d.N, h->d.Nz, st, h->w_err));
     check_launch(h, "project");
+    return false;
 }
 
 // Tiles of the staged E V B transpose, built on its first use (only the staged path and
@@ -617,8 +623,9 @@ void stage_pt(mpi_ffl_handle *h, const float *proj, float *x, cudaStream_t st) {
 }
 
 // blockdiag(A_DC) on projections: proj -> data
+// prepacked: the projector wrote the full stage's A operand (proj not stored)
 void line_forward_impl(mpi_ffl_handle *h, const float *proj, float *b, const float *htab, const float *gain,
-                       cudaStream_t st) {
+                       cudaStream_t st, bool prepacked = false) {
     const Dims &d = h->d;
     if (h->psf_model == MPI_FFL_PSF_TENSOR) {
         // slices coupled by the tensor PSF; the coil map and the gains are applied inside
@@ -633,7 +640,7 @@ void line_forward_impl(mpi_ffl_handle *h, const float *proj, float *b, const flo
     int path = h->path;
     if (path == MPI_FFL_PATH_FULL_GEMM && htab != h->t_htab) path = MPI_FFL_PATH_LINE_GEMM;  // other taps
     if (path == MPI_FFL_PATH_FULL_GEMM) {
-        TIMED(MPI_FFL_K_GEMM_FWD, col_forward(h, proj, true, gain, b, st));
+        TIMED(MPI_FFL_K_GEMM_FWD, col_forward(h, proj, true, gain, b, st, prepacked));
         check_launch(h, "gemm_fwd");
         return;
     }
@@ -658,8 +665,14 @@ void line_forward_impl(mpi_ffl_handle *h, const float *proj, float *b, const flo
 
 void forward_impl(mpi_ffl_handle *h, const float *x, float *b, const float *htab, const float *gain,
                   cudaStream_t st) {
-    stage_p(h, x, h->w_proj, st);
-    line_forward_impl(h, h->w_proj, b, htab, gain, st);
+    // The full-GEMM stage with the collinear PSF's own taps, no coil map: the projector
+    // splits its sums into the GEMM's A operand itself (the packing pass and the
+    // projections' round trip through HBM drop out; the same bf16 hi + lo values).
+    ProjPack pack{};
+    const bool fold = h->path == MPI_FFL_PATH_FULL_GEMM && h->psf_model != MPI_FFL_PSF_TENSOR && !h->t_coil &&
+                      htab == h->t_htab && col_prepack_targets(h, &pack);
+    const bool packed = stage_p(h, x, h->w_proj, st, fold ? pack : ProjPack{});
+    line_forward_impl(h, h->w_proj, b, htab, gain, st, packed);
 }
 
 // blockdiag(A_DC)^T without B's coil map: data -> projections

@@ -27,6 +27,7 @@
 #include <vector>
 
 #include "collapsed.h"
+#include "split_bf16.cuh"
 #include "tc_ptx.cuh"
 
 namespace mpiffl {
@@ -101,20 +102,7 @@ __device__ __forceinline__ void split4_tf32(const float (&v)[4], uint4 &hi, uint
     lo = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
-__device__ __forceinline__ void split8(const float (&v)[8], uint4 &hi, uint4 &lo) {
-    uint32_t h[4], l[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        __nv_bfloat162 h2 = __float22bfloat162_rn(make_float2(v[2 * i], v[2 * i + 1]));
-        const uint32_t hb = *reinterpret_cast<uint32_t *>(&h2);
-        const float h0 = __uint_as_float(hb << 16), h1 = __uint_as_float(hb & 0xFFFF0000u);
-        __nv_bfloat162 l2 = __float22bfloat162_rn(make_float2(v[2 * i] - h0, v[2 * i + 1] - h1));
-        h[i] = hb;
-        l[i] = *reinterpret_cast<uint32_t *>(&l2);
-    }
-    hi = make_uint4(h[0], h[1], h[2], h[3]);
-    lo = make_uint4(l[0], l[1], l[2], l[3]);
-}
+__device__ __forceinline__ void split8(const float (&v)[8], uint4 &hi, uint4 &lo) { split8_bf16(v, hi, lo); }
 
 constexpr int kProdWarps = 8;                     // A producers (and epilogue)
 constexpr int kGemmThreads = (kProdWarps + 2) * 32;  // + MMA issuer + B loader
@@ -807,6 +795,8 @@ void col_init(mpi_ffl_handle *h) {
                 s->oom = true;
                 return;
             }
+            // the rows past the last of a group stay zero when the projector writes A
+            cudaMemset(s->apk[dir][par], 0, std::max<size_t>(bytes, 1024));
         }
         cudaMemcpy(s->rows[par], rows.data(), rows.size() * sizeof(int), cudaMemcpyHostToDevice);
     }
@@ -867,7 +857,8 @@ int col_take_error(mpi_ffl_handle *h) {
 // Splits the A rows of the full line stage once (k_pack_lines, one launch for both
 // trajectories) and points the problems at them: the loader warp then stages A with one
 // bulk copy per half next to B's, and the producer warps only run the epilogue.
-static void pack_full(mpi_ffl_handle *h, int dir, const float *in, GemmArgs *g, cudaStream_t st) {
+static void pack_full(mpi_ffl_handle *h, int dir, const float *in, GemmArgs *g, cudaStream_t st,
+                      bool prepacked = false) {
     ColState *s = cs(h);
     PackLines pl[2] = {};
     for (int par = 0; par < s->n_par; ++par) {
@@ -878,6 +869,7 @@ static void pack_full(mpi_ffl_handle *h, int dir, const float *in, GemmArgs *g, 
         g[par].apk_cbase = 0;
         g[par].apk_cstep = 0;
     }
+    if (prepacked) return;
     const int G = (std::max(g[0].M, s->n_par > 1 ? g[1].M : 0) + 7) / 8;
     const long long work = (long long)G * g[0].nkc * 64;
     const int blocks = (int)std::min<long long>(4 * 152, (work + 255) / 256);
@@ -887,7 +879,21 @@ static void pack_full(mpi_ffl_handle *h, int dir, const float *in, GemmArgs *g, 
 }
 
 // fine -> data (W) or proj -> data (W H), gain per line
-void col_forward(mpi_ffl_handle *h, const float *in, bool full, const float *gain, float *data, cudaStream_t st) {
+bool col_prepack_targets(const mpi_ffl_handle *h, ProjPack *p) {
+    const ColState *s = cs(h);
+    if (!s || !s->ok || s->psf_stale || h->precision == MPI_FFL_PREC_TF32 || h->d.N % kBK != 0) return false;
+    *p = ProjPack{};
+    p->n_par = s->n_par;
+    for (int par = 0; par < s->n_par; ++par) {
+        p->out[par] = s->apk[0][par];
+        p->G[par] = (s->nrows[par] + 7) / 8;
+        p->nrow[par] = s->nrows[par] / h->d.M;
+    }
+    return true;
+}
+
+void col_forward(mpi_ffl_handle *h, const float *in, bool full, const float *gain, float *data, cudaStream_t st,
+                 bool prepacked) {
     ColState *s = cs(h);
     const Dims &d = h->d;
     GemmArgs g[2];
@@ -898,7 +904,7 @@ void col_forward(mpi_ffl_handle *h, const float *in, bool full, const float *gai
         g[par] = make_args(h, in, full ? d.N : d.Ne, full ? d.N : d.Ne, s->rows[par], s->nrows[par], *B[par], data,
                            2 * d.nb, s->rows[par], 2 * d.nb, gain, d.Nz);
     }
-    if (full) pack_full(h, 0, in, g, st);
+    if (full) pack_full(h, 0, in, g, st, prepacked);
     launch_problems(g, B, s->n_par, st);
 }
 

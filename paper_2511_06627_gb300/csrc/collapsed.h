@@ -13,8 +13,13 @@ bool col_init_oom(const mpi_ffl_handle *h);  // col_init failed on a device allo
 void col_mark_psf_stale(mpi_ffl_handle *h);  // the PSF changed: W H must be rebuilt before use
 bool col_psf_stale(const mpi_ffl_handle *h);
 int col_take_error(mpi_ffl_handle *h);   // 1 if a GEMM gave up on a bounded wait (clears it)
-// full = false: fine -> data with W; full = true: proj -> data with W H (per-line gain)
-void col_forward(mpi_ffl_handle *h, const float *in, bool full, const float *gain, float *data, cudaStream_t st);
+// full = false: fine -> data with W; full = true: proj -> data with W H (per-line gain).
+// prepacked: the projector already wrote the full stage's A operand (col_prepack_targets).
+void col_forward(mpi_ffl_handle *h, const float *in, bool full, const float *gain, float *data, cudaStream_t st,
+                 bool prepacked = false);
+// Where the projector may write the forward full stage's A operand (bf16 hi + lo), or
+// false when that stage does not take it (tf32 split, N not a multiple of 64 bins).
+bool col_prepack_targets(const mpi_ffl_handle *h, ProjPack *p);
 void col_adjoint(mpi_ffl_handle *h, const float *data, bool full, const float *gain, float *out, cudaStream_t st);
 
 // Batched full-GEMM line stages (continuous batching): fill host staging arrays of

@@ -309,8 +309,20 @@ void launch_transpose_xy(const float *vol, float *volT, int N, int Nz, cudaStrea
 bool project_il_ok(int N);
 size_t il_len(int N, int Nz);
 void launch_interleave(const float *vol, float *volI, float *volTI, int N, int Nz, cudaStream_t st);
+// The forward line-GEMM's A operand written by the projector itself (bf16 hi + lo, the
+// canonical 1 KB blocks [K chunk][hi, lo][group of 8 rows] per trajectory parity), when
+// out[0] is not NULL: rows of parity p are the lines (m, z) with z = p mod n_par, in
+// angle-major order, G[p] groups of 8 rows each, nrow[p] rows per angle. proj may then
+// be NULL (the projections are not stored).
+struct ProjPack {
+    uint8_t *out[2];
+    int G[2];
+    int nrow[2];
+    int n_par;
+};
+
 void launch_project_il(const float *volI, const float *volTI, const AngleParam *ang, const int *agroups,
-                       int n_agroups, float *proj, int N, int Nz, cudaStream_t st, int *err, uint32_t inject = 0);
+                       int n_agroups, float *proj, int N, int Nz, cudaStream_t st, int *err, uint32_t inject = 0, ProjPack pack = ProjPack{});
 void launch_project(const float *vol, const float *volT, const AngleParam *ang, const int *agroups,
                     int n_agroups, float *proj, int N, int Nz, cudaStream_t st, int *err);
 constexpr int kProjAnglesPerBlock = 2;  // angle slots per projector block (k_projector.cu)

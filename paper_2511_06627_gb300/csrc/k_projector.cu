@@ -8,6 +8,7 @@
 #include <algorithm>
 
 #include "internal.h"
+#include "split_bf16.cuh"
 #include "tc_ptx.cuh"
 
 namespace mpiffl {
@@ -408,7 +409,7 @@ __global__ void __launch_bounds__(1024 + 32) k_project_il(const float *__restric
                                                           const AngleParam *__restrict__ ang,
                                                           const int *__restrict__ agroups, float *__restrict__ proj,
                                                           int N, int Nz, int rays_per_angle, int *err,
-                                                          uint32_t inject) {
+                                                          uint32_t inject, ProjPack pack) {
     extern __shared__ __align__(128) float psm[];  // kPStages x LDC positions x kZc
     uint64_t *bars = reinterpret_cast<uint64_t *>(psm + kPStages * LDC * kZc);  // full[K], empty[K]
     const int bx = blockIdx.x, zb = blockIdx.y;
@@ -477,7 +478,8 @@ __global__ void __launch_bounds__(1024 + 32) k_project_il(const float *__restric
     bool good = true;
     for (int s = 0; s < N; ++s, fs += ap.fx_b) {
         const int k = s % kPStages;
-        if (!ptx::mbar_wait_bounded(&bars[k], (s / kPStages) & 1, 1u << 24)) {
+        // the warp gives up as one, so that its later votes and shuffles see all lanes
+        if (!__all_sync(0xffffffffu, ptx::mbar_wait_bounded(&bars[k], (s / kPStages) & 1, 1u << 24))) {
             good = false;
             break;
         }
@@ -508,37 +510,77 @@ __global__ void __launch_bounds__(1024 + 32) k_project_il(const float *__restric
         if ((tid & 31) == 0) atomicExch(err, 1);
         return;
     }
-    if (active) {
+#pragma unroll
+    for (int zz = 0; zz < kZc; ++zz) acc[zz] *= ap.scale;
+    if (active && proj) {
 #pragma unroll
         for (int zz = 0; zz < kZc; ++zz)
-            if (zz < nz) proj[((size_t)m * Nz + z0 + zz) * N + i] = acc[zz] * ap.scale;
+            if (zz < nz) proj[((size_t)m * Nz + z0 + zz) * N + i] = acc[zz];
+    }
+    if (pack.out[0]) {
+        // The eight lanes of rays 8u..8u+7 hold 8 slices each; a butterfly of shuffles
+        // transposes the 8 x 8 block, so that lane 8u + v holds slice v of those rays:
+        // eight consecutive K values of line (m, z0 + v), one 16-byte unit of the GEMM's
+        // A rows, split to bf16 hi and lo exactly as the packing pass splits them.
+        const int lane = tid & 31, v = lane & 7;
+        float a[kZc];
+#pragma unroll
+        for (int zz = 0; zz < kZc; ++zz) a[zz] = acc[zz];
+#pragma unroll
+        for (int stage = 0; stage < 3; ++stage) {
+            const int sh = 4 >> stage;
+            const bool hi = (lane & sh) != 0;
+#pragma unroll
+            for (int jj = 0; jj < kZc; ++jj) {
+                if (jj & sh) continue;  // j runs over the lower index of each exchanged pair
+                const float send = hi ? a[jj] : a[jj + sh];
+                const float recv = __shfl_xor_sync(0xffffffffu, send, sh);
+                if (hi) a[jj] = recv;
+                else a[jj + sh] = recv;
+            }
+        }
+        const int i0 = i - v;  // first ray of the unit
+        const int z = z0 + v;
+        if (m >= 0 && i0 < N && v < nz) {
+            const int par = pack.n_par > 1 ? (z & 1) : 0;
+            // selects, not indexing, so that the parameter block stays out of local memory
+            const int r = m * (par ? pack.nrow[1] : pack.nrow[0]) + (pack.n_par > 1 ? z >> 1 : z);
+            const int G = par ? pack.G[1] : pack.G[0];
+            const int c = i0 >> 6, kg = (i0 & 63) >> 3;
+            uint4 hv, lv;
+            split8_bf16(a, hv, lv);
+            uint8_t *base = (par ? pack.out[1] : pack.out[0]) + (size_t)(r >> 3) * 1024u + (uint32_t)kg * 128u + (uint32_t)(r & 7) * 16u;
+            *reinterpret_cast<uint4 *>(base + (size_t)(2 * c) * G * 1024u) = hv;
+            *reinterpret_cast<uint4 *>(base + (size_t)(2 * c + 1) * G * 1024u) = lv;
+        }
     }
 }
 
 template <int LDC>
 void launch_il(dim3 grid, int threads, cudaStream_t st, const float *volI, const float *volTI, const AngleParam *ang,
-               const int *agroups, float *proj, int N, int Nz, int rays, int *err, uint32_t inject) {
+               const int *agroups, float *proj, int N, int Nz, int rays, int *err, uint32_t inject, ProjPack pack) {
     const size_t smem = pipe_smem(LDC);  // kPStages x kZc x LDC floats, as the pipelined variant
     cudaFuncSetAttribute(k_project_il<LDC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     launch_dependent(k_project_il<LDC>, grid, dim3(threads), smem, st, volI, volTI, ang, agroups, proj, N, Nz, rays, err,
-                     inject);
+                     inject, pack);
 }
 
 bool project_il_ok(int N) { return N % 4 == 0 && pipe_ld(N) > 0; }
 
 void launch_project_il(const float *volI, const float *volTI, const AngleParam *ang, const int *agroups,
-                       int n_agroups, float *proj, int N, int Nz, cudaStream_t st, int *err, uint32_t inject) {
+                       int n_agroups, float *proj, int N, int Nz, cudaStream_t st, int *err, uint32_t inject,
+                       ProjPack pack) {
     const int rays = (N + 31) / 32 * 32;
     dim3 grid(n_agroups, (Nz + kZc - 1) / kZc);
     const int threads = rays * kProjAnglesPerBlock + 32;
     switch (pipe_ld(N)) {
-    case 40: launch_il<40>(grid, threads, st, volI, volTI, ang, agroups, proj, N, Nz, rays, err, inject); break;
-    case 72: launch_il<72>(grid, threads, st, volI, volTI, ang, agroups, proj, N, Nz, rays, err, inject); break;
-    case 136: launch_il<136>(grid, threads, st, volI, volTI, ang, agroups, proj, N, Nz, rays, err, inject); break;
-    case 200: launch_il<200>(grid, threads, st, volI, volTI, ang, agroups, proj, N, Nz, rays, err, inject); break;
-    case 264: launch_il<264>(grid, threads, st, volI, volTI, ang, agroups, proj, N, Nz, rays, err, inject); break;
-    case 392: launch_il<392>(grid, threads, st, volI, volTI, ang, agroups, proj, N, Nz, rays, err, inject); break;
-    default: launch_il<520>(grid, threads, st, volI, volTI, ang, agroups, proj, N, Nz, rays, err, inject); break;
+    case 40: launch_il<40>(grid, threads, st, volI, volTI, ang, agroups, proj, N, Nz, rays, err, inject, pack); break;
+    case 72: launch_il<72>(grid, threads, st, volI, volTI, ang, agroups, proj, N, Nz, rays, err, inject, pack); break;
+    case 136: launch_il<136>(grid, threads, st, volI, volTI, ang, agroups, proj, N, Nz, rays, err, inject, pack); break;
+    case 200: launch_il<200>(grid, threads, st, volI, volTI, ang, agroups, proj, N, Nz, rays, err, inject, pack); break;
+    case 264: launch_il<264>(grid, threads, st, volI, volTI, ang, agroups, proj, N, Nz, rays, err, inject, pack); break;
+    case 392: launch_il<392>(grid, threads, st, volI, volTI, ang, agroups, proj, N, Nz, rays, err, inject, pack); break;
+    default: launch_il<520>(grid, threads, st, volI, volTI, ang, agroups, proj, N, Nz, rays, err, inject, pack); break;
     }
 }
 

@@ -24,6 +24,11 @@ CASES = {
                  k_min=2, k_max=6, half_width=4),
     "wide_band": dict(nx=48, nz=4, n_angles=4, S=64, P=128, A=6.0, phi0=0.0, zigzag=1, Q=8, fwhm=3.0,
                       k_min=1, k_max=16, half_width=4, gamma=True),
+    # 64-bin detectors: the full-GEMM forward takes its A operand from the projector
+    "n64_zigzag": dict(nx=64, nz=5, n_angles=3, S=24, P=10, A=3.5, phi0=0.1, zigzag=1, Q=4, fwhm=2.5,
+                       k_min=1, k_max=3, half_width=2),
+    "n64_plain": dict(nx=64, nz=10, n_angles=4, S=32, P=12, A=4.0, phi0=0.25, zigzag=0, Q=4, fwhm=2.0,
+                      k_min=1, k_max=4, half_width=2),
 }
 PATHS = ["staged", "fused", "line_gemm", "full_gemm"]
 
@@ -75,6 +80,21 @@ def test_path_forward_and_adjoint(name, path):
     op.sync_check()
     assert rel_l2(b.cpu().numpy(), to_interleaved(operator.forward(x, st))) < OP_TOL
     assert rel_l2(xa.cpu().numpy(), operator.adjoint(y, st)) < OP_TOL
+
+
+@pytest.mark.parametrize("name", ["n64_zigzag", "n64_plain"])
+def test_projector_packed_operand_matches_the_packing_pass(name):
+    """With N a multiple of 64 the full-GEMM forward splits the projector's sums into the
+    GEMM's bf16 hi + lo operand inside the projector; the projections through the stage
+    entry points (stored, then split by the packing pass) give the same bits."""
+    st, op = _make(name)
+    op.set_path("full_gemm")
+    x = _t(random_volume(st.nz, st.nx, seed=45).astype(np.float32))
+    b = op.forward(x)
+    b_stages = op.line_forward(op.project(x))
+    op.sync_check()
+    assert torch.equal(b, b_stages)
+    assert torch.equal(op.forward(x), b)  # repeatable
 
 
 def test_gemm_paths_take_every_shape():
