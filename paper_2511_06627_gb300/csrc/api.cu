@@ -376,7 +376,7 @@ void release(mpi_ffl_handle *h) {
                     h->t_csr, h->t_tw1, h->t_tw2_ro, h->t_tw2_qr, h->t_dgam, h->t_dgam_unit, h->t_groups, h->w_volT,
                     h->w_proj, h->w_fine, h->w_sig, h->w_data, h->w_vol2, h->w_red, h->w_scal,
                     h->s_xp, h->s_y, h->s_g, h->s_r, h->s_hist, h->s_flags, h->tc_twb, h->t_agroups,
-                    h->t_tnf, h->t_vr, h->w_err, h->t_coil, h->w_projc, h->w_scanvol, h->w_volI, h->w_volTI,
+                    h->t_tnf, h->t_vr, h->w_err, h->t_coil, h->w_projc, h->w_scanvol, h->w_volI,
                     h->t_ra_tile, h->t_ra_j, h->t_ra_w, h->t_twp, h->w_bins};
     for (void *p : ptrs)
         if (p) dev_free(p);
@@ -484,8 +484,8 @@ void ensure_sig(mpi_ffl_handle *h) {
 bool stage_p(mpi_ffl_handle *h, const float *x, float *proj, cudaStream_t st, const ProjPack &pack = ProjPack{}) {
     if (h->w_volI) {  // the interleaved projector: both orientations from one pass over x
         const bool packed = pack.out[0] != nullptr;
-        TIMED(MPI_FFL_K_TRANSPOSE, launch_interleave(x, h->w_volI, h->w_volTI, h->d.N, h->d.Nz, st));
-        TIMED(MPI_FFL_K_PROJECT, launch_project_il(h->w_volI, h->w_volTI, h->t_ang, h->t_agroups, h->n_agroups,
+        TIMED(MPI_FFL_K_TRANSPOSE, launch_interleave(x, h->w_volI, h->d.N, h->d.Nz, st));
+        TIMED(MPI_FFL_K_PROJECT, launch_project_il(h->il_maps, h->t_ang, h->t_agroups, h->n_agroups,
                                                    packed ? nullptr : proj, h->d.N, h->d.Nz, st, h->w_err,
                                                    h->inject_polls, pack));
         check_launch(h, "project");
@@ -914,7 +914,11 @@ extern "C" int mpi_ffl_create(const mpi_ffl_geometry *geom, const mpi_ffl_trajec
         dev_alloc(h, &h->w_volT, d.nvox);
         if (project_il_ok(d.N)) {
             dev_alloc(h, &h->w_volI, il_len(d.N, d.Nz));
-            dev_alloc(h, &h->w_volTI, il_len(d.N, d.Nz));
+            if (!make_il_maps(h->w_volI, d.N, d.Nz, &h->il_maps)) {  // the pipelined projector serves
+                dev_free(h->w_volI);
+                h->w_volI = nullptr;
+                h->bytes -= (int64_t)(il_len(d.N, d.Nz) * sizeof(float));
+            }
         }
         dev_alloc(h, &h->w_proj, d.nproj);
         dev_alloc(h, &h->w_fine, d.nfine);

@@ -245,20 +245,28 @@ __device__ __forceinline__ void gemm_tile(const GemmArgs &g, int mt, int nt, uin
         }
         // ------------------------------------------------------------ epilogue
         // TMEM lane quadrant w % 4 = tile rows 32 (w % 4) .. +31; warps w and w + 4
-        // take alternate 16-column groups.
+        // take alternate 16-column groups. The scaled tile goes through shared memory
+        // (the stages are free once the last MMA is done; rows padded by 16 bytes, so a
+        // quarter warp's 16-byte stores take distinct bank groups) and leaves as one
+        // bulk copy per row, whole sectors instead of a row per lane per store.
         const int row = 32 * (warp & 3) + lane;
         const int gm = mt * kBM + row;
+        // the row's output index and scale are read while the MMAs run
         const int ar = gm < g.M ? __ldg(g.arow + gm) : -1;
+        const int cr = gm < g.M ? __ldg(g.crow + gm) : -1;
+        const float sc = (cr >= 0 && g.rscale) ? __ldg(g.rscale + ar / g.rdiv) : 1.f;
         int done = 0;
         if (ok && lane == 0) done = ptx::mbar_wait_sleep_bounded(&bars[2 * g.stages], 0, kWaitSleep);
         done = __shfl_sync(0xffffffffu, done, 0);
         __syncwarp();
-        if (ok && done) {
+        // the producer warps go on together only if every one of them saw the last MMA
+        if (ptx::bar_and(1, kProdWarps * 32, ok && done)) {
             ptx::tc_fence_after();
-            const int cr = gm < g.M ? __ldg(g.crow + gm) : -1;
-            const float sc = (cr >= 0 && g.rscale) ? __ldg(g.rscale + ar / g.rdiv) : 1.f;
             float *crow = cr >= 0 ? g.C + (size_t)cr * g.ldc : nullptr;
             const bool vecc = (g.ldc % 4 == 0) && ((reinterpret_cast<uintptr_t>(g.C) & 15) == 0);
+            const bool staged = vecc && g.Nc % 4 == 0;  // whole 16-byte units per row
+            float *ct = reinterpret_cast<float *>(sm);
+            const int ldt = g.BN + 4;
             const int nacc = min(g.nacc, g.nkc);
             const uint32_t tl = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
             for (int c0 = 16 * (warp >> 2); c0 < g.BN; c0 += 32) {
@@ -271,7 +279,12 @@ __device__ __forceinline__ void gemm_tile(const GemmArgs &g, int mt, int nt, uin
                     for (int u = 0; u < 16; ++u) v[u] += w[u];
                 }
                 const int n0 = nt * g.BN + c0;
-                if (crow) {
+                if (staged) {
+                    float4 *dst = reinterpret_cast<float4 *>(ct + row * ldt + c0);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        dst[u] = make_float4(sc * v[4 * u], sc * v[4 * u + 1], sc * v[4 * u + 2], sc * v[4 * u + 3]);
+                } else if (crow) {
                     if (vecc && n0 + 16 <= g.Nc) {
 #pragma unroll
                         for (int u = 0; u < 4; ++u)
@@ -284,7 +297,17 @@ __device__ __forceinline__ void gemm_tile(const GemmArgs &g, int mt, int nt, uin
                     }
                 }
             }
-        } else {
+            if (staged) {
+                ptx::fence_proxy_async_smem();  // the tile's generic stores, then the async-proxy reads
+                ptx::named_sync(1, kProdWarps * 32);
+                const int n0 = nt * g.BN, ncols = min(g.BN, g.Nc - n0);
+                if (warp < 4 && crow && ncols > 0) {
+                    ptx::bulk_s2g(crow + n0, ct + row * ldt, 4u * (uint32_t)ncols);
+                    ptx::bulk_commit();
+                    ptx::bulk_wait_all();
+                }
+            }
+        } else if (lane == 0) {
             atomicExch(flag, 1);
         }
     } else if (warp == kProdWarps) {

@@ -2,6 +2,7 @@
 // table layouts and the kernel launchers of each stage.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -21,6 +22,16 @@ namespace mpiffl {
 // near 200 voxels is only good to 1.5e-5, which on rough data shows as 1e-5
 // relative error); its high word is the cell and its low word the fraction. The
 // float fields serve the backprojector's nearest-ray estimate only.
+// The slice-interleaved volume volI[z block][y][x][kZc] as the projector's TMA source:
+// `row` copies one row (fixed y) of box positions, `col` one column (fixed x); both
+// land in shared memory with the 32-byte swizzle (the two 16-byte halves of a
+// position swapped when bit 2 of its staged index is set). A line of N positions
+// takes nbox boxes of `box` positions (box <= 256, a multiple of 4).
+struct IlMaps {
+    CUtensorMap row, col;
+    int nbox = 0, box = 0;
+};
+
 struct AngleParam {
     float inv_c;   // 1/cos (rows) or -1/sin (columns)
     float slope;   // tan (rows) or cot (columns)
@@ -133,7 +144,8 @@ struct mpi_ffl_handle {
     mpiffl::SegGroup *t_groups = nullptr;
     int n_groups = 0;
     int *t_agroups = nullptr;  // projector angle groups: kProjAnglesPerBlock indices, -1 = empty
-    float *w_volI = nullptr, *w_volTI = nullptr;  // slice-interleaved volume copies (il_len floats each)
+    float *w_volI = nullptr;  // slice-interleaved volume (il_len floats)
+    mpiffl::IlMaps il_maps;   // its tensor maps
     int n_agroups = 0;
 
     // workspace
@@ -308,7 +320,9 @@ void launch_transpose_xy(const float *vol, float *volT, int N, int Nz, cudaStrea
 // slice-interleaved volume copies and the projector that reads them (k_projector.cu)
 bool project_il_ok(int N);
 size_t il_len(int N, int Nz);
-void launch_interleave(const float *vol, float *volI, float *volTI, int N, int Nz, cudaStream_t st);
+void launch_interleave(const float *vol, float *volI, int N, int Nz, cudaStream_t st);
+// encodes the tensor maps of volI (false if the driver refuses them)
+bool make_il_maps(const float *volI, int N, int Nz, IlMaps *maps);
 // The forward line-GEMM's A operand written by the projector itself (bf16 hi + lo, the
 // canonical 1 KB blocks [K chunk][hi, lo][group of 8 rows] per trajectory parity), when
 // out[0] is not NULL: rows of parity p are the lines (m, z) with z = p mod n_par, in
@@ -321,7 +335,7 @@ struct ProjPack {
     int n_par;
 };
 
-void launch_project_il(const float *volI, const float *volTI, const AngleParam *ang, const int *agroups,
+void launch_project_il(const IlMaps &maps, const AngleParam *ang, const int *agroups,
                        int n_agroups, float *proj, int N, int Nz, cudaStream_t st, int *err, uint32_t inject = 0, ProjPack pack = ProjPack{});
 void launch_project(const float *vol, const float *volT, const AngleParam *ang, const int *agroups,
                     int n_agroups, float *proj, int N, int Nz, cudaStream_t st, int *err);

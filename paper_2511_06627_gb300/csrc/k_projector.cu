@@ -321,34 +321,35 @@ void launch_project(const float *vol, const float *volT, const AngleParam *ang, 
     k_project<<<grid, threads, smem, st>>>(vol, volT, ang, agroups, proj, N, Nz, rays);
 }
 
-// Interleaved variant (same shapes as the pipelined one). The volume is copied with each
-// line's kZc slices innermost, [z block][s][c][kZc], once for row-marched angles (s = y,
-// c = x) and once transposed for column-marched ones (s = x, c = y). The two 16-byte
-// halves of position c are swapped when bit 2 of c + kPad is set. A march step is then
-// one bulk copy of N kZc floats. A ray reads its two taps for all kZc slices with four
-// 16-byte loads. Eight rays whose positions differ mod 8 read eight distinct 16-byte
-// bank groups: position p puts slices 0-3 in group 2p + ((p >> 2) & 1) mod 8. The sums
-// are those of the pipelined variant, slice by slice.
+// Interleaved variant (same shapes as the pipelined one). The volume is copied once with
+// each line's kZc slices innermost, volI[z block][y][x][kZc]. A march step is one tensor
+// copy of the step's line: a row of volI for row-marched angles, a column (32-byte
+// pieces N rows apart) for column-marched ones. The copy writes shared memory with the
+// 32-byte swizzle, which swaps the two 16-byte halves of staged position p when bit 2
+// of p is set (stage bases are 256-byte aligned). A ray reads its two taps for all kZc
+// slices with four 16-byte loads. Eight rays whose positions differ mod 8 read eight
+// distinct 16-byte bank groups: position p puts slices 0-3 in group
+// 2p + ((p >> 2) & 1) mod 8. The sums are those of the pipelined variant, slice by slice.
 __host__ __device__ __forceinline__ int il_swap(int cs) { return (cs >> 2) & 1; }
 
 size_t il_len(int N, int Nz) { return (size_t)((Nz + kZc - 1) / kZc) * kZc * N * N; }
 
-// volI[zb][y][x][e] and volTI[zb][x][y][e] = vol[kZc zb + e][y][x] (zero past Nz), halves
-// swapped as above. A block of 8 x 32 threads moves a 32 x 32 tile of one slice block:
+// volI[zb][y][x][e] = vol[kZc zb + e][y][x] (zero past Nz). A block of 8 x 32 threads
+// moves a 32 x 32 tile of one slice block:
 // thread (tx, ty) loads 4 consecutive x of row ty of every slice (eight 16-byte loads;
 // N % 4 == 0) and forms each position's two halves in registers. The tile goes through
 // shared memory as 16-byte halves: half h of tile row r, column c sits at 16-byte slot
-// 64 r + 8 (c >> 2) + ((2 (c & 3) + h) ^ sw), sw = (c >> 2) ^ 2 (r & 3). Both copies are
+// 64 r + 8 (c >> 2) + ((2 (c & 3) + h) ^ sw), sw = (c >> 2) ^ 2 (r & 3). The rows are
 // then written from the tile, 32 consecutive 16-byte units of one output row per warp
-// (full 128-byte lines). Every 8-lane phase takes 8 distinct bank groups: the row stores
-// (c = 4 tx + q, tx over the lanes), the row reads (four aligned positions, both halves)
-// and the column reads (four aligned rows of one column, both halves).
+// (full 128-byte lines). Every 8-lane phase takes 8 distinct bank groups: the tile
+// stores (c = 4 tx + q, tx over the lanes) and the row reads (four aligned positions,
+// both halves).
 __device__ __forceinline__ int il_tile_slot(int r, int c, int h) {
     return 64 * r + 8 * (c >> 2) + ((2 * (c & 3) + h) ^ (((c >> 2) ^ (2 * (r & 3))) & 7));
 }
 
-__global__ void __launch_bounds__(256) k_interleave(const float *__restrict__ vol, float *__restrict__ volI,
-                                                    float *__restrict__ volTI, int N, int Nz) {
+__global__ void __launch_bounds__(256) k_interleave(const float *__restrict__ vol, float *__restrict__ volI, int N,
+                                                    int Nz) {
     __shared__ float4 tile[32 * 64];  // 32 rows x 32 columns x 2 halves
     const int tx = threadIdx.x, ty = threadIdx.y;  // 8 x 32
     const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 32, zb = blockIdx.z;
@@ -377,36 +378,77 @@ __global__ void __launch_bounds__(256) k_interleave(const float *__restrict__ vo
         tile[il_tile_slot(ty, c, 1)] = make_float4(f4, f5, f6, f7);
     }
     __syncthreads();
-    // thread t writes 16-byte unit j = t mod 64 (position j / 2, stored half j mod 2) of
-    // tile rows (volI) or tile columns (volTI) 4 i + t / 64
+    // thread t writes 16-byte unit j = t mod 64 (position j / 2, half j mod 2) of tile
+    // rows 4 i + t / 64
     const int t = ty * 8 + tx, j = t & 63, c = j >> 1, m = j & 1;
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
         const int r = 4 * i + (t >> 6);
         const int yy = y0 + r, x = x0 + c;  // volI: row yy, position x
         if (yy < N && x < N)
-            reinterpret_cast<float4 *>(volI + (((size_t)zb * N + yy) * N + x) * kZc)[m] =
-                tile[il_tile_slot(r, c, m ^ il_swap(x + kPad))];
-    }
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        const int r = 4 * i + (t >> 6);
-        const int xr = x0 + r, yp = y0 + c;  // volTI: row xr, position yp (tile row c, column r)
-        if (xr < N && yp < N)
-            reinterpret_cast<float4 *>(volTI + (((size_t)zb * N + xr) * N + yp) * kZc)[m] =
-                tile[il_tile_slot(c, r, m ^ il_swap(yp + kPad))];
+            reinterpret_cast<float4 *>(volI + (((size_t)zb * N + yy) * N + x) * kZc)[m] = tile[il_tile_slot(r, c, m)];
     }
 }
 
-void launch_interleave(const float *vol, float *volI, float *volTI, int N, int Nz, cudaStream_t st) {
+void launch_interleave(const float *vol, float *volI, int N, int Nz, cudaStream_t st) {
     dim3 grid((N + 31) / 32, (N + 31) / 32, (Nz + kZc - 1) / kZc), block(8, 32);
-    launch_dependent(k_interleave, grid, block, 0, st, vol, volI, volTI, N, Nz);
+    launch_dependent(k_interleave, grid, block, 0, st, vol, volI, N, Nz);
+}
+
+// Tensor maps of volI as a 4-D array (kZc floats, x, y, z block): boxes of one row
+// (kZc x box x 1 x 1) and of one column (kZc x 1 x box x 1), 32-byte swizzle, zero fill
+// past the volume's edge.
+bool make_il_maps(const float *volI, int N, int Nz, IlMaps *maps) {
+    using Encode = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    static Encode encode = nullptr;
+    if (!encode) {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn) {
+            cudaGetLastError();
+            return false;
+        }
+        encode = reinterpret_cast<Encode>(fn);
+    }
+    const int nbox = (N + 255) / 256;
+    const int box = ((N + nbox - 1) / nbox + 3) / 4 * 4;
+    if (kPad + nbox * box > pipe_ld(N)) return false;  // the boxes' zero fill stays inside the stage
+    const cuuint64_t dims[4] = {(cuuint64_t)kZc, (cuuint64_t)N, (cuuint64_t)N, (cuuint64_t)((Nz + kZc - 1) / kZc)};
+    const cuuint64_t strides[3] = {(cuuint64_t)kZc * 4, (cuuint64_t)kZc * 4 * N, (cuuint64_t)kZc * 4 * N * N};
+    const cuuint32_t elem[4] = {1, 1, 1, 1};
+    const cuuint32_t brow[4] = {(cuuint32_t)kZc, (cuuint32_t)box, 1, 1};
+    const cuuint32_t bcol[4] = {(cuuint32_t)kZc, 1, (cuuint32_t)box, 1};
+    void *base = const_cast<float *>(volI);
+    if (encode(&maps->row, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides, brow, elem,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS ||
+        encode(&maps->col, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides, bcol, elem,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    maps->nbox = nbox;
+    maps->box = box;
+    return true;
+}
+
+// One tensor copy of box positions from volI into shared memory (4-D coordinates:
+// slice 0, x, y, z block), completing its bytes on *bar.
+__device__ __forceinline__ void il_copy(float *dst, const CUtensorMap *map, int x, int y, int zb, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+        "[%6];" ::"r"(ptx::smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(x), "r"(y), "r"(zb), "r"(ptx::smem_u32(bar))
+        : "memory");
 }
 
 template <int LDC>
-__global__ void __launch_bounds__(1024 + 32) k_project_il(const float *__restrict__ volI,
-                                                          const float *__restrict__ volTI,
-                                                          const AngleParam *__restrict__ ang,
+__global__ void __launch_bounds__(1024 + 32) k_project_il(const __grid_constant__ CUtensorMap map_row,
+                                                          const __grid_constant__ CUtensorMap map_col, int nbox,
+                                                          int box, const AngleParam *__restrict__ ang,
                                                           const int *__restrict__ agroups, float *__restrict__ proj,
                                                           int N, int Nz, int rays_per_angle, int *err,
                                                           uint32_t inject, ProjPack pack) {
@@ -418,6 +460,12 @@ __global__ void __launch_bounds__(1024 + 32) k_project_il(const float *__restric
     const int z0 = zb * kZc;
     const int nz = min(kZc, Nz - z0);
     const int tid = threadIdx.x;
+    // the 32-byte swizzle is a function of the shared address: the stages must start on
+    // 256-byte boundaries for it to swap the halves of staged positions as il_swap says
+    if (ptx::smem_u32(psm) & 255u) {
+        if (tid == 0) atomicExch(err, 1);
+        return;
+    }
     // zero the pad positions [0, kPad) and [kPad + N, LDC) of every stage
     const int padp = LDC - N;
     for (int t = tid; t < kPStages * padp * kZc; t += nthreads_c + 32) {
@@ -442,8 +490,9 @@ __global__ void __launch_bounds__(1024 + 32) k_project_il(const float *__restric
     }
     ptx::grid_dep_wait();  // the interleaved volume comes from the previous kernel
     const AngleParam a0 = ang[agroups[bx * kProjAnglesPerBlock]];
-    const float *src = (a0.row_major ? volI : volTI) + (size_t)zb * N * N * kZc;  // one orientation per block
-    const uint32_t step_bytes = (uint32_t)N * kZc * 4u;
+    const bool rows = a0.row_major != 0;  // one orientation per block
+    const CUtensorMap *map = rows ? &map_row : &map_col;
+    const uint32_t step_bytes = (uint32_t)(nbox * box) * kZc * 4u;  // zero fill past N included
     if (tid >= nthreads_c) {
         // ---------------------------------------------------------------- producer
         if (tid == nthreads_c) {
@@ -458,7 +507,11 @@ __global__ void __launch_bounds__(1024 + 32) k_project_il(const float *__restric
                 // changed from run to run)
                 ptx::fence_proxy_async_smem();
                 ptx::mbar_arrive_expect_tx(&bars[k], step_bytes);
-                ptx::bulk_g2s(psm + ((size_t)k * LDC + kPad) * kZc, src + (size_t)s * N * kZc, step_bytes, &bars[k]);
+                for (int b = 0; b < nbox; ++b) {
+                    float *dst = psm + ((size_t)k * LDC + kPad + b * box) * kZc;
+                    if (rows) il_copy(dst, map, b * box, s, zb, &bars[k]);  // row y = s
+                    else il_copy(dst, map, s, b * box, zb, &bars[k]);       // column x = s
+                }
             }
         }
         return;
@@ -557,30 +610,30 @@ __global__ void __launch_bounds__(1024 + 32) k_project_il(const float *__restric
 }
 
 template <int LDC>
-void launch_il(dim3 grid, int threads, cudaStream_t st, const float *volI, const float *volTI, const AngleParam *ang,
+void launch_il(dim3 grid, int threads, cudaStream_t st, const IlMaps &maps, const AngleParam *ang,
                const int *agroups, float *proj, int N, int Nz, int rays, int *err, uint32_t inject, ProjPack pack) {
     const size_t smem = pipe_smem(LDC);  // kPStages x kZc x LDC floats, as the pipelined variant
     cudaFuncSetAttribute(k_project_il<LDC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    launch_dependent(k_project_il<LDC>, grid, dim3(threads), smem, st, volI, volTI, ang, agroups, proj, N, Nz, rays, err,
-                     inject, pack);
+    launch_dependent(k_project_il<LDC>, grid, dim3(threads), smem, st, maps.row, maps.col, maps.nbox, maps.box, ang,
+                     agroups, proj, N, Nz, rays, err, inject, pack);
 }
 
 bool project_il_ok(int N) { return N % 4 == 0 && pipe_ld(N) > 0; }
 
-void launch_project_il(const float *volI, const float *volTI, const AngleParam *ang, const int *agroups,
+void launch_project_il(const IlMaps &maps, const AngleParam *ang, const int *agroups,
                        int n_agroups, float *proj, int N, int Nz, cudaStream_t st, int *err, uint32_t inject,
                        ProjPack pack) {
     const int rays = (N + 31) / 32 * 32;
     dim3 grid(n_agroups, (Nz + kZc - 1) / kZc);
     const int threads = rays * kProjAnglesPerBlock + 32;
     switch (pipe_ld(N)) {
-    case 40: launch_il<40>(grid, threads, st, volI, volTI, ang, agroups, proj, N, Nz, rays, err, inject, pack); break;
-    case 72: launch_il<72>(grid, threads, st, volI, volTI, ang, agroups, proj, N, Nz, rays, err, inject, pack); break;
-    case 136: launch_il<136>(grid, threads, st, volI, volTI, ang, agroups, proj, N, Nz, rays, err, inject, pack); break;
-    case 200: launch_il<200>(grid, threads, st, volI, volTI, ang, agroups, proj, N, Nz, rays, err, inject, pack); break;
-    case 264: launch_il<264>(grid, threads, st, volI, volTI, ang, agroups, proj, N, Nz, rays, err, inject, pack); break;
-    case 392: launch_il<392>(grid, threads, st, volI, volTI, ang, agroups, proj, N, Nz, rays, err, inject, pack); break;
-    default: launch_il<520>(grid, threads, st, volI, volTI, ang, agroups, proj, N, Nz, rays, err, inject, pack); break;
+    case 40: launch_il<40>(grid, threads, st, maps, ang, agroups, proj, N, Nz, rays, err, inject, pack); break;
+    case 72: launch_il<72>(grid, threads, st, maps, ang, agroups, proj, N, Nz, rays, err, inject, pack); break;
+    case 136: launch_il<136>(grid, threads, st, maps, ang, agroups, proj, N, Nz, rays, err, inject, pack); break;
+    case 200: launch_il<200>(grid, threads, st, maps, ang, agroups, proj, N, Nz, rays, err, inject, pack); break;
+    case 264: launch_il<264>(grid, threads, st, maps, ang, agroups, proj, N, Nz, rays, err, inject, pack); break;
+    case 392: launch_il<392>(grid, threads, st, maps, ang, agroups, proj, N, Nz, rays, err, inject, pack); break;
+    default: launch_il<520>(grid, threads, st, maps, ang, agroups, proj, N, Nz, rays, err, inject, pack); break;
     }
 }
 
