@@ -76,11 +76,11 @@ struct GemmArgs {
 
 // The tensor-core accumulation into TMEM is not round-to-nearest FP32, so its error
 // grows with the number of MMAs chained into one accumulator. K chunks are spread
-// over nacc accumulators (as many as fit two blocks per SM into the 512 TMEM
+// over nacc accumulators (as many as fit per_sm blocks per SM into the 512 TMEM
 // columns, at most 4), which the epilogue adds in FP32.
-void set_accumulators(GemmArgs &g) {
+void set_accumulators(GemmArgs &g, int per_sm = 2) {
     g.acc_stride = (g.BN + 31) / 32 * 32;
-    g.nacc = std::max(1, std::min({4, 256 / g.acc_stride, g.nkc}));
+    g.nacc = std::max(1, std::min({4, 512 / per_sm / g.acc_stride, g.nkc}));
     const int cols = g.nacc * g.acc_stride;
     g.tmem_cols = cols <= 32 ? 32 : cols <= 64 ? 64 : cols <= 128 ? 128 : cols <= 256 ? 256 : 512;
 }
@@ -510,6 +510,7 @@ std::vector<uint8_t> pack_b(const std::vector<double> &Bm, int Nv, int Kv, int B
 struct Packed {
     uint8_t *dev = nullptr;
     int BN = 0, ntile = 0, nkc = 0;
+    int per_sm = 2;  // blocks per SM the tiling was chosen for (1: deeper pipeline, all TMEM)
 };
 
 struct ColState {
@@ -591,13 +592,14 @@ bool upload_packed(Packed &p, const std::vector<uint8_t> &v) {
     return cudaMemcpy(p.dev, v.data(), v.size(), cudaMemcpyHostToDevice) == cudaSuccess;
 }
 
-// Pipeline depth: as many stages (2..4) as leave room for two blocks per SM, so that
-// a grid of up to two blocks per SM runs in one wave.
-size_t smem_for(int BN, int &stages) {
+// Pipeline depth: for two blocks per SM, as many stages (2..4) as leave room for both,
+// so that a grid of up to two blocks per SM runs in one wave; for one block per SM, up
+// to 4 stages in the whole shared memory (all K chunks of a 256-deep K in flight).
+size_t smem_for(int BN, int &stages, int per_sm = 2) {
     const size_t stage = 2u * kBM * kBK * 2 + 2u * BN * kBK * 2;
     const size_t two_per_sm = (113u * 1024u - 256u) / stage;
     const size_t cap = (220u * 1024u - 256u) / stage;
-    stages = (int)std::min<size_t>(cap, std::max<size_t>(2, std::min<size_t>(4, two_per_sm)));
+    stages = (int)std::min<size_t>(cap, std::max<size_t>(2, std::min<size_t>(4, per_sm == 1 ? cap : two_per_sm)));
     return stages * stage + 256;
 }
 
@@ -620,8 +622,8 @@ GemmArgs make_args(const mpi_ffl_handle *h, const float *A, int64_t lda, int Ka,
     g.rdiv = rdiv;
     g.prec = h->precision;
     g.tf32 = h->precision == MPI_FFL_PREC_TF32 ? 1 : 0;
-    smem_for(B.BN, g.stages);
-    set_accumulators(g);
+    smem_for(B.BN, g.stages, B.per_sm);
+    set_accumulators(g, B.per_sm);
     g.err = cs(h)->err;
     g.done = nullptr;
     g.inject = h->inject_polls;
@@ -632,7 +634,7 @@ GemmArgs make_args(const mpi_ffl_handle *h, const float *A, int64_t lda, int Ka,
 void launch_problems(const GemmArgs *g, const Packed *const *B, int n, cudaStream_t st) {
     int stages = 0;
     size_t smem = 0;
-    for (int i = 0; i < n; ++i) smem = std::max(smem, smem_for(B[i]->BN, stages));
+    for (int i = 0; i < n; ++i) smem = std::max(smem, smem_for(B[i]->BN, stages, B[i]->per_sm));
     const int mt0 = (g[0].M + kBM - 1) / kBM;
     const bool tf32 = g[0].tf32 != 0;
     if (n == 1) {
@@ -679,8 +681,8 @@ int gemm_problems(const mpi_ffl_handle *h, bool adjoint, const float *in, float 
         g.rdiv = d.Nz;
         g.prec = h->precision;
         g.tf32 = f;
-        smem_for(B.BN, g.stages);
-        set_accumulators(g);
+        smem_for(B.BN, g.stages, B.per_sm);
+        set_accumulators(g, B.per_sm);
         g.err = s->err;
         g.done = done;
         for (int mt = 0; mt < (g.M + kBM - 1) / kBM; ++mt)
@@ -775,28 +777,41 @@ void col_init(mpi_ffl_handle *h) {
         }
         for (int o = 0; o < R; ++o)
             for (int i = 0; i < d.N; ++i) WHt[(size_t)i * R + o] = WH[(size_t)o * d.N + i];
-        auto mk1 = [&](Packed &p, const std::vector<double> &m, int Nv, int Kv, int BN, bool tf) {
+        auto mk1 = [&](Packed &p, const std::vector<double> &m, int Nv, int Kv, int BN, int per_sm, bool tf) {
             p.BN = BN;
+            p.per_sm = per_sm;
             return upload_packed(p, pack_b(m, Nv, Kv, BN, p.ntile, p.nkc, tf));
         };
-        auto mk = [&](Packed (&p)[2][2], const std::vector<double> &m, int Nv, int Kv, int BN) {
-            return mk1(p[0][par], m, Nv, Kv, BN, false) && mk1(p[1][par], m, Nv, Kv, BN, true);
+        auto mk = [&](Packed (&p)[2][2], const std::vector<double> &m, int Nv, int Kv, int BN, int per_sm) {
+            return mk1(p[0][par], m, Nv, Kv, BN, per_sm, false) && mk1(p[1][par], m, Nv, Kv, BN, per_sm, true);
         };
         // N tile: about two blocks per SM over both trajectories' M tiles
         int n_sm = 152, dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
         const int mtiles = std::max(1, d.n_par * ((d.nseg / d.n_par + kBM - 1) / kBM));
-        // N tile: at most two blocks per SM over the m tiles of both trajectories, so a
-        // line stage runs in one wave
-        auto pick_bn = [&](int Nv) {
+        // N tile: one block per SM over the m tiles of both trajectories when tiles of at
+        // most 256 columns fit in one wave that way (then a block keeps all K chunks in
+        // flight and owns the TMEM); else at most two blocks per SM, still one wave
+        auto pick_bn = [&](int Nv, int &per_sm) {
+            auto round = [](int bn) { return std::max(32, std::min(256, (bn + 15) / 16 * 16)); };
+            const int one = n_sm / mtiles;
+            if (one >= 1) {
+                const int bn = round((Nv + one - 1) / one);
+                if ((Nv + bn - 1) / bn * mtiles <= n_sm) {
+                    per_sm = 1;
+                    return bn;
+                }
+            }
+            per_sm = 2;
             const int want_tiles = std::max(1, (2 * n_sm) / mtiles);
-            int bn = (Nv + want_tiles - 1) / want_tiles;
-            bn = std::max(32, std::min(256, (bn + 15) / 16 * 16));
-            return bn;
+            return round((Nv + want_tiles - 1) / want_tiles);
         };
-        if (!mk(s->evf_f, Wr, R, d.Ne, pick_bn(R)) || !mk(s->evf_a, Wt, d.Ne, R, pick_bn(d.Ne)) ||
-            !mk(s->full_f, WH, R, d.N, pick_bn(R)) || !mk(s->full_a, WHt, d.N, R, pick_bn(d.N))) {
+        int ps[4];
+        const int bn_ef = pick_bn(R, ps[0]), bn_ea = pick_bn(d.Ne, ps[1]);
+        const int bn_ff = pick_bn(R, ps[2]), bn_fa = pick_bn(d.N, ps[3]);
+        if (!mk(s->evf_f, Wr, R, d.Ne, bn_ef, ps[0]) || !mk(s->evf_a, Wt, d.Ne, R, bn_ea, ps[1]) ||
+            !mk(s->full_f, WH, R, d.N, bn_ff, ps[2]) || !mk(s->full_a, WHt, d.N, R, bn_fa, ps[3])) {
             s->oom = true;
             return;
         }
@@ -968,8 +983,7 @@ int col_batch_prepare(mpi_ffl_handle *const *hs, const float *const *in, float *
         if (k < 0) return -1;
         for (int i = base_items; i < n_items; ++i) items[i].x += np;
         for (int i = 0; i < k; ++i) {
-            int st = 0;
-            smem = std::max(smem, smem_for(a[np + i].BN, st));
+            smem = std::max(smem, (size_t)a[np + i].stages * (2u * kBM * kBK * 2 + 2u * a[np + i].BN * kBK * 2) + 256);
             tmem_cols = std::max(tmem_cols, a[np + i].tmem_cols);
         }
         np += k;
