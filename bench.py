@@ -273,13 +273,13 @@ SMEM_BYTES = {
     "backproject": lambda d: 8 * d["M"] * d["nvox"],
 }
 
-# DRAM bytes (read + write) per launch from the ncu capture summarised in
-# profiles/projector_il_invivo.md (cold caches, 256^2x128, 36 angles). Reported only
-# for that workload and only while the kernel is the one that was captured.
+# DRAM bytes (read + write) per launch from one ncu capture of each kernel (cold
+# caches, 256^2x128, 36 angles, --set full, one launch). Reported only for that
+# workload and only while the kernel is the one that was captured.
 DRAM_TRAFFIC = {
-    "project": 67_126_528 + 1_161_472,    # reads both interleaved copies of the volume
-    "backproject": 4_732_160 + 1_024,     # reads the projections; the volume it writes stays in L2
-    "transpose": 33_571_072 + 7_517_952,  # interleave pass: most of its writes stay in L2
+    "project": 33_576_448 + 51_456,     # reads the interleaved copy once; its GEMM operand stays in L2
+    "backproject": 4_736_000 + 0,       # reads the projections; the volume it writes stays in L2
+    "transpose": 33_564_672 + 418_048,  # interleave pass: most of its writes stay in L2
 }
 
 
