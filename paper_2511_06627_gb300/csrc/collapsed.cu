@@ -894,7 +894,16 @@ int col_take_error(mpi_ffl_handle *h) {
 
 // Splits the A rows of the full line stage once (k_pack_lines, one launch for both
 // trajectories) and points the problems at them: the loader warp then stages A with one
-// bulk copy per half next to B's, and the producer warps only run the epilogue.
+// bulk copy per half next to B's, and the producer warps only run the epilogue. Worth a
+// launch only when many N tiles would split the same rows: with at most kSplitTiles N
+// tiles the producer warps split A themselves.
+constexpr int kSplitTiles = 4;
+static bool pack_pays(const Packed *const *B, int n) {
+    for (int i = 0; i < n; ++i)
+        if (B[i]->ntile > kSplitTiles) return true;
+    return false;
+}
+
 static void pack_full(mpi_ffl_handle *h, int dir, const float *in, GemmArgs *g, cudaStream_t st,
                       bool prepacked = false) {
     ColState *s = cs(h);
@@ -942,7 +951,7 @@ void col_forward(mpi_ffl_handle *h, const float *in, bool full, const float *gai
         g[par] = make_args(h, in, full ? d.N : d.Ne, full ? d.N : d.Ne, s->rows[par], s->nrows[par], *B[par], data,
                            2 * d.nb, s->rows[par], 2 * d.nb, gain, d.Nz);
     }
-    if (full) pack_full(h, 0, in, g, st, prepacked);
+    if (full && (prepacked || pack_pays(B, s->n_par))) pack_full(h, 0, in, g, st, prepacked);
     launch_problems(g, B, s->n_par, st);
 }
 
@@ -959,7 +968,7 @@ void col_adjoint(mpi_ffl_handle *h, const float *data, bool full, const float *g
         g[par] = make_args(h, data, 2 * d.nb, 2 * d.nb, s->rows[par], s->nrows[par], *B[par], out, nout, s->rows[par],
                            nout, gain, d.Nz);
     }
-    if (full) pack_full(h, 1, data, g, st);
+    if (full && pack_pays(B, s->n_par)) pack_full(h, 1, data, g, st);
     launch_problems(g, B, s->n_par, st);
 }
 

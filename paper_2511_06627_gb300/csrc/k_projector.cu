@@ -166,6 +166,9 @@ __global__ void __launch_bounds__(1024) k_project(const float *__restrict__ vol,
 // immediates, and the sums equal those of the checked form (a zero tap adds nothing).
 constexpr int kPStages = 8;
 constexpr int kPad = 4;
+// the interleaved projector's stages go in groups of kPGroup march steps, one pair of
+// barriers per group (fewer waits and arrivals per step)
+constexpr int kPGroup = 2, kPSlots = kPStages / kPGroup;
 
 template <int LD>
 __device__ __forceinline__ void project_pipe_body(const float *__restrict__ vol, const float *__restrict__ volT,
@@ -453,7 +456,8 @@ __global__ void __launch_bounds__(1024 + 32) k_project_il(const __grid_constant_
                                                           int N, int Nz, int rays_per_angle, int *err,
                                                           uint32_t inject, ProjPack pack) {
     extern __shared__ __align__(128) float psm[];  // kPStages x LDC positions x kZc
-    uint64_t *bars = reinterpret_cast<uint64_t *>(psm + kPStages * LDC * kZc);  // full[K], empty[K]
+    // kPGroup consecutive march steps share one pair of barriers: full[kPSlots], empty[kPSlots]
+    uint64_t *bars = reinterpret_cast<uint64_t *>(psm + kPStages * LDC * kZc);
     const int bx = blockIdx.x, zb = blockIdx.y;
     const int nthreads_c = rays_per_angle * kProjAnglesPerBlock;  // consumers
     const int ncw = nthreads_c / 32;
@@ -474,9 +478,9 @@ __global__ void __launch_bounds__(1024 + 32) k_project_il(const __grid_constant_
         psm[((size_t)stg * LDC + (pp < kPad ? pp : N + pp)) * kZc + e] = 0.f;
     }
     if (tid == 0) {
-        for (int k = 0; k < kPStages; ++k) {
-            ptx::mbar_init(&bars[k], 1);
-            ptx::mbar_init(&bars[kPStages + k], ncw);
+        for (int u = 0; u < kPSlots; ++u) {
+            ptx::mbar_init(&bars[u], 1);
+            ptx::mbar_init(&bars[kPSlots + u], ncw);
         }
         ptx::fence_mbar_init();
     }
@@ -485,7 +489,7 @@ __global__ void __launch_bounds__(1024 + 32) k_project_il(const __grid_constant_
         // failure-detection test hook: before any copy is issued, every thread waits on
         // the first empty barrier, which only the consumers (all waiting here) would
         // complete; the bounded waits run out, the block records a timeout and returns
-        if (!ptx::mbar_wait_bounded(&bars[kPStages], 0, inject) && tid == 0) atomicExch(err, 1);
+        if (!ptx::mbar_wait_bounded(&bars[kPSlots], 0, inject) && tid == 0) atomicExch(err, 1);
         return;
     }
     ptx::grid_dep_wait();  // the interleaved volume comes from the previous kernel
@@ -496,21 +500,26 @@ __global__ void __launch_bounds__(1024 + 32) k_project_il(const __grid_constant_
     if (tid >= nthreads_c) {
         // ---------------------------------------------------------------- producer
         if (tid == nthreads_c) {
-            for (int s = 0; s < N; ++s) {
-                const int k = s % kPStages;
-                if (s >= kPStages && !ptx::mbar_wait_bounded(&bars[kPStages + k], ((s / kPStages) - 1) & 1, 1u << 24)) {
+            for (int s0 = 0; s0 < N; s0 += kPGroup) {
+                const int gi = s0 / kPGroup, u = gi % kPSlots;
+                if (gi >= kPSlots &&
+                    !ptx::mbar_wait_bounded(&bars[kPSlots + u], ((gi / kPSlots) - 1) & 1, 1u << 24)) {
                     atomicExch(err, 1);
                     break;
                 }
-                // generic-proxy reads of the stage, then its async-proxy refill: without
+                // generic-proxy reads of the stages, then their async-proxy refill: without
                 // this fence some consumers read the next step's data (the sums then
                 // changed from run to run)
                 ptx::fence_proxy_async_smem();
-                ptx::mbar_arrive_expect_tx(&bars[k], step_bytes);
-                for (int b = 0; b < nbox; ++b) {
-                    float *dst = psm + ((size_t)k * LDC + kPad + b * box) * kZc;
-                    if (rows) il_copy(dst, map, b * box, s, zb, &bars[k]);  // row y = s
-                    else il_copy(dst, map, s, b * box, zb, &bars[k]);       // column x = s
+                const int ns = min(kPGroup, N - s0);
+                ptx::mbar_arrive_expect_tx(&bars[u], (uint32_t)ns * step_bytes);
+                for (int e = 0; e < ns; ++e) {
+                    const int s = s0 + e, k = u * kPGroup + e;
+                    for (int b = 0; b < nbox; ++b) {
+                        float *dst = psm + ((size_t)k * LDC + kPad + b * box) * kZc;
+                        if (rows) il_copy(dst, map, b * box, s, zb, &bars[u]);  // row y = s
+                        else il_copy(dst, map, s, b * box, zb, &bars[u]);       // column x = s
+                    }
                 }
             }
         }
@@ -529,34 +538,40 @@ __global__ void __launch_bounds__(1024 + 32) k_project_il(const __grid_constant_
 #pragma unroll
     for (int zz = 0; zz < kZc; ++zz) acc[zz] = 0.f;
     bool good = true;
-    for (int s = 0; s < N; ++s, fs += ap.fx_b) {
-        const int k = s % kPStages;
+    for (int s0 = 0; s0 < N; s0 += kPGroup) {
+        const int gi = s0 / kPGroup, u = gi % kPSlots;
         // the warp gives up as one, so that its later votes and shuffles see all lanes
-        if (!__all_sync(0xffffffffu, ptx::mbar_wait_bounded(&bars[k], (s / kPStages) & 1, 1u << 24))) {
+        if (!__all_sync(0xffffffffu, ptx::mbar_wait_bounded(&bars[u], (gi / kPSlots) & 1, 1u << 24))) {
             good = false;
             break;
         }
-        int cell;
-        float t;
-        fx_split(fs, cell, t);
-        // A ray whose left tap is below -1 or above N - 1 has both taps on the zero pads
-        // and adds nothing at this step; a warp all of whose rays are there (oblique rays
-        // near the detector's edges, about a tenth of the warp-steps) skips the loads.
-        if (__any_sync(0xffffffffu, cell >= -1 && cell <= N - 1)) {
-            const int cs = min(max(cell, -2), N) + kPad;  // staged position of the left tap
-            const float *b0 = psm + ((size_t)k * LDC + cs) * kZc;
-            const int w0 = 4 * il_swap(cs), w1 = 4 * il_swap(cs + 1);
-            const float4 l0 = *reinterpret_cast<const float4 *>(b0 + w0);
-            const float4 l1 = *reinterpret_cast<const float4 *>(b0 + 4 - w0);
-            const float4 r0 = *reinterpret_cast<const float4 *>(b0 + kZc + w1);
-            const float4 r1 = *reinterpret_cast<const float4 *>(b0 + kZc + 4 - w1);
-            const float v0[kZc] = {l0.x, l0.y, l0.z, l0.w, l1.x, l1.y, l1.z, l1.w};
-            const float v1[kZc] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
 #pragma unroll
-            for (int zz = 0; zz < kZc; ++zz) acc[zz] = fmaf(1.f - t, v0[zz], fmaf(t, v1[zz], acc[zz]));
+        for (int e = 0; e < kPGroup; ++e) {
+            if (s0 + e >= N) break;  // uniform over the block
+            const int k = u * kPGroup + e;
+            int cell;
+            float t;
+            fx_split(fs, cell, t);
+            fs += ap.fx_b;
+            // A ray whose left tap is below -1 or above N - 1 has both taps on the zero pads
+            // and adds nothing at this step; a warp all of whose rays are there (oblique
+            // rays near the detector's edges, about a tenth of the warp-steps) skips the loads.
+            if (__any_sync(0xffffffffu, cell >= -1 && cell <= N - 1)) {
+                const int cs = min(max(cell, -2), N) + kPad;  // staged position of the left tap
+                const float *b0 = psm + ((size_t)k * LDC + cs) * kZc;
+                const int w0 = 4 * il_swap(cs), w1 = 4 * il_swap(cs + 1);
+                const float4 l0 = *reinterpret_cast<const float4 *>(b0 + w0);
+                const float4 l1 = *reinterpret_cast<const float4 *>(b0 + 4 - w0);
+                const float4 r0 = *reinterpret_cast<const float4 *>(b0 + kZc + w1);
+                const float4 r1 = *reinterpret_cast<const float4 *>(b0 + kZc + 4 - w1);
+                const float v0[kZc] = {l0.x, l0.y, l0.z, l0.w, l1.x, l1.y, l1.z, l1.w};
+                const float v1[kZc] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+#pragma unroll
+                for (int zz = 0; zz < kZc; ++zz) acc[zz] = fmaf(1.f - t, v0[zz], fmaf(t, v1[zz], acc[zz]));
+            }
         }
         __syncwarp();
-        if ((tid & 31) == 0) ptx::mbar_arrive(&bars[kPStages + k]);
+        if ((tid & 31) == 0) ptx::mbar_arrive(&bars[kPSlots + u]);
     }
     ptx::grid_dep_launch();
     if (!good) {
