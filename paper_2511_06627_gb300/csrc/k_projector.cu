@@ -164,11 +164,11 @@ __global__ void __launch_bounds__(1024) k_project(const float *__restrict__ vol,
 // LD >= N + 8, a compile-time constant), so a tap index clamped to [-2, N] reads a
 // zero outside the grid: the taps need no range checks, the slice offsets are
 // immediates, and the sums equal those of the checked form (a zero tap adds nothing).
-constexpr int kPStages = 8;
+constexpr int kPStages = 12;
 constexpr int kPad = 4;
 // the interleaved projector's stages go in groups of kPGroup march steps, one pair of
 // barriers per group (fewer waits and arrivals per step)
-constexpr int kPGroup = 2, kPSlots = kPStages / kPGroup;
+constexpr int kPGroup = 4, kPSlots = kPStages / kPGroup;
 
 template <int LD>
 __device__ __forceinline__ void project_pipe_body(const float *__restrict__ vol, const float *__restrict__ volT,
