@@ -673,15 +673,29 @@ constexpr int kBpRow = 20;
 static_assert(kBpRow >= kBpZ && kBpRow % 4 == 0 && (kBpRow / 4) % 2 == 1, "row of 16-byte groups, odd count");
 static_assert(kBpChunk * kBpSeg <= kBpTX * kBpTY, "one staging thread per (angle, ray) of a chunk");
 
+// What the gather loop reads per angle (one 16-byte load): the ray spacing fx_d, the
+// nearest-ray estimate's 1/inv_c, and the window's first ray ilo with the orientation
+// in bit 0 (2 ilo + row_major).
+struct __align__(16) BpAngle {
+    long long fx_d;
+    float inv_c_rcp;
+    int ilo_rm;
+};
+// Per angle and march step s = (row-major ? y_lo : x_lo) + ds of the tile (one 16-byte
+// load): the step's Q32.32 base position fx_a + s fx_b, and slope (s - c) + c of the
+// nearest-ray estimate, the same operations the thread would do for its own step.
+struct __align__(16) BpStep {
+    long long gs;
+    float bs;
+    float pad_;
+};
+
 struct __align__(16) BpShared {
     float seg[kBpChunk][kBpSeg][kBpRow];
     AngleParam ang[kBpChunk];
     int ilo[kBpChunk];
-    // per angle and march step s = (row-major ? y_lo : x_lo) + ds of the tile: the
-    // step's Q32.32 base position fx_a + s fx_b, and slope (s - c) + c of the nearest-ray
-    // estimate, the same operations the thread would do for its own step
-    long long gs[kBpChunk][kBpTX];
-    float bs[kBpChunk][kBpTX];
+    BpAngle pa[kBpChunk];
+    BpStep st[kBpChunk][kBpTX];
 };
 static_assert(kBpTX >= kBpTY, "the per-step tables hold the tile's longer side");
 
@@ -703,6 +717,10 @@ __device__ __forceinline__ void backproject_body(const float *__restrict__ proj,
     const int ylo = by * kBpTY, yhi = min(ylo + kBpTY, N) - 1;
     // threads past the grid edge follow the loop on the edge voxel and store nothing
     const int ix = min(x, N - 1), iy = min(y, N - 1);
+    // the voxel's march step within the tile and its index along the step's line, for
+    // row-marched (R) and column-marched (C) angles
+    const int dsR = iy - ylo, dsC = ix - xlo;
+    const float fqR = (float)ix, fqC = (float)iy;
     float acc[kBpZ];
 #pragma unroll
     for (int zz = 0; zz < kBpZ; ++zz) acc[zz] = 0.f;
@@ -717,6 +735,7 @@ __device__ __forceinline__ void backproject_body(const float *__restrict__ proj,
             const int lo = min(min(nearest_ray(a, s0, q0, c), nearest_ray(a, s0, q1, c)),
                                min(nearest_ray(a, s1, q0, c), nearest_ray(a, s1, q1, c)));
             S.ilo[tid] = lo - 1;
+            S.pa[tid] = BpAngle{a.fx_d, a.inv_c_rcp, 2 * (lo - 1) + (a.row_major ? 1 : 0)};
         }
         __syncthreads();
         // thread (a, j) stages ray ilo[a] + j of angle m0 + a: its kBpZ slices, read with
@@ -739,33 +758,36 @@ __device__ __forceinline__ void backproject_body(const float *__restrict__ proj,
             const int a = t / kBpTX, ds = t - a * kBpTX;
             const AngleParam A = S.ang[a];
             const int s = (A.row_major ? ylo : xlo) + ds;
-            S.gs[a][ds] = A.fx_a + (long long)s * A.fx_b;
-            S.bs[a][ds] = fmaf(A.slope, (float)s - c, c);
+            S.st[a][ds] = BpStep{A.fx_a + (long long)s * A.fx_b, fmaf(A.slope, (float)s - c, c), 0.f};
         }
         __syncthreads();
         for (int a = 0; a < na; ++a) {
-            const bool rm = S.ang[a].row_major != 0;
-            const int ds = rm ? iy - ylo : ix - xlo;  // march step holding this voxel, within the tile
-            const int q = rm ? ix : iy;              // its index along the step's line
-            const long long fxd = S.ang[a].fx_d;
+            const BpAngle an = S.pa[a];
+            const bool rm = (an.ilo_rm & 1) != 0;
+            const int ds = rm ? dsR : dsC;  // march step holding this voxel, within the tile
+            const int q = rm ? ix : iy;     // its index along the step's line
+            const long long fxd = an.fx_d;
+            const BpStep sp = S.st[a][ds];
             // nearest ray (estimate): inv_c (i - c) + slope (s - c) + c = q
-            const int i1 = __float2int_rn(fmaf((float)q - S.bs[a][ds], S.ang[a].inv_c_rcp, c));
-            // the forward's fixed-point positions of rays i1-1, i1, i1+1 at step s, and
-            // the weights it gives cell q: 1 - t from a ray in cell q, t from one in q-1
-            long long g = S.gs[a][ds] + (long long)(i1 - 1) * fxd;
-            float w[3];
-#pragma unroll
-            for (int u = 0; u < 3; ++u, g += fxd) {
+            const int i1 = __float2int_rn(fmaf((rm ? fqR : fqC) - sp.bs, an.inv_c_rcp, c));
+            // The forward's fixed-point positions of rays i1-1, i1, i1+1 at step s give cell
+            // q the weight 1 - t from a ray in cell q and t from one in cell q-1; two
+            // consecutive rays carry it. Ray i1-1 does (and the pair is (i1-1, i1)) when it
+            // lies in cell q, or in cell q-1 with a nonzero fraction (t = 0 when the
+            // fraction's top 23 bits are zero); else the pair is (i1, i1+1). Only the two
+            // rays of the pair are evaluated.
+            const long long g0 = sp.gs + (long long)(i1 - 1) * fxd;
+            const int k0 = (int)(g0 >> 32);
+            const bool lo = k0 == q || (k0 == q - 1 && (unsigned)g0 >= 512u);
+            const long long gA = lo ? g0 : g0 + fxd;
+            auto weight = [q](long long g) {
                 int k;
                 float t;
                 fx_split(g, k, t);
-                w[u] = k == q ? 1.f - t : (k == q - 1 ? t : 0.f);
-            }
-            const float w0 = w[0], w1 = w[1], w2 = w[2];
-            // two consecutive rays carry the weight: (i1-1, i1) or (i1, i1+1)
-            const bool lo = w0 != 0.f;
-            const float wA = lo ? w0 : w1, wB = lo ? w1 : w2;
-            const int j = min(max(i1 - (lo ? 1 : 0) - S.ilo[a], 0), kBpSeg - 2);
+                return k == q ? 1.f - t : (k == q - 1 ? t : 0.f);
+            };
+            const float wA = weight(gA), wB = weight(gA + fxd);
+            const int j = min(max(i1 - (lo ? 1 : 0) - (an.ilo_rm >> 1), 0), kBpSeg - 2);
             const float4 *pa = reinterpret_cast<const float4 *>(&S.seg[a][j][0]);
             const float4 *pb = reinterpret_cast<const float4 *>(&S.seg[a][j + 1][0]);
 #pragma unroll
