@@ -253,15 +253,30 @@ void angle_table(mpi_ffl_handle *h) {
                           fx(ctr - inv_c * ctr - slope * ctr), fx(inv_c), fx(slope)};
     }
     upload(h, &h->t_ang, a);
-    // projector blocks hold kProjAnglesPerBlock angles of one orientation
+    // Projector blocks hold kProjAnglesPerBlock (two) angles of one orientation. Angles
+    // differ in cost (oblique rays meet more shared-memory bank conflicts and fewer of
+    // them leave the grid), and the blocks run as one wave, so each block pairs a costly
+    // angle with a cheap one: sorted by the modelled cost, the costliest of an odd count
+    // goes alone, then the costliest remaining with the cheapest. Which block sums an
+    // angle does not change its sums.
+    static_assert(kProjAnglesPerBlock == 2, "the pairing below forms blocks of two angles");
+    std::vector<double> cost(d.M);
+    for (int m = 0; m < d.M; ++m) cost[m] = project_il_cost(a[m], d.N);
     std::vector<int> groups;
     for (int orient = 1; orient >= 0; --orient) {
         std::vector<int> ms;
         for (int m = 0; m < d.M; ++m)
             if (a[m].row_major == orient) ms.push_back(m);
-        for (size_t k = 0; k < ms.size(); k += kProjAnglesPerBlock)
-            for (int u = 0; u < kProjAnglesPerBlock; ++u)
-                groups.push_back(k + u < ms.size() ? ms[k + u] : -1);
+        std::stable_sort(ms.begin(), ms.end(), [&](int x, int y) { return cost[x] < cost[y]; });
+        size_t lo = 0, hi = ms.size();
+        if (ms.size() % 2) {
+            groups.push_back(ms[--hi]);
+            groups.push_back(-1);
+        }
+        while (lo < hi) {
+            groups.push_back(ms[--hi]);
+            groups.push_back(ms[lo++]);
+        }
     }
     h->n_agroups = (int)(groups.size() / kProjAnglesPerBlock);
     upload(h, &h->t_agroups, groups);

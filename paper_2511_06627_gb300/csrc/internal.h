@@ -319,6 +319,7 @@ cudaError_t dev_free(void *p);
 void launch_transpose_xy(const float *vol, float *volT, int N, int Nz, cudaStream_t st);
 // slice-interleaved volume copies and the projector that reads them (k_projector.cu)
 bool project_il_ok(int N);
+double project_il_cost(const AngleParam &a, int N);
 size_t il_len(int N, int Nz);
 void launch_interleave(const float *vol, float *volI, int N, int Nz, cudaStream_t st);
 // encodes the tensor maps of volI (false if the driver refuses them)

@@ -335,6 +335,46 @@ void launch_project(const float *vol, const float *volT, const AngleParam *ang, 
 // 2p + ((p >> 2) & 1) mod 8. The sums are those of the pipelined variant, slice by slice.
 __host__ __device__ __forceinline__ int il_swap(int cs) { return (cs >> 2) & 1; }
 
+// Shared-memory wavefronts one angle costs the interleaved projector for one slice
+// block: per active warp-step, its four 16-byte tap loads, each quarter warp taking one
+// wavefront per distinct 16-byte address in its most used bank group (a model that
+// matches the measured bank conflicts), over every eighth-or-so march step (32 of
+// them). The host uses it to give the projector blocks equal work.
+double project_il_cost(const AngleParam &a, int N) {
+    const int rays = (N + 31) / 32 * 32;
+    const int stride = std::max(1, N / 32);
+    double total = 0.0;
+    int cs[32];
+    for (int s = stride / 2; s < N; s += stride) {
+        for (int w = 0; w < rays; w += 32) {
+            bool any = false;
+            for (int l = 0; l < 32; ++l) {
+                const long long f = a.fx_a + (long long)(w + l) * a.fx_d + (long long)s * a.fx_b;
+                const int cell = (int)(f >> 32);
+                any |= cell >= -1 && cell <= N - 1;
+                cs[l] = std::min(std::max(cell, -2), N) + kPad;
+            }
+            if (!any) continue;
+            for (int ld = 0; ld < 4; ++ld) {
+                const int dp = ld >> 1, h = ld & 1;
+                for (int q = 0; q < 4; ++q) {
+                    int addr[8], per_group[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+                    int worst = 0;
+                    for (int j = 0; j < 8; ++j) {
+                        const int p = cs[8 * q + j] + dp;
+                        addr[j] = 2 * p + (h ^ il_swap(p));
+                        bool seen = false;
+                        for (int k = 0; k < j; ++k) seen |= addr[k] == addr[j];
+                        if (!seen) worst = std::max(worst, ++per_group[addr[j] & 7]);
+                    }
+                    total += worst;
+                }
+            }
+        }
+    }
+    return total;
+}
+
 size_t il_len(int N, int Nz) { return (size_t)((Nz + kZc - 1) / kZc) * kZc * N * N; }
 
 // volI[zb][y][x][e] = vol[kZc zb + e][y][x] (zero past Nz). A block of 8 x 32 threads
