@@ -257,8 +257,8 @@ ALGO_BYTES = {
     "dft_adj": lambda d: 4 * (d["nsig"] + d["ndata"]),
     "tc_fwd": lambda d: 4 * (d["nfine"] + d["ndata"]),
     "tc_adj": lambda d: 4 * (d["nfine"] + d["ndata"]),
-    # the slice-interleaving pass: reads the volume, writes its two interleaved copies
-    "transpose": lambda d: 12 * d["nvox"],
+    # the slice-interleaving pass: reads the volume, writes its interleaved copy
+    "transpose": lambda d: 8 * d["nvox"],
     # the full-GEMM path applies W H to projections, the line-GEMM path W to fine rows
     "gemm_fwd": lambda d: 4 * ((d["nproj"] if d["path"].startswith("full_gemm") else d["nfine"]) + d["ndata"]),
     "gemm_adj": lambda d: 4 * ((d["nproj"] if d["path"].startswith("full_gemm") else d["nfine"]) + d["ndata"]),
