@@ -152,58 +152,47 @@ void launch_psf_adj(const float *fine, const float *htab, float *proj, const Dim
 
 // ----------------------------------------------------------------------------- E V B
 
-__global__ void __launch_bounds__(256) k_resample_fwd(const float *__restrict__ fine,
-                                                      const TrajEntry *__restrict__ traj,
-                                                      const float *__restrict__ gain,
-                                                      const SegGroup *__restrict__ groups,
-                                                      float *__restrict__ sig, Dims d) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= d.L) return;
-    const SegGroup g = groups[blockIdx.y];
-    const TrajEntry te = traj[(size_t)g.parity * d.L + j];
-    const float gm = gain[g.m];
-    for (int l = 0; l < g.count; ++l) {
-        const int seg = g.m * d.Nz + g.z0 + l * g.zstride;
-        const float *row = fine + (size_t)seg * d.Ne;
-        const float v = fmaf(te.w0, __ldg(row + te.n), te.w1 * __ldg(row + te.n + 1));
-        sig[(size_t)seg * d.L + j] = gm * v;
-    }
-}
-
-// Four consecutive samples per thread (L % 4 == 0, 16-byte aligned signal): the same
-// products as k_resample_fwd, stored with one 16-byte store per line.
+// Four samples per thread, each of the group's lines: the signal s = g_m v_j lerp of the
+// fine row at the FFL position (one product per tap, the same for every line).
 __global__ void __launch_bounds__(256) k_resample_fwd4(const float *__restrict__ fine,
                                                        const TrajEntry *__restrict__ traj,
                                                        const float *__restrict__ gain,
                                                        const SegGroup *__restrict__ groups,
                                                        float *__restrict__ sig, Dims d) {
-    const int j0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
-    if (j0 >= d.L) return;
+    // A warp takes 128 consecutive samples, lane l the samples l, l + 32, l + 64, l + 96:
+    // the lanes of one gather read neighbouring fine cells (a few sectors per load,
+    // where four consecutive samples per lane spread a load over a sector per lane),
+    // and each store is one 128-byte line of the signal, stored with the streaming hint
+    // (written once, read once by the band DFT).
+    const int lane = threadIdx.x & 31;
+    const int jw = 4 * (blockIdx.x * blockDim.x + (threadIdx.x & ~31));
     const SegGroup g = groups[blockIdx.y];
     TrajEntry te[4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) te[u] = traj[(size_t)g.parity * d.L + j0 + u];
+    for (int u = 0; u < 4; ++u) {
+        const int j = jw + lane + 32 * u;
+        te[u] = j < d.L ? traj[(size_t)g.parity * d.L + j] : TrajEntry{0, 0.f, 0.f};
+    }
     const float gm = gain[g.m];
-    for (int l = 0; l < g.count; ++l) {
+#pragma unroll
+    for (int l = 0; l < kGroup; ++l) {
+        if (l >= g.count) break;
         const int seg = g.m * d.Nz + g.z0 + l * g.zstride;
         const float *row = fine + (size_t)seg * d.Ne;
-        float v[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) v[u] = gm * fmaf(te[u].w0, __ldg(row + te[u].n), te[u].w1 * __ldg(row + te[u].n + 1));
-        *reinterpret_cast<float4 *>(sig + (size_t)seg * d.L + j0) = make_float4(v[0], v[1], v[2], v[3]);
+        for (int u = 0; u < 4; ++u) {
+            const int j = jw + lane + 32 * u;
+            const float v = gm * fmaf(te[u].w0, __ldg(row + te[u].n), te[u].w1 * __ldg(row + te[u].n + 1));
+            if (j < d.L) __stcs(sig + (size_t)seg * d.L + j, v);
+        }
     }
 }
 
 void launch_resample_fwd(const float *fine, const TrajEntry *traj, const float *gain,
                          const SegGroup *groups, int n_groups, float *sig, const Dims &d,
                          cudaStream_t st) {
-    if (d.L % 4 == 0 && (reinterpret_cast<uintptr_t>(sig) & 15) == 0) {
-        dim3 grid((d.L / 4 + 255) / 256, n_groups);
-        k_resample_fwd4<<<grid, 256, 0, st>>>(fine, traj, gain, groups, sig, d);
-        return;
-    }
-    dim3 grid((d.L + 255) / 256, n_groups);
-    k_resample_fwd<<<grid, 256, 0, st>>>(fine, traj, gain, groups, sig, d);
+    dim3 grid((d.L + 1023) / 1024, n_groups);
+    k_resample_fwd4<<<grid, 256, 0, st>>>(fine, traj, gain, groups, sig, d);
 }
 
 __global__ void __launch_bounds__(128) k_resample_adj(const float *__restrict__ sig,
@@ -695,7 +684,7 @@ __global__ void __launch_bounds__(32 * kDfWarps) k_dft_adj_stream(const float *_
             for (int k = 1; k <= HW; ++k) acc = fmaf(B[i][k], t[k].y, acc);
             v[i] = acc;
         }
-        out[(size_t)p * q4] = make_float4(v[0], v[1], v[2], v[3]);
+        __stcs(out + (size_t)p * q4, make_float4(v[0], v[1], v[2], v[3]));  // written once, read once
 #pragma unroll
         for (int k = 1; k <= HW; ++k) {
             idx[k] += k;
