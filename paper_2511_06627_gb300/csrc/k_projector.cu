@@ -566,8 +566,9 @@ __global__ void __launch_bounds__(1024 + 32) k_project_il(const __grid_constant_
         return;
     }
     // -------------------------------------------------------------------- consumers
-    // Threads of an inactive slot or beyond the last ray run the loop on clamped,
-    // in-bounds taps and store nothing; slices past nz hold zeros, never stored.
+    // The warps of an inactive slot (a block with one angle) only wait and arrive.
+    // Threads beyond the last ray run the loop on clamped, in-bounds taps and store
+    // nothing; slices past nz hold zeros, never stored.
     const int slot = tid / rays_per_angle;
     const int i = tid % rays_per_angle;
     const int m = agroups[bx * kProjAnglesPerBlock + slot];
@@ -596,7 +597,7 @@ __global__ void __launch_bounds__(1024 + 32) k_project_il(const __grid_constant_
             // A ray whose left tap is below -1 or above N - 1 has both taps on the zero pads
             // and adds nothing at this step; a warp all of whose rays are there (oblique
             // rays near the detector's edges, about a tenth of the warp-steps) skips the loads.
-            if (__any_sync(0xffffffffu, cell >= -1 && cell <= N - 1)) {
+            if (m >= 0 && __any_sync(0xffffffffu, cell >= -1 && cell <= N - 1)) {  // m: uniform per warp
                 const int cs = min(max(cell, -2), N) + kPad;  // staged position of the left tap
                 const float *b0 = psm + ((size_t)k * LDC + cs) * kZc;
                 const int w0 = 4 * il_swap(cs), w1 = 4 * il_swap(cs + 1);
