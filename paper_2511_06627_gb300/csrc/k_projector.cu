@@ -287,8 +287,13 @@ int pipe_ld(int N) {
 
 size_t pipe_smem(int ld) { return sizeof(float) * kPStages * kZc * ld + 16 * kPStages; }
 
+// The pipelined and interleaved projectors run kProjAnglesPerBlock angles of
+// (N + 31) / 32 * 32 rays each plus a producer warp in one block: at most 1024 threads,
+// so N <= 496; wider detectors take the plain projector.
+bool pipe_threads_ok(int N) { return (N + 31) / 32 * 32 * kProjAnglesPerBlock + 32 <= 1024; }
+
 bool pipe_ok(const float *vol, const float *volT, int N) {
-    return N % 4 == 0 && pipe_ld(N) > 0 && (reinterpret_cast<uintptr_t>(vol) & 15) == 0 &&
+    return N % 4 == 0 && pipe_ld(N) > 0 && pipe_threads_ok(N) && (reinterpret_cast<uintptr_t>(vol) & 15) == 0 &&
            (reinterpret_cast<uintptr_t>(volT) & 15) == 0;
 }
 
@@ -675,7 +680,7 @@ void launch_il(dim3 grid, int threads, cudaStream_t st, const IlMaps &maps, cons
                      agroups, proj, N, Nz, rays, err, inject, pack);
 }
 
-bool project_il_ok(int N) { return N % 4 == 0 && pipe_ld(N) > 0; }
+bool project_il_ok(int N) { return N % 4 == 0 && pipe_ld(N) > 0 && pipe_threads_ok(N); }
 
 void launch_project_il(const IlMaps &maps, const AngleParam *ang, const int *agroups,
                        int n_agroups, float *proj, int N, int Nz, cudaStream_t st, int *err, uint32_t inject,
@@ -965,7 +970,7 @@ void launch_transpose_batch(const TransposeJob *jobs, const int *offs, int n, in
                                                                                                    total);
 }
 
-bool project_batch_ok(int N) { return N % 4 == 0 && pipe_ld(N) > 0; }
+bool project_batch_ok(int N) { return N % 4 == 0 && pipe_ld(N) > 0 && pipe_threads_ok(N); }
 
 template <int LD>
 void launch_pbatch(const ProjectJob *jobs, const int *offs, int n, int total, int threads, int *err,

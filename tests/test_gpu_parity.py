@@ -230,3 +230,26 @@ def test_compression_analysis_matches_the_oracle():
             assert abs(got[a, c] - ref) <= 1e-5 * ref, (K, w, got[a, c], ref)
     # monotone in both the harmonic count and the bandwidth, and at most 1
     assert np.all(np.diff(got, axis=0) >= 0) and np.all(np.diff(got, axis=1) >= 0) and got.max() <= 1.0
+
+
+@pytest.mark.parametrize("n", [300, 320, 512])
+def test_projector_pair_on_wide_detectors(n):
+    """Above 256 bins the interleaved projector stages each march line with two tensor
+    copies (boxes of at most 256 positions, zero fill past the line's end), and N = 300 is
+    not a multiple of the 32 rays of a warp: P and P^T (Sec. 2.2, Eq. (19)) against the
+    oracle, with a 45 deg tie and 90 deg among the angles and a ragged slice block."""
+    from oracle import projection
+    from paper_2511_06627_gb300 import FFLOperator
+
+    nz = 9
+    angles = [0.0, 0.3, math.pi / 4, 1.2, math.pi / 2, 2.5]
+    kw = dict(nx=n, nz=nz, n_angles=len(angles), S=32, P=16, A=4.0, phi0=0.0, zigzag=1, Q=4, fwhm=2.5,
+              k_min=1, k_max=3, half_width=2)
+    op = FFLOperator(**kw, angles=angles)
+    x = random_volume(nz, n, seed=47).astype(np.float32)
+    p = _n(op.project(_t(x)))
+    assert rel_l2(p, projection.project(x.astype(np.float64), angles)) < OP_TOL
+    rng = np.random.default_rng(48)
+    q = rng.standard_normal((len(angles), nz, n)).astype(np.float32)
+    v = _n(op.backproject(_t(q)))
+    assert rel_l2(v, projection.backproject(q.astype(np.float64), angles, n)) < OP_TOL
