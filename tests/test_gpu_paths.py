@@ -29,6 +29,9 @@ CASES = {
                        k_min=1, k_max=3, half_width=2),
     "n64_plain": dict(nx=64, nz=10, n_angles=4, S=32, P=12, A=4.0, phi0=0.25, zigzag=0, Q=4, fwhm=2.0,
                       k_min=1, k_max=4, half_width=2),
+    # the widest detector the library takes (512 bins): the plain projector, 512-row GEMMs
+    "n512": dict(nx=512, nz=3, n_angles=3, S=32, P=16, A=4.0, phi0=0.1, zigzag=1, Q=4, fwhm=2.5,
+                 k_min=1, k_max=3, half_width=2),
 }
 PATHS = ["staged", "fused", "line_gemm", "full_gemm"]
 
