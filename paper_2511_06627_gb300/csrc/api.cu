@@ -682,7 +682,7 @@ void forward_impl(mpi_ffl_handle *h, const float *x, float *b, const float *htab
                   cudaStream_t st) {
     // The full-GEMM stage with the collinear PSF's own taps, no coil map: the projector
     // splits its sums into the GEMM's A operand itself (the packing pass and the
-    // projections' round trip through HBM drop out; the same bf16 hi + lo values).
+    // projections' round trip through HBM drop out; the same hi + lo values).
     ProjPack pack{};
     const bool fold = h->path == MPI_FFL_PATH_FULL_GEMM && h->psf_model != MPI_FFL_PSF_TENSOR && !h->t_coil &&
                       htab == h->t_htab && col_prepack_targets(h, &pack);

@@ -27,7 +27,7 @@
 #include <vector>
 
 #include "collapsed.h"
-#include "split_bf16.cuh"
+#include "split_operands.cuh"
 #include "tc_ptx.cuh"
 
 namespace mpiffl {
@@ -83,23 +83,6 @@ void set_accumulators(GemmArgs &g, int per_sm = 2) {
     g.nacc = std::max(1, std::min({4, 512 / per_sm / g.acc_stride, g.nkc}));
     const int cols = g.nacc * g.acc_stride;
     g.tmem_cols = cols <= 32 ? 32 : cols <= 64 ? 64 : cols <= 128 ? 128 : cols <= 256 ? 256 : 512;
-}
-
-// tf32 hi + lo split of 4 floats (round to nearest, ties away): hi = tf32(v), lo = tf32(v - hi)
-__device__ __forceinline__ uint32_t to_tf32(float v) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
-    return r;
-}
-__device__ __forceinline__ void split4_tf32(const float (&v)[4], uint4 &hi, uint4 &lo) {
-    uint32_t h[4], l[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        h[i] = to_tf32(v[i]);
-        l[i] = to_tf32(v[i] - __uint_as_float(h[i]));
-    }
-    hi = make_uint4(h[0], h[1], h[2], h[3]);
-    lo = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
 __device__ __forceinline__ void split8(const float (&v)[8], uint4 &hi, uint4 &lo) { split8_bf16(v, hi, lo); }
@@ -928,9 +911,11 @@ static void pack_full(mpi_ffl_handle *h, int dir, const float *in, GemmArgs *g, 
 // fine -> data (W) or proj -> data (W H), gain per line
 bool col_prepack_targets(const mpi_ffl_handle *h, ProjPack *p) {
     const ColState *s = cs(h);
-    if (!s || !s->ok || s->psf_stale || h->precision == MPI_FFL_PREC_TF32 || h->d.N % kBK != 0) return false;
+    const bool tf32 = h->precision == MPI_FFL_PREC_TF32;
+    if (!s || !s->ok || s->psf_stale || h->d.N % (tf32 ? kBK / 2 : kBK) != 0) return false;
     *p = ProjPack{};
     p->n_par = s->n_par;
+    p->tf32 = tf32 ? 1 : 0;
     for (int par = 0; par < s->n_par; ++par) {
         p->out[par] = s->apk[0][par];
         p->G[par] = (s->nrows[par] + 7) / 8;

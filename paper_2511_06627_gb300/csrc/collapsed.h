@@ -17,8 +17,9 @@ int col_take_error(mpi_ffl_handle *h);   // 1 if a GEMM gave up on a bounded wai
 // prepacked: the projector already wrote the full stage's A operand (col_prepack_targets).
 void col_forward(mpi_ffl_handle *h, const float *in, bool full, const float *gain, float *data, cudaStream_t st,
                  bool prepacked = false);
-// Where the projector may write the forward full stage's A operand (bf16 hi + lo), or
-// false when that stage does not take it (tf32 split, N not a multiple of 64 bins).
+// Where the projector may write the forward full stage's A operand (bf16 or tf32 hi +
+// lo), or false when that stage does not take it (N not a multiple of the K chunk: 64
+// bins in bf16, 32 in tf32).
 bool col_prepack_targets(const mpi_ffl_handle *h, ProjPack *p);
 void col_adjoint(mpi_ffl_handle *h, const float *data, bool full, const float *gain, float *out, cudaStream_t st);
 

@@ -324,7 +324,7 @@ size_t il_len(int N, int Nz);
 void launch_interleave(const float *vol, float *volI, int N, int Nz, cudaStream_t st);
 // encodes the tensor maps of volI (false if the driver refuses them)
 bool make_il_maps(const float *volI, int N, int Nz, IlMaps *maps);
-// The forward line-GEMM's A operand written by the projector itself (bf16 hi + lo, the
+// The forward line-GEMM's A operand written by the projector itself (bf16 or tf32 hi + lo, the
 // canonical 1 KB blocks [K chunk][hi, lo][group of 8 rows] per trajectory parity), when
 // out[0] is not NULL: rows of parity p are the lines (m, z) with z = p mod n_par, in
 // angle-major order, G[p] groups of 8 rows each, nrow[p] rows per angle. proj may then
@@ -334,6 +334,7 @@ struct ProjPack {
     int G[2];
     int nrow[2];
     int n_par;
+    int tf32;  // 1: tf32 hi + lo (4 K values per 16-byte unit), 0: bf16 (8)
 };
 
 void launch_project_il(const IlMaps &maps, const AngleParam *ang, const int *agroups,

@@ -8,7 +8,7 @@
 #include <algorithm>
 
 #include "internal.h"
-#include "split_bf16.cuh"
+#include "split_operands.cuh"
 #include "tc_ptx.cuh"
 
 namespace mpiffl {
@@ -635,8 +635,9 @@ __global__ void __launch_bounds__(1024 + 32) k_project_il(const __grid_constant_
     if (pack.out[0]) {
         // The eight lanes of rays 8u..8u+7 hold 8 slices each; a butterfly of shuffles
         // transposes the 8 x 8 block, so that lane 8u + v holds slice v of those rays:
-        // eight consecutive K values of line (m, z0 + v), one 16-byte unit of the GEMM's
-        // A rows, split to bf16 hi and lo exactly as the packing pass splits them.
+        // eight consecutive K values of line (m, z0 + v): one 16-byte unit of the GEMM's
+        // A rows in bf16 or two in tf32, split to hi and lo exactly as the packing pass
+        // splits them.
         const int lane = tid & 31, v = lane & 7;
         float a[kZc];
 #pragma unroll
@@ -661,12 +662,23 @@ __global__ void __launch_bounds__(1024 + 32) k_project_il(const __grid_constant_
             // selects, not indexing, so that the parameter block stays out of local memory
             const int r = m * (par ? pack.nrow[1] : pack.nrow[0]) + (pack.n_par > 1 ? z >> 1 : z);
             const int G = par ? pack.G[1] : pack.G[0];
-            const int c = i0 >> 6, kg = (i0 & 63) >> 3;
+            uint8_t *row = (par ? pack.out[1] : pack.out[0]) + (size_t)(r >> 3) * 1024u + (uint32_t)(r & 7) * 16u;
+            auto put = [&](int c, int kg, const uint4 &hv, const uint4 &lv) {
+                uint8_t *base = row + (uint32_t)kg * 128u;
+                *reinterpret_cast<uint4 *>(base + (size_t)(2 * c) * G * 1024u) = hv;
+                *reinterpret_cast<uint4 *>(base + (size_t)(2 * c + 1) * G * 1024u) = lv;
+            };
             uint4 hv, lv;
-            split8_bf16(a, hv, lv);
-            uint8_t *base = (par ? pack.out[1] : pack.out[0]) + (size_t)(r >> 3) * 1024u + (uint32_t)kg * 128u + (uint32_t)(r & 7) * 16u;
-            *reinterpret_cast<uint4 *>(base + (size_t)(2 * c) * G * 1024u) = hv;
-            *reinterpret_cast<uint4 *>(base + (size_t)(2 * c + 1) * G * 1024u) = lv;
+            if (pack.tf32) {  // 32 K values per chunk, two units of four
+                const float f0[4] = {a[0], a[1], a[2], a[3]}, f1[4] = {a[4], a[5], a[6], a[7]};
+                split4_tf32(f0, hv, lv);
+                put(i0 >> 5, (i0 & 31) >> 2, hv, lv);
+                split4_tf32(f1, hv, lv);
+                put(i0 >> 5, ((i0 & 31) >> 2) + 1, hv, lv);
+            } else {  // 64 K values per chunk, one unit of eight
+                split8_bf16(a, hv, lv);
+                put(i0 >> 6, (i0 & 63) >> 3, hv, lv);
+            }
         }
     }
 }

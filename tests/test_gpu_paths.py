@@ -85,13 +85,19 @@ def test_path_forward_and_adjoint(name, path):
     assert rel_l2(xa.cpu().numpy(), operator.adjoint(y, st)) < OP_TOL
 
 
+@pytest.mark.parametrize("tf32", [False, True])
 @pytest.mark.parametrize("name", ["n64_zigzag", "n64_plain"])
-def test_projector_packed_operand_matches_the_packing_pass(name):
-    """With N a multiple of 64 the full-GEMM forward splits the projector's sums into the
-    GEMM's bf16 hi + lo operand inside the projector; the projections through the stage
-    entry points (stored, then split by the packing pass) give the same bits."""
+def test_projector_packed_operand_matches_the_packing_pass(name, tf32):
+    """With N a multiple of the K chunk (64 bins in bf16, 32 in tf32) the full-GEMM
+    forward splits the projector's sums into the GEMM's hi + lo operand inside the
+    projector; the projections through the stage entry points (stored, then split by the
+    GEMM or its packing pass) give the same bits."""
+    from paper_2511_06627_gb300 import PREC_TF32
+
     st, op = _make(name)
     op.set_path("full_gemm")
+    if tf32:
+        op.set_precision(PREC_TF32)
     x = _t(random_volume(st.nz, st.nx, seed=45).astype(np.float32))
     b = op.forward(x)
     b_stages = op.line_forward(op.project(x))
