@@ -228,8 +228,10 @@ __device__ __forceinline__ void project_pipe_body(const float *__restrict__ vol,
         return;
     }
     // -------------------------------------------------------------------- consumers
-    // Threads of an inactive slot or beyond the last ray run the loop on clamped,
-    // in-bounds taps and store nothing; slices past nz hold stale data, never stored.
+    // The warps of an inactive slot (a block with one angle) only wait and arrive, as do
+    // the warps all of whose rays lie off the grid at a step (both taps on the zero pads:
+    // nothing to add). Threads beyond the last ray run the loop on clamped, in-bounds
+    // taps and store nothing; slices past nz hold stale data, never stored.
     const int slot = tid / rays_per_angle;
     const int i = tid % rays_per_angle;
     const int m = agroups[bx * kProjAnglesPerBlock + slot];
@@ -242,17 +244,20 @@ __device__ __forceinline__ void project_pipe_body(const float *__restrict__ vol,
     bool good = true;
     for (int s = 0; s < N; ++s, fs += ap.fx_b) {
         const int k = s % kPStages;
-        if (!ptx::mbar_wait_bounded(&bars[k], (s / kPStages) & 1, 1u << 24)) {
+        // the warp gives up as one, so that its vote below sees all lanes
+        if (!__all_sync(0xffffffffu, ptx::mbar_wait_bounded(&bars[k], (s / kPStages) & 1, 1u << 24))) {
             good = false;
             break;
         }
         int cell;
         float t;
         fx_split(fs, cell, t);
-        const int kk = min(max(cell, -2), N);
-        const float *p = psm + k * kZc * LD + kPad + kk;
+        if (m >= 0 && __any_sync(0xffffffffu, cell >= -1 && cell <= N - 1)) {  // m: uniform per warp
+            const int kk = min(max(cell, -2), N);
+            const float *p = psm + k * kZc * LD + kPad + kk;
 #pragma unroll
-        for (int zz = 0; zz < kZc; ++zz) acc[zz] = fmaf(1.f - t, p[zz * LD], fmaf(t, p[zz * LD + 1], acc[zz]));
+            for (int zz = 0; zz < kZc; ++zz) acc[zz] = fmaf(1.f - t, p[zz * LD], fmaf(t, p[zz * LD + 1], acc[zz]));
+        }
         __syncwarp();
         if ((tid & 31) == 0) ptx::mbar_arrive(&bars[kPStages + k]);
     }
