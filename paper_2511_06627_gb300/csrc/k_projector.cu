@@ -456,18 +456,19 @@ bool make_il_maps(const float *volI, int N, int Nz, IlMaps *maps) {
     using Encode = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-    static Encode encode = nullptr;
-    if (!encode) {
+    // looked up once, thread-safely (handles may be created from several threads)
+    static const Encode encode = []() -> Encode {
         void *fn = nullptr;
         cudaDriverEntryPointQueryResult q{};
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
                 cudaSuccess ||
             q != cudaDriverEntryPointSuccess || !fn) {
             cudaGetLastError();
-            return false;
+            return nullptr;
         }
-        encode = reinterpret_cast<Encode>(fn);
-    }
+        return reinterpret_cast<Encode>(fn);
+    }();
+    if (!encode) return false;
     const int nbox = (N + 255) / 256;
     const int box = ((N + nbox - 1) / nbox + 3) / 4 * 4;
     if (kPad + nbox * box > pipe_ld(N)) return false;  // the boxes' zero fill stays inside the stage
