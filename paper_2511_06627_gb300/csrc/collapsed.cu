@@ -99,7 +99,10 @@ struct AChunk {
 // MODE 0: bf16 operands, 1: tf32, 2: as g.tf32 says (batches that may mix both).
 // One output tile. With tslot_ext NULL the block allocates (and at the end frees) its own
 // TMEM columns; a persistent block passes the slot of columns it holds for all its tiles.
-template <int MODE>
+// PRE: every problem of the launch has A pre-split (g.apk), and the producer warps' split
+// is compiled out (a smaller kernel: the forward's blocks live a few microseconds, and
+// instruction fetch is among their stalls).
+template <int MODE, bool PRE = false>
 __device__ __forceinline__ void gemm_tile(const GemmArgs &g, int mt, int nt, uint8_t *sm, const uint32_t *tslot_ext) {
     const bool tf32 = MODE == 2 ? g.tf32 != 0 : MODE == 1;
     const uint32_t bytesA = kBM * kBK * 2;          // one of hi | lo
@@ -217,14 +220,16 @@ __device__ __forceinline__ void gemm_tile(const GemmArgs &g, int mt, int nt, uin
             return true;
         };
         bool ok = true;
-        AChunk ca, cb;
-        if (!g.apk) load(0, ca);
-        for (int kc = 0; kc < g.nkc && ok && !g.apk; kc += 2) {
-            if (kc + 1 < g.nkc) load(kc + 1, cb);
-            ok = produce(kc, ca);
-            if (!ok || kc + 1 >= g.nkc) break;
-            if (kc + 2 < g.nkc) load(kc + 2, ca);
-            ok = produce(kc + 1, cb);
+        if constexpr (!PRE) {
+            AChunk ca, cb;
+            if (!g.apk) load(0, ca);
+            for (int kc = 0; kc < g.nkc && ok && !g.apk; kc += 2) {
+                if (kc + 1 < g.nkc) load(kc + 1, cb);
+                ok = produce(kc, ca);
+                if (!ok || kc + 1 >= g.nkc) break;
+                if (kc + 2 < g.nkc) load(kc + 2, ca);
+                ok = produce(kc + 1, cb);
+            }
         }
         // ------------------------------------------------------------ epilogue
         // TMEM lane quadrant w % 4 = tile rows 32 (w % 4) .. +31; warps w and w + 4
@@ -369,9 +374,9 @@ __device__ __forceinline__ void gemm_tile(const GemmArgs &g, int mt, int nt, uin
     if (!tslot_ext && warp == 0) ptx::tmem_dealloc(tmem, g.tmem_cols);
 }
 
-template <int MODE>
+template <int MODE, bool PRE = false>
 __device__ __forceinline__ void gemm_body(const GemmArgs &g, int mt, int nt, uint8_t *sm) {
-    gemm_tile<MODE>(g, mt, nt, sm, nullptr);
+    gemm_tile<MODE, PRE>(g, mt, nt, sm, nullptr);
 }
 
 template <int MODE>
@@ -383,12 +388,12 @@ __global__ void __launch_bounds__(kGemmThreads, 2) k_gemm_split(GemmArgs g) {
 // Both trajectories of a line stage in one launch: blocks [0, n0) belong to g0 (m
 // tile b / nt0, n tile b % nt0, so the n tiles of an m tile run side by side and
 // share its A rows in L2), the rest to g1.
-template <int MODE>
+template <int MODE, bool PRE = false>
 __global__ void __launch_bounds__(kGemmThreads, 2) k_gemm_pair(GemmArgs g0, GemmArgs g1, int nt0, int n0, int nt1) {
     extern __shared__ __align__(128) uint8_t sm[];
     const int b = blockIdx.x;
-    if (b < n0) gemm_body<MODE>(g0, b / nt0, b % nt0, sm);
-    else gemm_body<MODE>(g1, (b - n0) / nt1, (b - n0) % nt1, sm);
+    if (b < n0) gemm_body<MODE, PRE>(g0, b / nt0, b % nt0, sm);
+    else gemm_body<MODE, PRE>(g1, (b - n0) / nt1, (b - n0) % nt1, sm);
 }
 
 // One persistent launch for several GEMM problems: items[i] = (problem, m tile, n tile).
@@ -627,12 +632,9 @@ void launch_problems(const GemmArgs *g, const Packed *const *B, int n, cudaStrea
     }
     const int n0 = mt0 * B[0]->ntile;
     const int n1 = (g[1].M + kBM - 1) / kBM * B[1]->ntile;
-    if (tf32)
-        launch_dependent(k_gemm_pair<1>, dim3(n0 + n1), dim3(kGemmThreads), smem, st, g[0], g[1], B[0]->ntile, n0,
-                         B[1]->ntile);
-    else
-        launch_dependent(k_gemm_pair<0>, dim3(n0 + n1), dim3(kGemmThreads), smem, st, g[0], g[1], B[0]->ntile, n0,
-                         B[1]->ntile);
+    const bool pre = g[0].apk && g[1].apk;  // both trajectories' A pre-split
+    auto kern = tf32 ? (pre ? k_gemm_pair<1, true> : k_gemm_pair<1>) : (pre ? k_gemm_pair<0, true> : k_gemm_pair<0>);
+    launch_dependent(kern, dim3(n0 + n1), dim3(kGemmThreads), smem, st, g[0], g[1], B[0]->ntile, n0, B[1]->ntile);
 }
 
 }  // namespace
@@ -827,7 +829,8 @@ void col_init(mpi_ffl_handle *h) {
     }
     cudaMemset(s->err, 0, sizeof(int));
     for (const void *k : {(const void *)k_gemm_split<0>, (const void *)k_gemm_split<1>, (const void *)k_gemm_pair<0>,
-                          (const void *)k_gemm_pair<1>})
+                          (const void *)k_gemm_pair<1>, (const void *)k_gemm_pair<0, true>,
+                          (const void *)k_gemm_pair<1, true>})
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     cudaGetLastError();
     s->ok = true;
@@ -877,15 +880,8 @@ int col_take_error(mpi_ffl_handle *h) {
 
 // Splits the A rows of the full line stage once (k_pack_lines, one launch for both
 // trajectories) and points the problems at them: the loader warp then stages A with one
-// bulk copy per half next to B's, and the producer warps only run the epilogue. Worth a
-// launch only when many N tiles would split the same rows: with at most kSplitTiles N
-// tiles the producer warps split A themselves.
-constexpr int kSplitTiles = 4;
-static bool pack_pays(const Packed *const *B, int n) {
-    for (int i = 0; i < n; ++i)
-        if (B[i]->ntile > kSplitTiles) return true;
-    return false;
-}
+// bulk copy per half next to B's, and the producer warps only run the epilogue (the
+// launch then takes the GEMM without the producers' split, a smaller kernel).
 
 static void pack_full(mpi_ffl_handle *h, int dir, const float *in, GemmArgs *g, cudaStream_t st,
                       bool prepacked = false) {
@@ -936,7 +932,7 @@ void col_forward(mpi_ffl_handle *h, const float *in, bool full, const float *gai
         g[par] = make_args(h, in, full ? d.N : d.Ne, full ? d.N : d.Ne, s->rows[par], s->nrows[par], *B[par], data,
                            2 * d.nb, s->rows[par], 2 * d.nb, gain, d.Nz);
     }
-    if (full && (prepacked || pack_pays(B, s->n_par))) pack_full(h, 0, in, g, st, prepacked);
+    if (full) pack_full(h, 0, in, g, st, prepacked);
     launch_problems(g, B, s->n_par, st);
 }
 
@@ -953,7 +949,7 @@ void col_adjoint(mpi_ffl_handle *h, const float *data, bool full, const float *g
         g[par] = make_args(h, data, 2 * d.nb, 2 * d.nb, s->rows[par], s->nrows[par], *B[par], out, nout, s->rows[par],
                            nout, gain, d.Nz);
     }
-    if (full && pack_pays(B, s->n_par)) pack_full(h, 1, data, g, st);
+    if (full) pack_full(h, 1, data, g, st);
     launch_problems(g, B, s->n_par, st);
 }
 
